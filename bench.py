@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the deflated Schur-complement solve (Algorithm 3 of Joshi &
+Diamessis) on GB300.
+
+Workload (default): the 2-D Poisson-Neumann problem on [0,1]^2, 16 x 16 SMPM
+elements with n = 16 GLL points per direction (r = 65,536 nodes, k = 15,360
+interface slots), FP64, one seeded Fourier right-hand side, GMRES(50) to a
+relative residual of 1e-10.  A step is one complete schur_solve: right-hand
+side projection, b_S, the deflated block-Jacobi GMRES, assembly, recovery and
+zero-mean normalisation.  The factor step is timed once, separately.
+
+Reported: solves/s (whole job, all ranks), the same metric end to end through
+the host-pointer C ABI entry (host->device copy of f, device->host copy of u
+inside the timed region), the roofline of the dominant kernel pair (the fused
+S M^-1 apply) measured with CUDA events on the launching stream, SM clocks
+sampled during the timed region, and the CPU oracle timed on a bounded sample.
+
+--impl reference times the oracle (the plain FP64 CPU implementation written
+from the paper) on the same workload, one oracle solve per step.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solves/s to 1e-10 residual (mixed vs FP64); Schur-apply HBM GB/s"
+WORKLOAD = {"mx": 16, "my": 16, "n": 16, "nrhs": 1, "tol": 1e-10, "restart": 50, "seed": 1000}
+WORKLOAD_NAME = "SMPM Poisson-Neumann, 16x16 elements, n=16 (r=65536), FP64, 1 Fourier RHS, GMRES(50) to 1e-10"
+L2_FLUSH_BYTES = 512 << 20          # > 4x the 126 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- CPU oracle
+def oracle_solve_seconds(steps, warmup, seed):
+    """Time the oracle's Algorithm 3 on the bench workload in a fresh
+    single-threaded process; returns (per-solve seconds list, iterations)."""
+    code = r"""
+import json, os, sys, time
+sys.path.insert(0, %r)
+from oracle.smpm import SMPMGrid
+from oracle.schur import SchurSystem
+from oracle import methods
+from paper_1601_03432_gb300 import inputs
+W = %r
+g = SMPMGrid(W["mx"], W["my"], W["n"])
+s = SchurSystem(g)
+x, y = g.coords()
+f, _ = inputs.fourier_rhs(x, y, seed=W["seed"])
+times, its = [], None
+for i in range(%d + %d):
+    t = time.perf_counter()
+    u, info = methods.algorithm3(s, g.rhs(f), tol=W["tol"], restart=W["restart"])
+    dt = time.perf_counter() - t
+    if i >= %d:
+        times.append(dt)
+    its = info["iterations"]
+print(json.dumps({"times": times, "iterations": its}))
+""" % (ROOT, WORKLOAD, warmup, steps, warmup)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["times"], out["iterations"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, its = oracle_solve_seconds(args.steps, args.warmup, WORKLOAD["seed"])
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": "fp64", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d oracle Algorithm-3 solves of the bench workload (setup excluded), "
+                                   "%d GMRES iterations each" % (len(times), its)},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1601_03432_gb300 import Grid, inputs
+    from paper_1601_03432_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+
+    W = WORKLOAD
+    g = Grid(W["mx"], W["my"], W["n"])
+    t0 = time.perf_counter()
+    g.factor(tol=W["tol"], restart=W["restart"])
+    factor_s = time.perf_counter() - t0
+    x, y = g.node_coords()
+    f, _ = inputs.fourier_rhs(x, y, seed=W["seed"] + rank)
+    fd = torch.as_tensor(f, dtype=torch.float64, device="cuda")
+    ud = torch.zeros_like(fd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    rep = None
+    for _ in range(args.warmup):
+        rep = g.solve(fd, ud)[0]
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = []
+    launches = 0
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                   # evict L2 between steps (not timed)
+        evs[i][0].record(stream)
+        rep = g.solve(fd, ud)[0]
+        evs[i][1].record(stream)
+        iters.append(rep["iterations"])
+        launches += rep["launches"]
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms = float(t.item())
+    value = world * args.steps / (dev_ms / 1e3)
+
+    # ---- end to end through the host-pointer entry point
+    fh = torch.empty(g.r, dtype=torch.float64).pin_memory()
+    uh = torch.empty(g.r, dtype=torch.float64).pin_memory()
+    fh.copy_(torch.as_tensor(f))
+    fnp, unp = fh.numpy(), uh.numpy()
+    g.solve_host(fnp, unp)
+    barrier()
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        g.solve_host(fnp, unp)
+        e2e_ms += (time.perf_counter() - a) * 1e3
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / (float(t.item()) / 1e3)
+    err_e2e = float(np.abs(unp - ud.cpu().numpy()).max())
+
+    # ---- roofline of the fused S M^-1 apply (k_black + k_white)
+    kp, n, nel = g.kp, W["n"], W["mx"] * W["my"]
+    v = torch.randn(kp, dtype=torch.float64, device="cuda")
+    yv = torch.empty_like(v)
+    reps = 50
+    for _ in range(5):
+        g.apply_schur_precond(v, yv)
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(0.5)
+    ka.record(stream)
+    for _ in range(reps):
+        g.apply_schur_precond(v, yv)
+    kb.record(stream)
+    torch.cuda.synchronize()
+    k_ms = ka.elapsed_time(kb) / reps
+    nblack = g.nblack
+    nwhite = nel - nblack
+    M = 4 * n
+    mat_bytes = 8 * (nblack * (2 * M * M + 4 * n * n) + nwhite * M * M)
+    vec_bytes = 8 * (nblack * 4 * M + nwhite * 4 * M)   # v, t reads; t, y writes
+    flops = 2 * (nblack * (2 * M * M + 4 * n * n) + nwhite * M * M)
+    achieved_gbs = (mat_bytes + vec_bytes) / (k_ms * 1e-3) / 1e9
+    achieved_tf = flops / (k_ms * 1e-3) / 1e12
+    fp64_peak_tf = 152 * 2070e6 * 4 / 1e12    # 2 FP64 FMA / clk / SM
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle runs in a fresh single-threaded process after the GPU timing
+        cpu = {}
+        try:
+            cpu["times"], cpu["its"] = oracle_solve_seconds(2, 0, WORKLOAD["seed"])
+        except Exception as ex:  # reported, not fatal
+            cpu["error"] = str(ex)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, **W, "precision": "fp64", "precond": "block-Jacobi + deflation",
+                       "l2": "flushed between steps (512 MiB write, not timed)", "factor_s": round(factor_s, 3),
+                       "gmres_iterations": iters[-1], "wall_s": round(wall, 3)},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
+                    "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},
+            "gpu_launches": launches,
+            "roofline": {"kernel": "k_black+k_white (S M^-1 apply, FP64)", "bound": "alu",
+                         "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved_tf / fp64_peak_tf, "traffic": None,
+                         "achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                         "hbm_frac": achieved_gbs / hbm_peak, "us_per_apply": k_ms * 1e3,
+                         "note": "FP64 peak derived from unit counts and the max clock; working set L2-resident"},
+        }
+        if cpu is not None:
+            if "times" in cpu:
+                cv = len(cpu["times"]) / sum(cpu["times"])
+                line["cpu_baseline"] = {"value": cv, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                        "sample": "%d oracle Algorithm-3 solves of the bench workload (setup "
+                                                  "excluded), %d GMRES iterations" % (len(cpu["times"]), cpu["its"])}
+            else:
+                line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                        "sample": "failed: " + cpu.get("error", "")[:200]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,170 @@
+/*
+ * smpm.h -- C ABI of the GB300 solver for the deflated Schur-complement
+ * method of Joshi & Diamessis, "A deflated Schur complement method for the
+ * iterative solution of a high-order discontinuous element discretization of
+ * the Poisson equation" (arXiv 1601.03432).
+ *
+ * The library solves the 2-D Poisson-Neumann problem (Eq. poisson)
+ *     lap u = f on [0,Lx]x[0,Ly],   n.grad u = g on the boundary,
+ * discretised by the spectral multidomain penalty method (Sec. 1.2,
+ * Eq. smpm_poisson) on an my x mx grid of elements with n x n GLL points each,
+ * by Algorithm 3 (Sec. 2): GMRES on the deflated, block-Jacobi preconditioned
+ * Schur complement system, with the null-space projections of Sec. 1.4.
+ *
+ * Layouts (all arrays are plain float64, no padding between elements):
+ *   node vectors (length r = n*n*mx*my): element e = iy*mx + ix, then node
+ *     (a, b) at e*n*n + b*n + a (a = x index, fastest).
+ *   slot vectors (length kp = 4*n*mx*my): one slot per (element, face, face
+ *     node) at e*4n + F*n + t, faces F = W,E,S,N = 0,1,2,3, t increasing along
+ *     the face.  Slots on physical-boundary faces are padding for interface
+ *     vectors (Sec. 1.3: interfaces carry 2n nodes, n on either side) and
+ *     carry the Neumann data g for the solve.
+ *
+ * Ownership: the handle owns every device factor it allocates; the caller
+ * owns every buffer it passes.  Device pointers must be valid on the current
+ * CUDA device for the given stream.  Calls on one handle are not thread-safe.
+ * Every entry point returns an smpm_status; on error the output buffers are
+ * unspecified unless stated.  smpm_last_error() gives a message.
+ */
+#ifndef SMPM_H
+#define SMPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smpm_handle_s* smpm_handle;
+
+typedef enum {
+  SMPM_OK = 0,
+  SMPM_EINVAL = 1,        /* bad argument (sizes, null pointers, options)        */
+  SMPM_ENOINTERFACE = 2,  /* mx*my < 2: no interface, A is singular (Sec. 1.3)  */
+  SMPM_ENOMEM = 3,        /* device or host allocation failed                   */
+  SMPM_ECUDA = 4,         /* a CUDA call failed                                 */
+  SMPM_ENOTCONV = 5,      /* GMRES did not reach tol within maxit (u = best)    */
+  SMPM_EBREAKDOWN = 6,    /* Arnoldi breakdown before tol                       */
+  SMPM_ENAN = 7,          /* NaN/Inf met in the input or the iteration          */
+  SMPM_ESTATE = 8         /* call order violated (e.g. solve before factor)     */
+} smpm_status;
+
+/* Solver options.  precond: 0 = none (Algorithm 1), 1 = block-Jacobi
+ * (Algorithm 2), 2 = block-Jacobi + deflation (Algorithm 3, default).
+ * precision: 0 = FP64 throughout; 1 = FP32 inner GMRES inside FP64 iterative
+ * refinement.  tau_scale scales the penalty tau_F = -tau_scale n(n-1)/h_perp
+ * and robin_scale the Robin identity weight p_F = robin_scale n(n-1)/h_perp
+ * of Eq. smpm_poisson (defaults 1 and 0.25). */
+typedef struct {
+  double tol;          /* relative residual target of GMRES (default 1e-10)  */
+  int restart;         /* GMRES restart length m (default 50, max 200)        */
+  int maxit;           /* maximum Arnoldi steps in total (default 1000)       */
+  int precision;       /* 0 FP64, 1 FP32-inner + FP64 refinement              */
+  int precond;         /* 0, 1, 2 as above                                    */
+  double tau_scale;    /* default 1.0                                         */
+  double robin_scale;  /* default 0.25                                        */
+} smpm_opts;
+
+/* Per-solve report, written by schur_solve when the pointer is non-null. */
+typedef struct {
+  int iterations;        /* Arnoldi steps (all restarts, all refinement sweeps) */
+  int restarts;          /* GMRES restarts                                       */
+  int refinements;       /* outer refinement sweeps (precision 1), else 0        */
+  int converged;         /* 1 if the GMRES estimate reached tol                  */
+  double gmres_relres;   /* final GMRES residual estimate / ||P b_S||            */
+  double schur_relres;   /* ||b_S - S x_S|| / ||b_S|| recomputed in FP64          */
+  int launches;          /* CUDA kernels launched by this solve                  */
+} smpm_report;
+
+/* Fill o with the defaults listed above. */
+void smpm_default_opts(smpm_opts* o);
+
+/* Geometry of Sec. 1.2: an my x mx Cartesian grid of elements on
+ * [0,Lx]x[0,Ly] with n GLL points per direction (2 <= n <= 32,
+ * 1 <= mx, my <= 4096).  No device work.  Errors: EINVAL, ENOMEM. */
+smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* h);
+
+/* Sizes: r = n^2 mx my nodes, kp = 4 n mx my slots, d interfaces, k = 2 n d
+ * real interface slots, nblack checkerboard blocks.  Any pointer may be null. */
+smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d,
+                       long long* k, long long* nblack);
+
+/* Host arrays x, y (length r each) of the node coordinates (element map of
+ * Sec. 1.2), for building f and g. */
+smpm_status smpm_node_coords(smpm_handle h, double* x, double* y);
+
+/* Host array (length r) of the GLL quadrature weight of every node. */
+smpm_status smpm_node_mass(smpm_handle h, double* w);
+
+/* Factor step (Sec. 1.3 - 2): element operators A_e and their tensor-product
+ * inverses, the per-element interface factors T_e = B_e A_e^-1 E_e, the
+ * block-Jacobi blocks M_b = S[block, block] (Fig. 2) in the reduced form
+ * G_b = (I - X_b Y_b)^-1, the coarse matrix C = Z^T S Z and its regularised
+ * inverse, and the null vectors u_L, u_S, u_C (Sec. 1.4).  Computed on the
+ * host in FP64 and uploaded; o may be null for the defaults.  stream is a
+ * cudaStream_t (null = legacy default stream).  Errors: EINVAL,
+ * ENOINTERFACE, ENOMEM, ECUDA. */
+smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream);
+
+/* Algorithm 3 (or 1/2 per opts.precond) for nrhs right-hand sides.
+ *   f : device, r * nrhs, right-hand side of Eq. poisson at the nodes
+ *   g : device, kp * nrhs or null (= 0), Neumann data on boundary-face slots
+ *       (interface slots are ignored)
+ *   u : device, r * nrhs, output, normalised to zero GLL-weighted mean
+ *   tol <= 0 takes opts.tol.  rep (host, nrhs entries) may be null.
+ * The right-hand side b = f + tau g is projected out of u_L (Eq.
+ * regularize_poisson) and b_S out of u_S (Eq. regularize_schur).
+ * Errors: EINVAL, ESTATE (no factor), ENOTCONV (u holds the last iterate),
+ * ENAN, ECUDA. */
+smpm_status schur_solve(smpm_handle h, const double* f, const double* g, double tol,
+                        int nrhs, double* u, smpm_report* rep, void* stream);
+
+/* As schur_solve, with f, g and u in HOST memory: the library copies the
+ * inputs to its device staging buffers, solves, and copies u back before
+ * returning (the stream is synchronised). */
+smpm_status schur_solve_host(smpm_handle h, const double* f, const double* g, double tol,
+                             int nrhs, double* u, smpm_report* rep, void* stream);
+
+/* ---- single operators on device slot/node vectors (one right-hand side);
+ * these are the building blocks of the solve, exported for testing. -------- */
+
+/* y = S v, S = I + B A^-1 E (Eq. schur_complement_system); v, y: kp. */
+smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream);
+/* t = M^-1 v, block-Jacobi of Sec. 2 / Fig. 2; v, t: kp. */
+smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream);
+/* y = S M^-1 v computed in the fused checkerboard form; v, y: kp. */
+smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, void* stream);
+/* y = P v, P = I - S Z C^-1 Z^T (Eq. projection1) with the regularised C^-1. */
+smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream);
+/* y = Q v, Q = I - Z C^-1 Z^T S (Eq. projection2). */
+smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream);
+/* b_S = B A^-1 b (Algorithm 1, step 2); b: r, bS: kp. */
+smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream);
+/* u = A^-1 (b - E x) (back-substitution of Sec. 1.3); b: r, x: kp, u: r. */
+smpm_status smpm_recover(smpm_handle h, const double* b, const double* x, double* u, void* stream);
+/* Null vectors (device outputs): u_L (r), u_S (kp), u_C (d). Any may be null. */
+smpm_status smpm_null_vectors(smpm_handle h, double* uL, double* uS, double* uC, void* stream);
+/* Host copy of C = Z^T S Z (d*d, row-major). */
+smpm_status smpm_coarse_matrix(smpm_handle h, double* C);
+
+/* Host part of schur_factor only (no device work, no GPU needed): builds the
+ * FP64 factors in host memory so that they can be inspected with
+ * smpm_host_factor.  A later schur_factor recomputes them. */
+smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o);
+
+/* Copy the host factor array `name` into out (host, count doubles; count must
+ * equal the array length, returned through *len when out is null).  Names:
+ * "x1d","w1d","D" (Sec. 1.2), "T" (nel*(4n)^2, T_e row-major), "G", "X"
+ * (block-Jacobi, per black element), "black" (black element ids as doubles),
+ * "C","H","c0","uC" (coarse, Sec. 2), "uS","B1" (kp), "uL","what" (r),
+ * "null_iterations" (1 value). */
+smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long long count, long long* len);
+
+/* Release every resource of h (null is ignored). */
+void smpm_destroy(smpm_handle h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* smpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMPM_H */

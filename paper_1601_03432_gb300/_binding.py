@@ -1,0 +1,229 @@
+"""ctypes binding of libsmpm.so (argument marshalling only).
+
+Every computation runs inside the C ABI declared in ``include/smpm.h``; this
+module converts Python/NumPy/PyTorch arguments into plain pointers and sizes.
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmpm.so")
+
+SMPM_OK, SMPM_EINVAL, SMPM_ENOINTERFACE, SMPM_ENOMEM, SMPM_ECUDA, SMPM_ENOTCONV, SMPM_EBREAKDOWN, SMPM_ENAN, \
+    SMPM_ESTATE = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "EBREAKDOWN", "ENAN", "ESTATE"]
+
+# every symbol include/smpm.h declares
+EXPORTS = [
+    "smpm_default_opts", "smpm_setup", "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
+    "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
+    "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
+    "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
+]
+
+
+class SmpmOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("tau_scale", ctypes.c_double),
+                ("robin_scale", ctypes.c_double)]
+
+
+class SmpmReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("converged", ctypes.c_int), ("gmres_relres", ctypes.c_double), ("schur_relres", ctypes.c_double),
+                ("launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SmpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsmpm.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsmpm.so is not built; run __graft_entry__.build() "
+                              "(python -m paper_1601_03432_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        L.smpm_default_opts.argtypes = [ctypes.POINTER(SmpmOpts)]
+        L.smpm_default_opts.restype = None
+        L.smpm_setup.argtypes = [I, I, I, D, D, ctypes.POINTER(P)]
+        L.smpm_sizes.argtypes = [P] + [ctypes.POINTER(LL)] * 5
+        L.smpm_node_coords.argtypes = [P, P, P]
+        L.smpm_node_mass.argtypes = [P, P]
+        L.schur_factor.argtypes = [P, ctypes.POINTER(SmpmOpts), P]
+        L.schur_solve.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
+        L.schur_solve_host.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
+        for name in ["smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond", "smpm_apply_deflation",
+                     "smpm_apply_deflation_q", "smpm_schur_rhs"]:
+            getattr(L, name).argtypes = [P, P, P, P]
+        L.smpm_recover.argtypes = [P, P, P, P, P]
+        L.smpm_null_vectors.argtypes = [P, P, P, P, P]
+        L.smpm_coarse_matrix.argtypes = [P, P]
+        L.smpm_factor_host_only.argtypes = [P, ctypes.POINTER(SmpmOpts)]
+        L.smpm_host_factor.argtypes = [P, ctypes.c_char_p, P, LL, ctypes.POINTER(LL)]
+        L.smpm_destroy.argtypes = [P]
+        L.smpm_destroy.restype = None
+        L.smpm_last_error.argtypes = []
+        L.smpm_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("smpm_default_opts", "smpm_destroy", "smpm_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(status, allow=()):
+    if status != SMPM_OK and status not in allow:
+        raise SmpmError(status, lib().smpm_last_error().decode())
+    return status
+
+
+def default_opts(**kw):
+    o = SmpmOpts()
+    lib().smpm_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / NumPy array (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("arrays must be contiguous float64")
+        return x.ctypes.data
+    if x.dtype.__str__() != "torch.float64" or not x.is_contiguous():
+        raise TypeError("tensors must be contiguous float64")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Grid:
+    """One SMPM grid and its factors, owned through an smpm_handle."""
+
+    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0):
+        h = ctypes.c_void_p()
+        check(lib().smpm_setup(mx, my, n, float(Lx), float(Ly), ctypes.byref(h)))
+        self.h = h
+        self.mx, self.my, self.n, self.Lx, self.Ly = mx, my, n, Lx, Ly
+        vals = [ctypes.c_longlong() for _ in range(5)]
+        check(lib().smpm_sizes(h, *[ctypes.byref(v) for v in vals]))
+        self.r, self.kp, self.d, self.k, self.nblack = [v.value for v in vals]
+        self.factored = False
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().smpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def node_coords(self):
+        x = np.empty(self.r)
+        y = np.empty(self.r)
+        check(lib().smpm_node_coords(self.h, x.ctypes.data, y.ctypes.data))
+        return x, y
+
+    def node_mass(self):
+        w = np.empty(self.r)
+        check(lib().smpm_node_mass(self.h, w.ctypes.data))
+        return w
+
+    def factor(self, stream=None, **opts):
+        o = default_opts(**opts)
+        check(lib().schur_factor(self.h, ctypes.byref(o), _stream(stream)))
+        self.opts = o
+        self.factored = True
+
+    def factor_host_only(self, **opts):
+        o = default_opts(**opts)
+        check(lib().smpm_factor_host_only(self.h, ctypes.byref(o)))
+
+    def host_factor(self, name):
+        n = ctypes.c_longlong()
+        check(lib().smpm_host_factor(self.h, name.encode(), None, 0, ctypes.byref(n)))
+        out = np.empty(n.value)
+        check(lib().smpm_host_factor(self.h, name.encode(), out.ctypes.data, n.value, None))
+        return out
+
+    def coarse_matrix(self):
+        C = np.empty((self.d, self.d))
+        check(lib().smpm_coarse_matrix(self.h, C.ctypes.data))
+        return C
+
+    def solve(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
+        """schur_solve on device tensors (float64, contiguous); returns the reports."""
+        reps = (SmpmReport * nrhs)()
+        st = lib().schur_solve(self.h, _ptr(f), _ptr(g), float(tol), nrhs, _ptr(u), reps, _stream(stream))
+        check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
+        return [r.as_dict() for r in reps]
+
+    def solve_host(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
+        """schur_solve_host on host NumPy arrays."""
+        reps = (SmpmReport * nrhs)()
+        st = lib().schur_solve_host(self.h, _ptr(f), _ptr(g), float(tol), nrhs, _ptr(u), reps, _stream(stream))
+        check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
+        return [r.as_dict() for r in reps]
+
+    def _op(self, name, v, out, stream=None):
+        check(getattr(lib(), name)(self.h, _ptr(v), _ptr(out), _stream(stream)))
+        return out
+
+    def apply_schur(self, v, out, stream=None):
+        return self._op("smpm_apply_schur", v, out, stream)
+
+    def apply_precond(self, v, out, stream=None):
+        return self._op("smpm_apply_precond", v, out, stream)
+
+    def apply_schur_precond(self, v, out, stream=None):
+        return self._op("smpm_apply_schur_precond", v, out, stream)
+
+    def apply_deflation(self, v, out, stream=None):
+        return self._op("smpm_apply_deflation", v, out, stream)
+
+    def apply_deflation_q(self, v, out, stream=None):
+        return self._op("smpm_apply_deflation_q", v, out, stream)
+
+    def schur_rhs(self, b, out, stream=None):
+        return self._op("smpm_schur_rhs", b, out, stream)
+
+    def recover(self, b, x, out, stream=None):
+        check(lib().smpm_recover(self.h, _ptr(b), _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def null_vectors(self, uL, uS, uC, stream=None):
+        check(lib().smpm_null_vectors(self.h, _ptr(uL), _ptr(uS), _ptr(uC), _stream(stream)))

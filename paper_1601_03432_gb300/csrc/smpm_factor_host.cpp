@@ -1,0 +1,784 @@
+// Host factor step of the deflated Schur-complement method (FP64).
+//
+// Builds, from the definitions of Sec. 1.2 - 2 of Joshi & Diamessis:
+//   * GLL nodes/weights (Golub-Welsch on the Jacobi matrix of P_N', Newton
+//     polish) and the differentiation matrix (barycentric form), Sec. 1.2;
+//   * the element operator A_e of Sec. 1.3, which on an axis-aligned
+//     rectangle is exactly the Kronecker sum I (x) K_x + K_y (x) I of two 1-D
+//     operators, inverted by fast diagonalisation (K = V diag(lam) V^-1 from
+//     the symmetric eigenproblem of W^1/2 K W^-1/2, W the GLL weights);
+//   * T_e = B_e A_e^-1 E_e (4n x 4n): the map from element e's own interface
+//     slots to the neighbours' slots facing e, i.e. the element's share of
+//     S = I + B A^-1 E (Eq. schur_complement_system);
+//   * the block-Jacobi blocks of Sec. 2 / Fig. 2 in reduced form: for a black
+//     element, M_b = [[I, X], [Y, I]] over (own slots, facing slots) with
+//     Y = T_e and X the four n x n blocks of the neighbours' T facing e, and
+//     M_b^-1 is applied through G = (I - X Y)^-1;
+//   * C = Z^T S Z, its right null vector c0 (Z c0 = B 1), its left null
+//     vector u_C and the regularised inverse H (C y = r - u_C u_C^T r,
+//     c0^T y = 0) from one dense LU of the bordered matrix [[C, c0], [c0^T, 0]];
+//   * u_S, the unit left null vector of S, from the bordered system
+//     [[S^T, a], [a^T, 0]] [y; eta] = [0; 1], a = B1/||B1||, by
+//     right-preconditioned GMRES with iterative refinement,
+//     and u_L = -A^-T B^T u_S normalised (u_L^T L = -u_S^T S B = 0), Sec. 1.4.
+//
+// Identical element matrices (same face types; h is uniform per direction)
+// are computed once and copied: the stored factors are per element.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "smpm_internal.h"
+
+namespace smpm {
+namespace {
+
+// ---------------------------------------------------------------- dense LA
+// Cyclic Jacobi eigen-solver for a symmetric n x n matrix (row-major).
+// On return lam holds the eigenvalues and V (row-major) the eigenvectors as
+// columns.
+void sym_eig(int n, std::vector<double> A, std::vector<double>* lam, std::vector<double>* V) {
+  V->assign(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) (*V)[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i * n + j] * A[i * n + j];
+        if (i != j) off += A[i * n + j] * A[i * n + j];
+      }
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double app = A[p * n + p], aqq = A[q * n + q];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- J^T A J
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = (*V)[k * n + p], vkq = (*V)[k * n + q];
+          (*V)[k * n + p] = c * vkp - s * vkq;
+          (*V)[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam->resize(n);
+  for (int i = 0; i < n; ++i) (*lam)[i] = A[i * n + i];
+}
+
+// LU with partial pivoting (row-major, in place).
+struct DenseLU {
+  int n = 0;
+  std::vector<double> a;
+  std::vector<int> piv;
+  bool ok = false;
+};
+
+DenseLU lu_factor(const double* A, int n) {
+  DenseLU f;
+  f.n = n;
+  f.a.assign(A, A + static_cast<size_t>(n) * n);
+  f.piv.resize(n);
+  double* a = f.a.data();
+  f.ok = true;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(a[static_cast<size_t>(k) * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = std::fabs(a[static_cast<size_t>(i) * n + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    f.piv[k] = p;
+    if (best == 0.0) { f.ok = false; continue; }
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[static_cast<size_t>(k) * n + j], a[static_cast<size_t>(p) * n + j]);
+    double inv = 1.0 / a[static_cast<size_t>(k) * n + k];
+    double* rk = a + static_cast<size_t>(k) * n;
+#pragma omp parallel for schedule(static) if (n - k > 256)
+    for (int i = k + 1; i < n; ++i) {
+      double* ri = a + static_cast<size_t>(i) * n;
+      double l = ri[k] * inv;
+      ri[k] = l;
+      if (l != 0.0)
+        for (int j = k + 1; j < n; ++j) ri[j] -= l * rk[j];
+    }
+  }
+  return f;
+}
+
+void lu_solve(const DenseLU& f, double* b) {
+  const int n = f.n;
+  const double* a = f.a.data();
+  for (int k = 0; k < n; ++k)
+    if (f.piv[k] != k) std::swap(b[k], b[f.piv[k]]);
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    const double* ri = a + static_cast<size_t>(i) * n;
+    for (int j = 0; j < i; ++j) s -= ri[j] * b[j];
+    b[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    const double* ri = a + static_cast<size_t>(i) * n;
+    for (int j = i + 1; j < n; ++j) s -= ri[j] * b[j];
+    b[i] = s / ri[i];
+  }
+}
+
+// Solve A^T x = b with the factors of A.
+void lu_solve_T(const DenseLU& f, double* b) {
+  const int n = f.n;
+  const double* a = f.a.data();
+  for (int j = 0; j < n; ++j) {  // U^T z = b
+    double s = b[j];
+    for (int i = 0; i < j; ++i) s -= a[static_cast<size_t>(i) * n + j] * b[i];
+    b[j] = s / a[static_cast<size_t>(j) * n + j];
+  }
+  for (int j = n - 1; j >= 0; --j) {  // L^T w = z
+    double s = b[j];
+    for (int i = j + 1; i < n; ++i) s -= a[static_cast<size_t>(i) * n + j] * b[i];
+    b[j] = s;
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (f.piv[k] != k) std::swap(b[k], b[f.piv[k]]);
+}
+
+// -------------------------------------------------------------- Legendre
+void legendre(int N, double x, double* p, double* dp) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (N == 0) { *p = 1.0; *dp = 0.0; return; }
+  for (int k = 1; k < N; ++k) {
+    double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+    double d2 = d0 + (2.0 * k + 1.0) * p1;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *p = p1;
+  *dp = d1;
+}
+
+// 1-D operator K (n x n, row-major) of one direction: s^2 D^2 plus the face
+// rows of Eq. smpm_poisson: on the low face (outward normal -1) the row gets
+// tau (p * chi_lo * e_0 - s D[0,:]), on the high face tau (p * chi_hi *
+// e_{n-1} + s D[n-1,:]); chi = 1 for an interface face, 0 on the boundary.
+void build_K(const Geometry& g, const std::vector<double>& D, double s, double tau, double p, bool chi_lo,
+             bool chi_hi, std::vector<double>* K) {
+  const int n = g.n;
+  K->assign(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double acc = 0;
+      for (int c = 0; c < n; ++c) acc += D[i * n + c] * D[c * n + j];
+      (*K)[i * n + j] = s * s * acc;
+    }
+  for (int j = 0; j < n; ++j) {
+    (*K)[j] += tau * (-s * D[j]);
+    (*K)[(n - 1) * n + j] += tau * (s * D[(n - 1) * n + j]);
+  }
+  if (chi_lo) (*K)[0] += tau * p;
+  if (chi_hi) (*K)[(n - 1) * n + n - 1] += tau * p;
+}
+
+// Fast-diagonalisation factors of K: out = [V (n*n) | Vinv (n*n) | lam (n)].
+void fast_diag(int n, const std::vector<double>& w, const std::vector<double>& K, double* out) {
+  std::vector<double> Ks(static_cast<size_t>(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double a = std::sqrt(w[i]) * K[i * n + j] / std::sqrt(w[j]);
+      double b = std::sqrt(w[j]) * K[j * n + i] / std::sqrt(w[i]);
+      Ks[i * n + j] = 0.5 * (a + b);
+    }
+  std::vector<double> lam, Q;
+  sym_eig(n, Ks, &lam, &Q);
+  double* V = out;
+  double* Vi = out + n * n;
+  double* L = out + 2 * n * n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      V[i * n + j] = Q[i * n + j] / std::sqrt(w[i]);
+      Vi[i * n + j] = Q[j * n + i] * std::sqrt(w[j]);
+    }
+  for (int i = 0; i < n; ++i) L[i] = lam[i];
+}
+
+// U = A_e^-1 B for one element (B, U: n x n with U[b][a]), by fast
+// diagonalisation: U = Vy ((Vy^-1 B Vx^-T) ./ (lx_i + ly_j)) Vx^T.
+void elem_solve(int n, const double* fx, const double* fy, const double* B, double* U) {
+  const double *Vx = fx, *Vxi = fx + n * n, *lx = fx + 2 * n * n;
+  const double *Vy = fy, *Vyi = fy + n * n, *ly = fy + 2 * n * n;
+  std::vector<double> t1(n * n), t2(n * n);
+  for (int j = 0; j < n; ++j)  // t1 = Vyi B
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int b = 0; b < n; ++b) s += Vyi[j * n + b] * B[b * n + a];
+      t1[j * n + a] = s;
+    }
+  for (int j = 0; j < n; ++j)  // t2 = t1 Vxi^T ./ (lx + ly)
+    for (int i = 0; i < n; ++i) {
+      double s = 0;
+      for (int a = 0; a < n; ++a) s += t1[j * n + a] * Vxi[i * n + a];
+      t2[j * n + i] = s / (lx[i] + ly[j]);
+    }
+  for (int j = 0; j < n; ++j)  // t1 = t2 Vx^T
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int i = 0; i < n; ++i) s += t2[j * n + i] * Vx[a * n + i];
+      t1[j * n + a] = s;
+    }
+  for (int b = 0; b < n; ++b)  // U = Vy t1
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int j = 0; j < n; ++j) s += Vy[b * n + j] * t1[j * n + a];
+      U[b * n + a] = s;
+    }
+}
+
+// U = A_e^-T B: U = Vyi^T ((Vy^T B Vx) ./ (lx_i + ly_j)) Vxi.
+void elem_solve_T(int n, const double* fx, const double* fy, const double* B, double* U) {
+  const double *Vx = fx, *Vxi = fx + n * n, *lx = fx + 2 * n * n;
+  const double *Vy = fy, *Vyi = fy + n * n, *ly = fy + 2 * n * n;
+  std::vector<double> t1(n * n), t2(n * n);
+  for (int j = 0; j < n; ++j)
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int b = 0; b < n; ++b) s += Vy[b * n + j] * B[b * n + a];
+      t1[j * n + a] = s;
+    }
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      double s = 0;
+      for (int a = 0; a < n; ++a) s += t1[j * n + a] * Vx[a * n + i];
+      t2[j * n + i] = s / (lx[i] + ly[j]);
+    }
+  for (int j = 0; j < n; ++j)
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int i = 0; i < n; ++i) s += t2[j * n + i] * Vxi[i * n + a];
+      t1[j * n + a] = s;
+    }
+  for (int b = 0; b < n; ++b)
+    for (int a = 0; a < n; ++a) {
+      double s = 0;
+      for (int j = 0; j < n; ++j) s += Vyi[j * n + b] * t1[j * n + a];
+      U[b * n + a] = s;
+    }
+}
+
+// n_F . grad U at face node t of face F of one element (U[b][a]).
+double normal_derivative(const Geometry& g, const std::vector<double>& D, const double* U, int F, int t) {
+  const int n = g.n;
+  const double sx = 2.0 / g.hx, sy = 2.0 / g.hy;
+  double acc = 0;
+  switch (F) {
+    case FACE_W: for (int c = 0; c < n; ++c) acc += D[c] * U[t * n + c]; return -sx * acc;
+    case FACE_E: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[t * n + c]; return sx * acc;
+    case FACE_S: for (int c = 0; c < n; ++c) acc += D[c] * U[c * n + t]; return -sy * acc;
+    default: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[c * n + t]; return sy * acc;
+  }
+}
+
+struct Ctx {
+  const Geometry& g;
+  Factors* f;
+  double tau(int F) const { return F < 2 ? f->tau_x : f->tau_y; }
+  double pw(int F) const { return F < 2 ? f->p_x : f->p_y; }
+  const double* fx(int e) const { return f->fdx.data() + static_cast<size_t>(xclass(g, e)) * (2 * g.n * g.n + g.n); }
+  const double* fy(int e) const { return f->fdy.data() + static_cast<size_t>(yclass(g, e)) * (2 * g.n * g.n + g.n); }
+};
+
+// T_e for element e (M x M, row (F,t) = the flux into the neighbour across F,
+// column (G,s) = e's own slot).  Row (F,t) equals the B row of slot
+// (nbr(e,F), opp F, t): -tau_F (p_F w - n_F.grad w) at e's face node (F,t),
+// with w = A_e^-1 E_e (unit value at the face node of slot (G,s)).
+void element_T(const Ctx& c, int e, double* T) {
+  const Geometry& g = c.g;
+  const int n = g.n, M = g.M;
+  std::fill(T, T + M * M, 0.0);
+  std::vector<double> B(n * n), U(n * n);
+  for (int G = 0; G < 4; ++G) {
+    if (g.neighbour(e, G) < 0) continue;
+    for (int s = 0; s < n; ++s) {
+      std::fill(B.begin(), B.end(), 0.0);
+      int a, b;
+      g.face_node(G, s, &a, &b);
+      B[b * n + a] = 1.0;
+      elem_solve(n, c.fx(e), c.fy(e), B.data(), U.data());
+      for (int F = 0; F < 4; ++F) {
+        if (g.neighbour(e, F) < 0) continue;
+        for (int t = 0; t < n; ++t) {
+          int aa, bb;
+          g.face_node(F, t, &aa, &bb);
+          double val = c.pw(F) * U[bb * n + aa] - normal_derivative(g, c.f->D, U.data(), F, t);
+          T[(F * n + t) * M + G * n + s] = -c.tau(F) * val;
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------- slot operators (host)
+// out = S^T y on padded slot vectors: out_e = y_e + T_e^T yhat_e, yhat_e the
+// neighbours' slots facing e.
+void apply_ST(const Geometry& g, const Factors& f, const double* y, double* out) {
+  const int n = g.n, M = g.M;
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e) {
+    double yh[4 * kMaxN];
+    for (int F = 0; F < 4; ++F) {
+      int e2 = g.neighbour(static_cast<int>(e), F);
+      for (int t = 0; t < n; ++t) yh[F * n + t] = e2 >= 0 ? y[e2 * M + opposite(F) * n + t] : 0.0;
+    }
+    const double* T = f.T.data() + static_cast<size_t>(e) * M * M;
+    for (int col = 0; col < M; ++col) {
+      double s = y[e * M + col];
+      for (int row = 0; row < M; ++row) s += T[row * M + col] * yh[row];
+      out[e * M + col] = s;
+    }
+  }
+}
+
+// out = M^-T y, block by block: with M_b = [[I, X], [Y, I]],
+// M_b^T [a; b] = [p; q] gives a = G^T (p - Y^T q), b = q - X^T a.
+void apply_MinvT(const Geometry& g, const Factors& f, const double* y, double* out) {
+  const int n = g.n, M = g.M;
+  const long long nb = static_cast<long long>(f.black.size());
+#pragma omp parallel for schedule(static)
+  for (long long ib = 0; ib < nb; ++ib) {
+    int e = f.black[ib];
+    double p[4 * kMaxN], q[4 * kMaxN], r1[4 * kMaxN], a[4 * kMaxN];
+    int nb4[4];
+    for (int F = 0; F < 4; ++F) {
+      nb4[F] = g.neighbour(e, F);
+      for (int t = 0; t < n; ++t) {
+        p[F * n + t] = y[e * M + F * n + t];
+        q[F * n + t] = nb4[F] >= 0 ? y[nb4[F] * M + opposite(F) * n + t] : 0.0;
+      }
+    }
+    const double* T = f.T.data() + static_cast<size_t>(e) * M * M;
+    const double* Gm = f.G.data() + static_cast<size_t>(ib) * M * M;
+    const double* X = f.X.data() + static_cast<size_t>(ib) * 4 * n * n;
+    for (int c2 = 0; c2 < M; ++c2) {
+      double s = p[c2];
+      for (int row = 0; row < M; ++row) s -= T[row * M + c2] * q[row];
+      r1[c2] = s;
+    }
+    for (int c2 = 0; c2 < M; ++c2) {
+      double s = 0;
+      for (int row = 0; row < M; ++row) s += Gm[row * M + c2] * r1[row];
+      a[c2] = s;
+    }
+    for (int F = 0; F < 4; ++F) {
+      for (int t = 0; t < n; ++t) {
+        double s = 0;
+        for (int s2 = 0; s2 < n; ++s2) s += X[(F * n + s2) * n + t] * a[F * n + s2];
+        out[e * M + F * n + t] = a[F * n + t];
+        if (nb4[F] >= 0) out[nb4[F] * M + opposite(F) * n + t] = q[F * n + t] - s;
+      }
+    }
+  }
+}
+
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+// Restarted right-preconditioned GMRES (MGS) on the bordered transposed
+// system for u_S, with the unit border vector a = B1 / ||B1||.  Unknown
+// z = [y (kp); eta]; operator K P z = [S^T (M^-T y) + a eta; a^T (M^-T y)].
+// The true residual is recomputed at every restart and the solve repeats
+// (iterative refinement) until it stops decreasing or reaches round-off.
+int left_null_S(const Geometry& g, Factors* f, std::string* err) {
+  const size_t kp = static_cast<size_t>(g.kp), N = kp + 1;
+  std::vector<double> a(f->B1);
+  double an = std::sqrt(dot(a, a));
+  for (auto& v : a) v /= an;
+  std::vector<double> tmp(kp), tmp2(kp);
+  auto op = [&](const std::vector<double>& z, std::vector<double>& out) {
+    apply_MinvT(g, *f, z.data(), tmp.data());
+    apply_ST(g, *f, tmp.data(), tmp2.data());
+    double eta = z[kp], s = 0;
+    for (size_t i = 0; i < kp; ++i) {
+      out[i] = tmp2[i] + a[i] * eta;
+      s += a[i] * tmp[i];
+    }
+    out[kp] = s;
+  };
+  const int m = 300, maxit = 4000;
+  std::vector<double> x(N, 0.0), r(N, 0.0), w(N);
+  r[kp] = 1.0;  // b = [0; 1], x0 = 0
+  std::vector<std::vector<double>> V;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1);
+  int total = 0;
+  double beta = 1.0, best = 1e300;
+  while (total < maxit) {
+    beta = std::sqrt(dot(r, r));
+    if (beta <= 1e-16 || beta >= 0.5 * best) break;  // round-off reached or no progress
+    best = beta;
+    const double tol = 1e-3 * beta;                   // each cycle gains three digits
+    V.assign(1, r);
+    for (auto& v : V[0]) v /= beta;
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < m && total < maxit; ++j) {
+      op(V[j], w);
+      for (int i = 0; i <= j; ++i) {
+        double h = dot(V[i], w);
+        H[i * m + j] = h;
+        for (size_t q = 0; q < N; ++q) w[q] -= h * V[i][q];
+      }
+      for (int i = 0; i <= j; ++i) {  // second Gram-Schmidt sweep
+        double h = dot(V[i], w);
+        H[i * m + j] += h;
+        for (size_t q = 0; q < N; ++q) w[q] -= h * V[i][q];
+      }
+      double hn = std::sqrt(dot(w, w));
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      double den = std::hypot(H[j * m + j], hn);
+      cs[j] = H[j * m + j] / den;
+      sn[j] = hn / den;
+      H[j * m + j] = den;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++total;
+      if (std::fabs(gv[j + 1]) <= tol || hn == 0.0) { ++j; break; }
+      V.push_back(w);
+      for (auto& v : V.back()) v /= hn;
+    }
+    std::vector<double> yv(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int k2 = i + 1; k2 < j; ++k2) s -= H[i * m + k2] * yv[k2];
+      yv[i] = s / H[i * m + i];
+    }
+    for (int i = 0; i < j; ++i)
+      for (size_t q = 0; q < N; ++q) x[q] += yv[i] * V[i][q];
+    op(x, w);
+    for (size_t q = 0; q < N; ++q) r[q] = (q == kp ? 1.0 : 0.0) - w[q];
+  }
+  f->null_iterations = total;
+  f->null_relres = std::sqrt(dot(r, r));
+  if (!(f->null_relres <= 1e-12)) {
+    *err = "u_S bordered solve did not converge (residual " + std::to_string(f->null_relres) + ")";
+    return SMPM_ENOTCONV;
+  }
+  std::vector<double> y(kp);
+  apply_MinvT(g, *f, x.data(), y.data());
+  double nrm = std::sqrt(dot(y, y));
+  size_t imax = 0;
+  for (size_t i = 0; i < kp; ++i)
+    if (std::fabs(y[i]) > std::fabs(y[imax])) imax = i;
+  double sg = y[imax] >= 0 ? 1.0 : -1.0;
+  f->uS.resize(kp);
+  for (size_t i = 0; i < kp; ++i) f->uS[i] = sg * y[i] / nrm;
+  return SMPM_OK;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- public
+void gll(int n, std::vector<double>* x, std::vector<double>* w) {
+  const int N = n - 1;
+  x->assign(n, 0.0);
+  w->assign(n, 0.0);
+  (*x)[0] = -1.0;
+  (*x)[n - 1] = 1.0;
+  const int m = N - 1;  // interior nodes: zeros of P_N' ~ Gegenbauer C^(3/2)_{N-1}
+  if (m > 0) {
+    std::vector<double> J(static_cast<size_t>(m) * m, 0.0), lam, V;
+    for (int k = 1; k < m; ++k) {
+      double b = std::sqrt(k * (k + 2.0) / ((2.0 * k + 1.0) * (2.0 * k + 3.0)));
+      J[(k - 1) * m + k] = b;
+      J[k * m + k - 1] = b;
+    }
+    sym_eig(m, J, &lam, &V);
+    std::sort(lam.begin(), lam.end());
+    for (int i = 0; i < m; ++i) {
+      double xi = lam[i];
+      for (int it = 0; it < 8; ++it) {  // Newton on P_N'
+        double p, dp;
+        legendre(N, xi, &p, &dp);
+        double ddp = (2.0 * xi * dp - N * (N + 1.0) * p) / (1.0 - xi * xi);
+        double step = dp / ddp;
+        xi -= step;
+        if (std::fabs(step) < 1e-17) break;
+      }
+      (*x)[i + 1] = xi;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    double p, dp;
+    legendre(N, (*x)[i], &p, &dp);
+    (*w)[i] = 2.0 / (N * (N + 1.0) * p * p);
+  }
+}
+
+void diff_matrix(const std::vector<double>& x, std::vector<double>* D) {
+  const int n = static_cast<int>(x.size());
+  std::vector<double> lam(n, 1.0);  // barycentric weights
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (x[j] - x[k]);
+  D->assign(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) {
+        double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+        (*D)[i * n + j] = v;
+        diag -= v;
+      }
+    (*D)[i * n + i] = diag;
+  }
+}
+
+int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
+  const int n = g.n, M = g.M;
+  const double nn1 = n * (n - 1.0);
+  f->tau_x = -o.tau_scale * nn1 / g.hx;
+  f->tau_y = -o.tau_scale * nn1 / g.hy;
+  f->p_x = o.robin_scale * nn1 / g.hx;
+  f->p_y = o.robin_scale * nn1 / g.hy;
+  gll(n, &f->x1d, &f->w1d);
+  diff_matrix(f->x1d, &f->D);
+
+  // 1-D operators and their fast diagonalisation, 4 classes per direction
+  const int fds = 2 * n * n + n;
+  f->fdx.assign(4 * fds, 0.0);
+  f->fdy.assign(4 * fds, 0.0);
+  std::vector<double> K;
+  for (int cls = 0; cls < 4; ++cls) {
+    build_K(g, f->D, 2.0 / g.hx, f->tau_x, f->p_x, cls & 1, cls & 2, &K);
+    fast_diag(n, f->w1d, K, f->fdx.data() + cls * fds);
+    build_K(g, f->D, 2.0 / g.hy, f->tau_y, f->p_y, cls & 1, cls & 2, &K);
+    fast_diag(n, f->w1d, K, f->fdy.data() + cls * fds);
+  }
+  for (int cls = 0; cls < 4; ++cls)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double* lx = f->fdx.data() + cls * fds + 2 * n * n;
+        const double* ly = f->fdy.data() + cls * fds + 2 * n * n;
+        if (!(std::fabs(lx[i] + ly[j]) > 0)) {
+          // only the element without interfaces (mx = my = 1) is singular
+          if ((cls & 3) != 0) { *err = "singular element operator"; return SMPM_EINVAL; }
+        }
+      }
+  Ctx c{g, f};
+
+  // T_e, computed once per face-type mask
+  f->T.assign(static_cast<size_t>(g.nel) * M * M, 0.0);
+  std::map<int, std::vector<double>> tcache;
+  for (long long e = 0; e < g.nel; ++e) {
+    int key = g.mask(static_cast<int>(e));
+    if (!tcache.count(key)) {
+      std::vector<double> T(static_cast<size_t>(M) * M);
+      element_T(c, static_cast<int>(e), T.data());
+      tcache[key] = T;
+    }
+  }
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e) {
+    const std::vector<double>& T = tcache.at(g.mask(static_cast<int>(e)));
+    std::memcpy(f->T.data() + static_cast<size_t>(e) * M * M, T.data(), sizeof(double) * M * M);
+  }
+  f->Rs.assign(static_cast<size_t>(g.nel) * M * 4, 0.0);
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e) {
+    const double* T = f->T.data() + static_cast<size_t>(e) * M * M;
+    double* R = f->Rs.data() + static_cast<size_t>(e) * M * 4;
+    for (int row = 0; row < M; ++row)
+      for (int G = 0; G < 4; ++G) {
+        double s = 0;
+        for (int q = 0; q < n; ++q) s += T[row * M + G * n + q];
+        R[row * 4 + G] = s;
+      }
+  }
+
+  // checkerboard blocks
+  f->black.clear();
+  f->white.clear();
+  for (long long e = 0; e < g.nel; ++e) (g.black(static_cast<int>(e)) ? f->black : f->white).push_back(static_cast<int>(e));
+  const size_t nb = f->black.size();
+  f->G.assign(nb * M * M, 0.0);
+  f->X.assign(nb * 4 * n * n, 0.0);
+  std::map<long long, std::vector<double>> gcache;
+  for (size_t ib = 0; ib < nb; ++ib) {
+    int e = f->black[ib];
+    double* X = f->X.data() + ib * 4 * n * n;
+    long long key = g.mask(e);
+    for (int F = 0; F < 4; ++F) {
+      int e2 = g.neighbour(e, F);
+      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
+      if (e2 < 0) continue;
+      const double* T2 = f->T.data() + static_cast<size_t>(e2) * M * M;
+      int Fo = opposite(F);
+      for (int t = 0; t < n; ++t)
+        for (int s = 0; s < n; ++s) X[(F * n + t) * n + s] = T2[(Fo * n + t) * M + Fo * n + s];
+    }
+    if (!gcache.count(key)) {
+      const double* Y = f->T.data() + static_cast<size_t>(e) * M * M;
+      std::vector<double> A(static_cast<size_t>(M) * M, 0.0);
+      for (int F = 0; F < 4; ++F)
+        for (int t = 0; t < n; ++t)
+          for (int col = 0; col < M; ++col) {
+            double s = 0;
+            for (int q = 0; q < n; ++q) s += X[(F * n + t) * n + q] * Y[(F * n + q) * M + col];
+            A[(F * n + t) * M + col] = (F * n + t == col ? 1.0 : 0.0) - s;
+          }
+      DenseLU lu = lu_factor(A.data(), M);
+      if (!lu.ok) { *err = "singular block-Jacobi block"; return SMPM_EINVAL; }
+      std::vector<double> Gi(static_cast<size_t>(M) * M), col(M);
+      for (int j = 0; j < M; ++j) {
+        std::fill(col.begin(), col.end(), 0.0);
+        col[j] = 1.0;
+        lu_solve(lu, col.data());
+        for (int i = 0; i < M; ++i) Gi[i * M + j] = col[i];
+      }
+      gcache[key] = Gi;
+    }
+    const std::vector<double>& Gi = gcache.at(key);
+    std::memcpy(f->G.data() + ib * M * M, Gi.data(), sizeof(double) * M * M);
+  }
+
+  // B 1 and the coarse matrix C = Z^T S Z
+  f->B1.assign(g.kp, 0.0);
+  for (long long e = 0; e < g.nel; ++e)
+    for (int F = 0; F < 4; ++F)
+      if (g.neighbour(static_cast<int>(e), F) >= 0)
+        for (int t = 0; t < n; ++t) f->B1[e * M + F * n + t] = -(F < 2 ? f->tau_x * f->p_x : f->tau_y * f->p_y);
+  const int d = static_cast<int>(g.d);
+  f->C.assign(static_cast<size_t>(d) * d, 0.0);
+  f->c0.assign(d, 0.0);
+  for (int j = 0; j < d; ++j) f->C[static_cast<size_t>(j) * d + j] = 2.0 * n;
+  for (long long e = 0; e < g.nel; ++e) {
+    const double* R = f->Rs.data() + static_cast<size_t>(e) * M * 4;
+    for (int Fp = 0; Fp < 4; ++Fp) {
+      int i = g.iface(static_cast<int>(e), Fp);
+      if (i < 0) continue;
+      f->c0[i] = -(Fp < 2 ? f->tau_x * f->p_x : f->tau_y * f->p_y);
+      for (int F = 0; F < 4; ++F) {
+        int j = g.iface(static_cast<int>(e), F);
+        if (j < 0) continue;
+        double s = 0;
+        for (int t = 0; t < n; ++t) s += R[(Fp * n + t) * 4 + F];
+        f->C[static_cast<size_t>(i) * d + j] += s;
+      }
+    }
+  }
+  // bordered K = [[C, c0], [c0^T, 0]]: u_C from K^T [y; eta] = [0; 1], H from K^-1
+  {
+    const int d1 = d + 1;
+    std::vector<double> K1(static_cast<size_t>(d1) * d1, 0.0);
+    for (int i = 0; i < d; ++i) {
+      for (int j = 0; j < d; ++j) K1[static_cast<size_t>(i) * d1 + j] = f->C[static_cast<size_t>(i) * d + j];
+      K1[static_cast<size_t>(i) * d1 + d] = f->c0[i];
+      K1[static_cast<size_t>(d) * d1 + i] = f->c0[i];
+    }
+    DenseLU lu = lu_factor(K1.data(), d1);
+    if (!lu.ok) { *err = "singular bordered coarse matrix"; return SMPM_EINVAL; }
+    std::vector<double> y(d1, 0.0);
+    y[d] = 1.0;
+    lu_solve_T(lu, y.data());
+    double nrm = 0;
+    int imax = 0;
+    for (int i = 0; i < d; ++i) {
+      nrm += y[i] * y[i];
+      if (std::fabs(y[i]) > std::fabs(y[imax])) imax = i;
+    }
+    nrm = std::sqrt(nrm) * (y[imax] >= 0 ? 1.0 : -1.0);
+    f->uC.resize(d);
+    for (int i = 0; i < d; ++i) f->uC[i] = y[i] / nrm;
+    std::vector<double> Kinv(static_cast<size_t>(d) * d);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int j = 0; j < d; ++j) {
+      std::vector<double> col(d1, 0.0);
+      col[j] = 1.0;
+      lu_solve(lu, col.data());
+      for (int i = 0; i < d; ++i) Kinv[static_cast<size_t>(i) * d + j] = col[i];
+    }
+    f->H.assign(static_cast<size_t>(d) * d, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < d; ++i) {
+      double s = 0;
+      for (int j = 0; j < d; ++j) s += Kinv[static_cast<size_t>(i) * d + j] * f->uC[j];
+      for (int j = 0; j < d; ++j) f->H[static_cast<size_t>(i) * d + j] = Kinv[static_cast<size_t>(i) * d + j] - s * f->uC[j];
+    }
+  }
+
+  // null vectors of S and L
+  int st = left_null_S(g, f, err);
+  if (st != SMPM_OK) return st;
+  f->uL.assign(g.r, 0.0);
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e) {
+    // (B^T u_S)_e = sum over interface faces G of e, t:
+    //   -tau_G (p_G e_q(G,t) - n_G.grad|_(G,t))^T u_S(nbr(e,G), opp G, t)
+    std::vector<double> bt(n * n, 0.0), U(n * n);
+    for (int G = 0; G < 4; ++G) {
+      int e2 = g.neighbour(static_cast<int>(e), G);
+      if (e2 < 0) continue;
+      const double tg = G < 2 ? f->tau_x : f->tau_y, pg = G < 2 ? f->p_x : f->p_y;
+      const double sx = 2.0 / g.hx, sy = 2.0 / g.hy;
+      for (int t = 0; t < n; ++t) {
+        double v = -tg * f->uS[e2 * M + opposite(G) * n + t];
+        int a, b;
+        g.face_node(G, t, &a, &b);
+        bt[b * n + a] += pg * v;
+        for (int q = 0; q < n; ++q) {  // minus the transposed normal-derivative row
+          switch (G) {
+            case FACE_W: bt[t * n + q] -= -sx * f->D[q] * v; break;
+            case FACE_E: bt[t * n + q] -= sx * f->D[(n - 1) * n + q] * v; break;
+            case FACE_S: bt[q * n + t] -= -sy * f->D[q] * v; break;
+            default: bt[q * n + t] -= sy * f->D[(n - 1) * n + q] * v; break;
+          }
+        }
+      }
+    }
+    elem_solve_T(n, c.fx(static_cast<int>(e)), c.fy(static_cast<int>(e)), bt.data(), U.data());
+    for (int q = 0; q < n * n; ++q) f->uL[e * n * n + q] = -U[q];
+  }
+  {
+    double nrm = 0;
+    size_t imax = 0;
+    for (size_t i = 0; i < f->uL.size(); ++i) {
+      nrm += f->uL[i] * f->uL[i];
+      if (std::fabs(f->uL[i]) > std::fabs(f->uL[imax])) imax = i;
+    }
+    nrm = std::sqrt(nrm) * (f->uL[imax] >= 0 ? 1.0 : -1.0);
+    for (auto& v : f->uL) v /= nrm;
+  }
+  // normalised GLL mass for the zero-mean step
+  f->what.assign(g.r, 0.0);
+  double tot = 0;
+  for (long long e = 0; e < g.nel; ++e)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        double w = f->w1d[a] * f->w1d[b] * g.hx * g.hy / 4.0;
+        f->what[e * n * n + b * n + a] = w;
+        tot += w;
+      }
+  for (auto& v : f->what) v /= tot;
+  return SMPM_OK;
+}
+
+}  // namespace smpm

@@ -1,0 +1,99 @@
+// Internal declarations shared by the host factor step and the CUDA solve.
+#pragma once
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/smpm.h"
+
+namespace smpm {
+
+enum { FACE_W = 0, FACE_E = 1, FACE_S = 2, FACE_N = 3 };
+constexpr int kMaxN = 32;         // GLL points per direction
+constexpr int kMaxRestart = 200;  // GMRES restart length
+
+inline int opposite(int F) { return F ^ 1; }
+
+// Geometry and indexing of one grid (Sec. 1.2).  Element e = iy*mx + ix;
+// slot (e, F, t) at e*M + F*n + t with M = 4n; interfaces numbered row by
+// row: in element row iy, the mx-1 vertical interfaces (ix | ix+1) at
+// iy*(2mx-1) + ix, then the mx horizontal ones (row iy | iy+1) at
+// iy*(2mx-1) + mx-1 + ix.
+struct Geometry {
+  int mx = 0, my = 0, n = 0, M = 0;
+  double Lx = 1, Ly = 1, hx = 1, hy = 1;
+  long long nel = 0, nn = 0, r = 0, kp = 0, d = 0, k = 0;
+
+  int neighbour(int e, int F) const {
+    int ix = e % mx, iy = e / mx;
+    switch (F) {
+      case FACE_W: return ix > 0 ? e - 1 : -1;
+      case FACE_E: return ix < mx - 1 ? e + 1 : -1;
+      case FACE_S: return iy > 0 ? e - mx : -1;
+      default: return iy < my - 1 ? e + mx : -1;
+    }
+  }
+  int iface(int e, int F) const {
+    int ix = e % mx, iy = e / mx, row = 2 * mx - 1;
+    switch (F) {
+      case FACE_W: return ix > 0 ? iy * row + ix - 1 : -1;
+      case FACE_E: return ix < mx - 1 ? iy * row + ix : -1;
+      case FACE_S: return iy > 0 ? (iy - 1) * row + mx - 1 + ix : -1;
+      default: return iy < my - 1 ? iy * row + mx - 1 + ix : -1;
+    }
+  }
+  int mask(int e) const {
+    int m = 0;
+    for (int F = 0; F < 4; ++F)
+      if (neighbour(e, F) >= 0) m |= 1 << F;
+    return m;
+  }
+  bool black(int e) const { return ((e % mx) + (e / mx)) % 2 == 0; }
+  // (a, b) of face node t of face F
+  void face_node(int F, int t, int* a, int* b) const {
+    switch (F) {
+      case FACE_W: *a = 0; *b = t; break;
+      case FACE_E: *a = n - 1; *b = t; break;
+      case FACE_S: *a = t; *b = 0; break;
+      default: *a = t; *b = n - 1; break;
+    }
+  }
+};
+
+// Everything the factor step produces, in host memory (FP64).
+struct Factors {
+  double tau_x = 0, tau_y = 0, p_x = 0, p_y = 0;  // per face direction
+  std::vector<double> x1d, w1d, D;                  // GLL nodes, weights, D (n*n)
+  // fast diagonalisation of the 1-D operators K_x (4 classes by the W/E face
+  // types) and K_y (4 classes by S/N): per class V (n*n), Vinv (n*n), lam (n)
+  std::vector<double> fdx, fdy;
+  std::vector<double> T;     // nel * M*M : T_e[(F,t),(G,s)] row-major
+  std::vector<double> Rs;    // nel * M*4 : row sums of T_e per input face
+  std::vector<int> black, white;
+  std::vector<double> G;     // nblack * M*M : (I - X Y)^-1
+  std::vector<double> X;     // nblack * 4*n*n : X_F blocks
+  std::vector<double> C;     // d*d coarse matrix
+  std::vector<double> H;     // d*d regularised coarse inverse
+  std::vector<double> c0;    // d : right null vector of C
+  std::vector<double> uL, uS, uC, what;  // r, kp, d, r
+  std::vector<double> B1;    // kp : B 1 (right null vector of S)
+  int null_iterations = 0;   // GMRES steps of the u_S bordered solve
+  double null_relres = 0;
+};
+
+// Host factor step (smpm_factor_host.cpp).
+int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err);
+// Fast-diagonalisation class of element e in x and y.
+inline int xclass(const Geometry& g, int e) {
+  int ix = e % g.mx;
+  return (ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0);
+}
+inline int yclass(const Geometry& g, int e) {
+  int iy = e / g.mx;
+  return (iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0);
+}
+// GLL nodes and weights, differentiation matrix (host).
+void gll(int n, std::vector<double>* x, std::vector<double>* w);
+void diff_matrix(const std::vector<double>& x, std::vector<double>* D);
+
+}  // namespace smpm

@@ -1,0 +1,1210 @@
+// CUDA solve path and C ABI of the deflated Schur-complement method
+// (Joshi & Diamessis, Algorithms 1-3).  See include/smpm.h for the contract.
+//
+// One GMRES step of Algorithm 3 (x_1 := GMRES(P S M^-1, P b_S)) runs as:
+//   k_black   per black element: t = M^-1 v on its block (Fig. 2), in the
+//             reduced form a = G (p - X q), b = q - T_e a;
+//   k_white   per white element: y = S t; because M_b = S[block, block], the
+//             rows of S on white-owned slots reduce to y = v, so only the
+//             white elements' T_e products remain (each T_e is read once per
+//             step across the two kernels); also c = Z^T y per interface;
+//   k_coarse  c_hat = C^+ c with the precomputed regularised inverse;
+//   k_defl    w = y - (S Z) c_hat (Eq. projection1) fused with the first
+//             classical Gram-Schmidt pass h = V^T w;
+//   k_cgs2    w' = w - V h, h2 = V^T w' (re-orthogonalisation);
+//   k_cgs3    v_{j+1} = w' - V h2, ||v_{j+1}||, Givens update (FP64) and the
+//             convergence test on the rotated residual;
+//   k_scale   v_{j+1} /= ||v_{j+1}||.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "smpm_internal.h"
+#include "smpm_kernels.cuh"
+
+using namespace smpm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kSlotsPerBlock = 256;   // slots per CTA in the vector kernels
+constexpr int kElemThreads = 256;     // threads per element CTA
+
+struct GState {
+  double tolabs, beta0, beta, wnorm0sq, resid;
+  int j, converged, breakdown, nan;
+  double g[kMaxRestart + 1];
+  double cs[kMaxRestart], sn[kMaxRestart];
+  double R[(kMaxRestart + 1) * kMaxRestart];  // column j at R[j*(kMaxRestart+1)]
+  double h1[kMaxRestart + 2], h2[kMaxRestart + 2];
+  double y[kMaxRestart];
+  double scal[8];
+};
+
+// ------------------------------------------------------------ reductions
+__device__ bool last_block_done(unsigned* cnt) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(cnt, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// out[l] = sum_b part[l*nblk + b] for l < nout, in a fixed order.
+__device__ void finalize_partials(const double* part, int nblk, int nout, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = warp; l < nout; l += nw) {
+    double acc = 0;
+    for (int b = lane; b < nblk; b += 32) acc += __ldcg(part + (size_t)l * nblk + b);
+    acc = warp_sum(acc);
+    if (lane == 0) out[l] = acc;
+  }
+}
+
+// part[l*nblk + blockIdx] = sum_{i<CH} V[l][base+i] * wsh[i] for l < nvec, and
+// (with_norm) part[nvec*nblk + blockIdx] = sum wsh[i]^2.
+template <typename S>
+__device__ void block_multidot(const S* __restrict__ V, long long kp, int nvec, long long base, const double* wsh,
+                               bool with_norm, double* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int CH = blockDim.x;
+  const int nout = nvec + (with_norm ? 1 : 0);
+  for (int l = warp; l < nout; l += nw) {
+    double acc = 0;
+    if (l < nvec) {
+      const S* v = V + (size_t)l * kp + base;
+      for (int i = lane; i < CH && base + i < kp; i += 32) acc += (double)__ldg(v + i) * wsh[i];
+    } else {
+      for (int i = lane; i < CH; i += 32) acc += wsh[i] * wsh[i];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[(size_t)l * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// *out = x . y over n entries (FP64), via partials and the last block.
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, long long n, double* part,
+                      unsigned* cnt, double* out) {
+  double acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc += x[i] * y[i];
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+  if (last_block_done(cnt)) {
+    finalize_partials(part, gridDim.x, 1, out);
+    if (threadIdx.x == 0) *cnt = 0;
+  }
+}
+
+// u -= *c (removes the GLL-weighted mean, the constant Sec. 1.4 leaves open)
+__global__ void k_sub_const(double* u, const double* c, long long n) {
+  double m = *c;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    u[i] -= m;
+}
+
+// y -= (*alpha) * x
+__global__ void k_axpy_dev(const double* __restrict__ x, const double* alpha, double* y, long long n) {
+  double a = *alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] -= a * x[i];
+}
+
+// ------------------------------------------------------- element solves
+// U = A_e^-1 B by fast diagonalisation (the Kronecker-sum structure of A_e):
+// U = Vy ((Vy^-1 B Vx^-T) ./ (lx_i + ly_j)) Vx^T.  B, U, t1: n*n in shared.
+__device__ void elem_solve_dev(int n, const double* __restrict__ fx, const double* __restrict__ fy, const double* B,
+                               double* U, double* t1) {
+  const double *Vx = fx, *Vxi = fx + n * n, *lx = fx + 2 * n * n;
+  const double *Vy = fy, *Vyi = fy + n * n, *ly = fy + 2 * n * n;
+  const int nn = n * n;
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) {  // t1 = Vyi B
+    int j = q / n, a = q % n;
+    double s = 0;
+    for (int b = 0; b < n; ++b) s += __ldg(Vyi + j * n + b) * B[b * n + a];
+    t1[q] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) {  // U = t1 Vxi^T ./ (lx + ly)
+    int j = q / n, i = q % n;
+    double s = 0;
+    for (int a = 0; a < n; ++a) s += t1[j * n + a] * __ldg(Vxi + i * n + a);
+    U[q] = s / (__ldg(lx + i) + __ldg(ly + j));
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) {  // t1 = U Vx^T
+    int j = q / n, a = q % n;
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += U[j * n + i] * __ldg(Vx + a * n + i);
+    t1[q] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) {  // U = Vy t1
+    int b = q / n, a = q % n;
+    double s = 0;
+    for (int j = 0; j < n; ++j) s += __ldg(Vy + b * n + j) * t1[j * n + a];
+    U[q] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void face_node(int n, int F, int t, int* a, int* b) {
+  switch (F) {
+    case 0: *a = 0; *b = t; break;
+    case 1: *a = n - 1; *b = t; break;
+    case 2: *a = t; *b = 0; break;
+    default: *a = t; *b = n - 1; break;
+  }
+}
+
+// n_F . grad U at face node t (U in shared memory, D in global).
+__device__ double normal_deriv(const DevGeo& g, const double* __restrict__ D, const double* U, int F, int t) {
+  const int n = g.n;
+  double acc = 0;
+  switch (F) {
+    case 0: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[t * n + c]; return -g.sx * acc;
+    case 1: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[t * n + c]; return g.sx * acc;
+    case 2: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[c * n + t]; return -g.sy * acc;
+    default: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[c * n + t]; return g.sy * acc;
+  }
+}
+
+__device__ __forceinline__ const double* fd_x(const DevGeo& g, const double* fdx, int e) {
+  int ix = e % g.mx;
+  int cls = (ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0);
+  return fdx + (size_t)cls * (2 * g.n * g.n + g.n);
+}
+__device__ __forceinline__ const double* fd_y(const DevGeo& g, const double* fdy, int e) {
+  int iy = e / g.mx;
+  int cls = (iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0);
+  return fdy + (size_t)cls * (2 * g.n * g.n + g.n);
+}
+
+// b = f + tau_F g on physical-boundary face nodes (Eq. smpm_poisson).
+__global__ void k_rhs(DevGeo g, const double* __restrict__ f, const double* __restrict__ gn, double* b) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.r) return;
+  const int n = g.n, nn = n * n;
+  int e = (int)(q / nn), loc = (int)(q % nn), a = loc % n, bb = loc / n;
+  double v = f[q];
+  if (gn) {
+    const long long s0 = (long long)e * g.M;
+    if (a == 0 && dev_neighbour(g, e, 0) < 0) v += g.tau_x * gn[s0 + 0 * n + bb];
+    if (a == n - 1 && dev_neighbour(g, e, 1) < 0) v += g.tau_x * gn[s0 + 1 * n + bb];
+    if (bb == 0 && dev_neighbour(g, e, 2) < 0) v += g.tau_y * gn[s0 + 2 * n + a];
+    if (bb == n - 1 && dev_neighbour(g, e, 3) < 0) v += g.tau_y * gn[s0 + 3 * n + a];
+  }
+  b[q] = v;
+}
+
+// b_S = B A^-1 b (Algorithm 1 step 2): one CTA per element; the flux of
+// w = A_e^-1 b_e into the slot (nbr, opp F, t) is -tau_F (p_F w - n_F.grad w).
+// Slots on boundary faces are not written (the caller zeroes b_S).
+__global__ void k_schur_rhs(DevGeo g, const double* __restrict__ fdx, const double* __restrict__ fdy,
+                            const double* __restrict__ D, const double* __restrict__ b, double* bS) {
+  extern __shared__ double sh[];
+  const int n = g.n, nn = n * n, e = blockIdx.x;
+  double *B = sh, *U = sh + nn, *t1 = sh + 2 * nn;
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) B[q] = b[(size_t)e * nn + q];
+  __syncthreads();
+  elem_solve_dev(n, fd_x(g, fdx, e), fd_y(g, fdy, e), B, U, t1);
+  for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) {
+    int F = i / n, t = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    if (e2 < 0) continue;
+    int a, bb;
+    face_node(n, F, t, &a, &bb);
+    double tau = F < 2 ? g.tau_x : g.tau_y, p = F < 2 ? g.p_x : g.p_y;
+    double val = p * U[bb * n + a] - normal_deriv(g, D, U, F, t);
+    bS[(size_t)e2 * g.M + (F ^ 1) * n + t] = -tau * val;
+  }
+}
+
+// u = A^-1 (b - E x): one CTA per element.
+__global__ void k_recover(DevGeo g, const double* __restrict__ fdx, const double* __restrict__ fdy,
+                          const double* __restrict__ b, const double* __restrict__ x, double* u) {
+  extern __shared__ double sh[];
+  const int n = g.n, nn = n * n, e = blockIdx.x;
+  double *B = sh, *U = sh + nn, *t1 = sh + 2 * nn;
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) B[q] = b[(size_t)e * nn + q];
+  __syncthreads();
+  for (int F = 0; F < 4; ++F) {  // faces one after another: corner nodes get both slots
+    if (dev_neighbour(g, e, F) >= 0)
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int a, bb;
+        face_node(n, F, t, &a, &bb);
+        B[bb * n + a] -= x[(size_t)e * g.M + F * n + t];
+      }
+    __syncthreads();
+  }
+  elem_solve_dev(n, fd_x(g, fdx, e), fd_y(g, fdy, e), B, U, t1);
+  for (int q = threadIdx.x; q < nn; q += blockDim.x) u[(size_t)e * nn + q] = U[q];
+}
+
+// ------------------------------------------------------- slot operators
+// y = S v = v + scatter_e(T_e v_e) (Eq. schur_complement_system), push form:
+// element e writes the neighbours' slots facing it (each slot has exactly one
+// writer) and its own boundary-face slots.
+template <typename S>
+__global__ void k_schur(DevGeo g, const S* __restrict__ T, const S* __restrict__ v, S* y) {
+  extern __shared__ unsigned char shraw[];
+  S* ve = reinterpret_cast<S*>(shraw);
+  S* z = ve + g.M;
+  const int e = blockIdx.x, M = g.M, n = g.n;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) ve[i] = v[(size_t)e * M + i];
+  __syncthreads();
+  gemv_rows<S, S>(T + (size_t)e * M * M, ve, z, M);
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, t = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    if (e2 >= 0) {
+      size_t s = (size_t)e2 * M + (F ^ 1) * n + t;
+      y[s] = v[s] + z[i];
+    } else {
+      y[(size_t)e * M + i] = ve[i];
+    }
+  }
+}
+
+// Black step: t = M^-1 v on the block of black element e (own slots p,
+// facing slots q): a = G (p - X q), b = q - T_e a.  Writes t on the whole
+// block (every slot is in exactly one block).
+template <typename S>
+__global__ void k_black(DevGeo g, const int* __restrict__ black, const S* __restrict__ T, const S* __restrict__ G,
+                        const S* __restrict__ X, const S* __restrict__ v, S* t) {
+  extern __shared__ unsigned char shraw[];
+  const int M = g.M, n = g.n, ib = blockIdx.x, e = black[ib];
+  S* p = reinterpret_cast<S*>(shraw);
+  S* q = p + M;
+  S* r1 = q + M;
+  S* a = r1 + M;
+  S* z = a + M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    p[i] = v[(size_t)e * M + i];
+    q[i] = e2 >= 0 ? v[(size_t)e2 * M + (F ^ 1) * n + tt] : S(0);
+  }
+  __syncthreads();
+  const S* Xb = X + (size_t)ib * 4 * n * n;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    const S* xr = Xb + (size_t)(F * n + tt) * n;
+    S s = p[i];
+    for (int s2 = 0; s2 < n; ++s2) s -= __ldg(xr + s2) * q[F * n + s2];
+    r1[i] = s;
+  }
+  __syncthreads();
+  gemv_rows<S, S>(G + (size_t)ib * M * M, r1, a, M);
+  __syncthreads();
+  gemv_rows<S, S>(T + (size_t)e * M * M, a, z, M);
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    t[(size_t)e * M + i] = a[i];
+    if (e2 >= 0) t[(size_t)e2 * M + (F ^ 1) * n + tt] = q[i] - z[i];
+  }
+}
+
+// White step: y = S t given t = M^-1 v: on white-owned slots y = v; on the
+// black slots facing white element e, y = t + (T_e t_e).  Also c = Z^T y for
+// the interfaces of e (every interface has exactly one white side).
+template <typename S>
+__global__ void k_white(DevGeo g, const int* __restrict__ white, const S* __restrict__ T, const S* __restrict__ v,
+                        const S* __restrict__ t, S* y, double* c) {
+  extern __shared__ unsigned char shraw[];
+  const int M = g.M, n = g.n, e = white[blockIdx.x];
+  S* tb = reinterpret_cast<S*>(shraw);
+  S* z = tb + M;
+  double* cs = reinterpret_cast<double*>(z + M + (M & 1));
+  for (int i = threadIdx.x; i < M; i += blockDim.x) tb[i] = t[(size_t)e * M + i];
+  __syncthreads();
+  gemv_rows<S, S>(T + (size_t)e * M * M, tb, z, M);
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    S vo = v[(size_t)e * M + i];
+    y[(size_t)e * M + i] = vo;
+    double ci = 0;
+    if (e2 >= 0) {
+      size_t s = (size_t)e2 * M + (F ^ 1) * n + tt;
+      S ys = t[s] + z[i];
+      y[s] = ys;
+      ci = (double)vo + (double)ys;
+    }
+    cs[i] = ci;
+  }
+  __syncthreads();
+  if (c && threadIdx.x < 4) {
+    int F = threadIdx.x;
+    int j = dev_iface(g, e, F);
+    if (j >= 0) {
+      double s = 0;
+      for (int tt = 0; tt < n; ++tt) s += cs[F * n + tt];
+      c[j] = s;
+    }
+  }
+}
+
+// c = Z^T v: one thread per interface, summing its 2n slots.
+template <typename S>
+__global__ void k_zt(DevGeo g, const S* __restrict__ v, double* c) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= g.d) return;
+  const int row = 2 * g.mx - 1, n = g.n, M = g.M;
+  int iy = (int)(j / row), rem = (int)(j % row);
+  int e1, F1;
+  if (rem < g.mx - 1) { e1 = iy * g.mx + rem; F1 = 1; }
+  else { e1 = iy * g.mx + rem - (g.mx - 1); F1 = 3; }
+  int e2 = dev_neighbour(g, e1, F1);
+  double s = 0;
+  for (int t = 0; t < n; ++t)
+    s += (double)v[(size_t)e1 * M + F1 * n + t] + (double)v[(size_t)e2 * M + (F1 ^ 1) * n + t];
+  c[j] = s;
+}
+
+// out = H c (FP64, d x d, warp per row).
+__global__ void k_coarse(const double* __restrict__ H, const double* __restrict__ c, double* out, int d) {
+  const int lane = threadIdx.x & 31;
+  const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (row >= d) return;
+  const double* h = H + row * (long long)d;
+  double acc = 0;
+  for (int j = lane; j < d; j += 32) acc += __ldg(h + j) * __ldg(c + j);
+  acc = warp_sum(acc);
+  if (lane == 0) out[row] = acc;
+}
+
+// w = y - (S Z) chat on one slot (pull form); chat == nullptr gives w = y.
+template <typename S>
+__device__ __forceinline__ double deflate_slot(const DevGeo& g, const S* __restrict__ y, const double* __restrict__ chat,
+                                               const S* __restrict__ Rs, long long s) {
+  const int M = g.M, n = g.n;
+  int e = (int)(s / M), i = (int)(s % M), F = i / n, t = i % n;
+  int e2 = dev_neighbour(g, e, F);
+  if (e2 < 0) return 0.0;
+  double ys = (double)y[s];
+  if (!chat) return ys;
+  double acc = chat[dev_iface(g, e, F)];
+  const S* R = Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
+#pragma unroll
+  for (int G = 0; G < 4; ++G) {
+    int jj = dev_iface(g, e2, G);
+    if (jj >= 0) acc += (double)R[G] * chat[jj];
+  }
+  return ys - acc;
+}
+
+// Deflation (Eq. projection1) fused with the first Gram-Schmidt pass:
+// w = y - S Z chat; h1 = V[0..nvec)^T w; also ||w||^2.
+template <typename S>
+__global__ void k_defl_dots(DevGeo g, const S* __restrict__ y, const double* __restrict__ chat,
+                            const S* __restrict__ Rs, const S* __restrict__ V, int nvec, S* w, double* part,
+                            unsigned* cnt, GState* gs) {
+  __shared__ double wsh[kSlotsPerBlock];
+  const long long base = (long long)blockIdx.x * blockDim.x, s = base + threadIdx.x;
+  double ws = 0;
+  if (s < g.kp) {
+    S wv = (S)deflate_slot(g, y, chat, Rs, s);
+    w[s] = wv;
+    ws = (double)wv;
+  }
+  wsh[threadIdx.x] = ws;
+  __syncthreads();
+  if (nvec < 0) return;  // deflation only
+  block_multidot(V, g.kp, nvec, base, wsh, true, part);
+  if (last_block_done(cnt)) {
+    finalize_partials(part, gridDim.x, nvec + 1, gs->h1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      gs->wnorm0sq = gs->h1[nvec];
+      *cnt = 0;
+    }
+  }
+}
+
+// Second Gram-Schmidt pass: w2 = w - V h1, h2 = V^T w2.
+template <typename S>
+__global__ void k_cgs2(long long kp, const S* __restrict__ V, int nvec, const S* __restrict__ w, S* w2, double* part,
+                       unsigned* cnt, GState* gs) {
+  __shared__ double wsh[kSlotsPerBlock];
+  __shared__ double hs[kMaxRestart + 2];
+  for (int l = threadIdx.x; l < nvec; l += blockDim.x) hs[l] = gs->h1[l];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * blockDim.x, s = base + threadIdx.x;
+  double ws = 0;
+  if (s < kp) {
+    double acc = (double)w[s];
+    for (int l = 0; l < nvec; ++l) acc -= hs[l] * (double)__ldg(V + (size_t)l * kp + s);
+    S wv = (S)acc;
+    w2[s] = wv;
+    ws = (double)wv;
+  }
+  wsh[threadIdx.x] = ws;
+  __syncthreads();
+  block_multidot(V, kp, nvec, base, wsh, false, part);
+  if (last_block_done(cnt)) {
+    finalize_partials(part, gridDim.x, nvec, gs->h2);
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = 0;
+  }
+}
+
+// Third pass: v_{j+1} = w2 - V h2 (stored unnormalised in V[nvec]), its norm,
+// and the FP64 Givens update of Hessenberg column j = nvec - 1.
+template <typename S>
+__global__ void k_cgs3(long long kp, S* V, int nvec, const S* __restrict__ w2, double* part, unsigned* cnt,
+                       GState* gs) {
+  __shared__ double hs[kMaxRestart + 2];
+  __shared__ double red[32];
+  for (int l = threadIdx.x; l < nvec; l += blockDim.x) hs[l] = gs->h2[l];
+  __syncthreads();
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc2 = 0;
+  if (s < kp) {
+    double acc = (double)w2[s];
+    for (int l = 0; l < nvec; ++l) acc -= hs[l] * (double)V[(size_t)l * kp + s];
+    S wv = (S)acc;
+    V[(size_t)nvec * kp + s] = wv;
+    acc2 = (double)wv * (double)wv;
+  }
+  acc2 = warp_sum(acc2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+  if (last_block_done(cnt)) {
+    __shared__ double bsq;
+    finalize_partials(part, gridDim.x, 1, &bsq);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      const int j = nvec - 1, m1 = kMaxRestart + 1;
+      double beta = sqrt(bsq);
+      double* col = gs->R + (size_t)j * m1;
+      for (int l = 0; l <= j; ++l) col[l] = gs->h1[l] + gs->h2[l];
+      double hsub = beta;
+      for (int i = 0; i < j; ++i) {
+        double a = col[i], b = col[i + 1];
+        col[i] = gs->cs[i] * a + gs->sn[i] * b;
+        col[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
+      }
+      double den = hypot(col[j], hsub);
+      double c = den > 0 ? col[j] / den : 1.0, sn = den > 0 ? hsub / den : 0.0;
+      gs->cs[j] = c;
+      gs->sn[j] = sn;
+      col[j] = den;
+      gs->g[j + 1] = -sn * gs->g[j];
+      gs->g[j] = c * gs->g[j];
+      gs->resid = fabs(gs->g[j + 1]);
+      gs->beta = beta;
+      gs->j = j + 1;
+      gs->converged = gs->resid <= gs->tolabs;
+      gs->breakdown = beta <= 1e-14 * sqrt(gs->wnorm0sq);
+      gs->nan = !(isfinite(gs->resid) && isfinite(beta));
+    }
+  }
+}
+
+template <typename S>
+__global__ void k_scale_vec(long long kp, S* v, const GState* gs) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double beta = gs->beta;
+  if (s < kp && beta > 0) v[s] = (S)((double)v[s] / beta);
+}
+
+// ||x||: initialises a GMRES cycle (g = beta e_1, j = 0); with set_tol the
+// absolute target tol * beta is fixed (first cycle only).
+template <typename S>
+__global__ void k_cycle_init(long long kp, S* v0, double* part, unsigned* cnt, GState* gs, double tol, int set_tol) {
+  __shared__ double red[32];
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double acc = 0;
+  if (s < kp) acc = (double)v0[s] * (double)v0[s];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+  if (last_block_done(cnt)) {
+    __shared__ double bsq;
+    finalize_partials(part, gridDim.x, 1, &bsq);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *cnt = 0;
+      double beta = sqrt(bsq);
+      if (set_tol) {
+        gs->beta0 = beta;
+        gs->tolabs = tol * beta;
+      }
+      gs->beta = beta;
+      gs->g[0] = beta;
+      gs->j = 0;
+      gs->resid = beta;
+      gs->converged = beta <= gs->tolabs;
+      gs->breakdown = 0;
+      gs->nan = !isfinite(beta);
+    }
+  }
+}
+
+// Back substitution R y = g for the j columns of the current cycle.
+__global__ void k_trisolve(GState* gs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = gs->j, m1 = kMaxRestart + 1;
+  for (int i = j - 1; i >= 0; --i) {
+    double s = gs->g[i];
+    for (int k = i + 1; k < j; ++k) s -= gs->R[(size_t)k * m1 + i] * gs->y[k];
+    gs->y[i] = s / gs->R[(size_t)i * m1 + i];
+  }
+}
+
+// x += V[0..j) y
+template <typename S>
+__global__ void k_update(long long kp, const S* __restrict__ V, const GState* gs, S* x) {
+  __shared__ double ys[kMaxRestart];
+  const int j = gs->j;
+  for (int l = threadIdx.x; l < j; l += blockDim.x) ys[l] = gs->y[l];
+  __syncthreads();
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= kp) return;
+  double acc = (double)x[s];
+  for (int l = 0; l < j; ++l) acc += ys[l] * (double)V[(size_t)l * kp + s];
+  x[s] = (S)acc;
+}
+
+// out = a - b
+template <typename S>
+__global__ void k_sub(long long n, const S* __restrict__ a, const S* __restrict__ b, S* out) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s < n) out[s] = a[s] - b[s];
+}
+
+// x = t - Z (chat - chat_b) on interface slots (Eq. deflated_schur assembly).
+__global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double* __restrict__ chat,
+                           const double* __restrict__ chat_b, double* x) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.kp) return;
+  const int M = g.M, n = g.n;
+  int e = (int)(s / M), i = (int)(s % M), F = i / n;
+  int j = dev_iface(g, e, F);
+  if (j < 0) { x[s] = 0.0; return; }
+  double cb = chat_b ? chat_b[j] : 0.0;
+  x[s] = t[s] - (chat ? chat[j] : 0.0) + cb;
+}
+
+// ------------------------------------------------------------- host side
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ===================================================================== handle
+struct smpm_handle_s {
+  Geometry g;
+  smpm_opts opts{};
+  bool factored = false;
+  Factors f;
+  DevGeo dg{};
+  // device factors
+  double *dT = nullptr, *dRs = nullptr, *dG = nullptr, *dX = nullptr, *dH = nullptr;
+  double *dfdx = nullptr, *dfdy = nullptr, *dD = nullptr;
+  double *duL = nullptr, *duS = nullptr, *duC = nullptr, *dwhat = nullptr;
+  int *dblack = nullptr, *dwhite = nullptr;
+  // workspace
+  double *wb = nullptr, *wbS = nullptr, *wV = nullptr, *wt = nullptr, *wy = nullptr, *ww = nullptr;
+  double *ww2 = nullptr, *wx = nullptr, *wrg = nullptr, *wtmp = nullptr;
+  double *wc = nullptr, *wchat = nullptr, *wcb = nullptr, *wchatb = nullptr;
+  double *wpart = nullptr;
+  unsigned* wcnt = nullptr;
+  GState* wgs = nullptr;
+  // staging for the host-pointer entry point
+  double *sf = nullptr, *sg = nullptr, *su = nullptr;
+  size_t sf_n = 0;
+  std::vector<void*> allocs;
+  long long launches = 0;  // kernels launched by this handle (for reports)
+};
+
+namespace {
+
+smpm_status fail(smpm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? SMPM_ENOMEM : SMPM_ECUDA,                     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+#define CHECK_LAUNCH()    \
+  do {                    \
+    ++h->launches;        \
+    CU(cudaGetLastError()); \
+  } while (0)
+
+template <typename P>
+smpm_status dalloc(smpm_handle h, P** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+  if (e != cudaSuccess) return fail(SMPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return SMPM_OK;
+}
+
+template <typename P>
+smpm_status upload(smpm_handle h, P** p, const std::vector<P>& src, cudaStream_t st) {
+  smpm_status s = dalloc(h, p, src.size() ? src.size() : 1);
+  if (s != SMPM_OK) return s;
+  if (!src.empty()) CU(cudaMemcpyAsync(*p, src.data(), src.size() * sizeof(P), cudaMemcpyHostToDevice, st));
+  return SMPM_OK;
+}
+
+void free_all(smpm_handle h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+size_t elem_smem(int n) { return 3 * (size_t)n * n * sizeof(double); }
+
+// ---- operator launches (FP64) ----------------------------------------
+smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  k_schur<double><<<(unsigned)g.nel, kElemThreads, 2 * g.M * sizeof(double), st>>>(g, h->dT, v, y);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+// t = M^-1 v (t fully written), then optionally y = S t and c = Z^T y.
+smpm_status launch_precond(smpm_handle h, const double* v, double* t, double* y, double* c, cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  const unsigned nb = (unsigned)h->f.black.size(), nw = (unsigned)h->f.white.size();
+  if (nw > 0) CU(cudaMemsetAsync(t, 0, g.kp * sizeof(double), st));  // white boundary slots
+  k_black<double><<<nb, kElemThreads, 5 * g.M * sizeof(double), st>>>(g, h->dblack, h->dT, h->dG, h->dX, v, t);
+  CHECK_LAUNCH();
+  if (y) {
+    CU(cudaMemsetAsync(y, 0, g.kp * sizeof(double), st));  // black boundary slots
+    if (nw > 0) {
+      k_white<double><<<nw, kElemThreads, (3 * g.M + 2) * sizeof(double), st>>>(g, h->dwhite, h->dT, v, t, y, c);
+      CHECK_LAUNCH();
+    }
+  }
+  return SMPM_OK;
+}
+
+smpm_status launch_zt(smpm_handle h, const double* v, double* c, cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  k_zt<double><<<blocks_for(g.d, 128), 128, 0, st>>>(g, v, c);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status launch_coarse(smpm_handle h, const double* c, double* chat, cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  k_coarse<<<blocks_for(g.d * 32, 256), 256, 0, st>>>(h->dH, c, chat, (int)g.d);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+// w = y - S Z chat (chat may be null: w = y); nvec >= 0 also runs the first
+// Gram-Schmidt pass against V[0..nvec).
+smpm_status launch_defl(smpm_handle h, const double* y, const double* chat, int nvec, double* w, cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  k_defl_dots<double><<<blocks_for(g.kp, kSlotsPerBlock), kSlotsPerBlock, 0, st>>>(
+      g, y, chat, h->dRs, h->wV, nvec, w, h->wpart, h->wcnt, h->wgs);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status launch_dot(smpm_handle h, const double* x, const double* y, long long n, double* out, cudaStream_t st) {
+  unsigned nb = std::min<unsigned>(blocks_for(n, 256), 1024u);
+  k_dot<<<nb, 256, 0, st>>>(x, y, n, h->wpart, h->wcnt, out);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status launch_axpy(smpm_handle h, const double* x, const double* alpha, double* y, long long n, cudaStream_t st) {
+  unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4096u);
+  k_axpy_dev<<<nb, 256, 0, st>>>(x, alpha, y, n);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+// y = op(v) for the GMRES of the chosen algorithm, followed by the first
+// Gram-Schmidt pass against V[0..nvec) (nvec < 0: no dots).  Output in w.
+smpm_status apply_gmres_op(smpm_handle h, const double* v, int nvec, double* w, cudaStream_t st) {
+  smpm_status s;
+  switch (h->opts.precond) {
+    case 0:
+      if ((s = launch_schur(h, v, h->wy, st))) return s;
+      return launch_defl(h, h->wy, nullptr, nvec, w, st);
+    case 1:
+      if ((s = launch_precond(h, v, h->wt, h->wy, nullptr, st))) return s;
+      return launch_defl(h, h->wy, nullptr, nvec, w, st);
+    default:
+      if ((s = launch_precond(h, v, h->wt, h->wy, h->wc, st))) return s;
+      if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
+      return launch_defl(h, h->wy, h->wchat, nvec, w, st);
+  }
+}
+
+smpm_status read_state(smpm_handle h, GState* hs, cudaStream_t st) {
+  CU(cudaMemcpyAsync(hs, h->wgs, offsetof(GState, g), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return SMPM_OK;
+}
+
+// One right-hand side, FP64, Algorithms 1-3.
+smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* u, double tol, smpm_report* rep,
+                      cudaStream_t st) {
+  const DevGeo& g = h->dg;
+  const long long kp = g.kp;
+  const int m = h->opts.restart;
+  const unsigned nbs = blocks_for(kp, kSlotsPerBlock);
+  smpm_status s;
+  smpm_report R{};
+  const long long launches0 = h->launches;
+  double* scal = reinterpret_cast<double*>(reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal));
+
+  // Algorithm steps 1-3: b = f + tau g; b -= u_L (u_L^T b); b_S = B A^-1 b; b_S -= u_S (u_S^T b_S)
+  k_rhs<<<blocks_for(g.r, 256), 256, 0, st>>>(g, f, gn, h->wb);
+  CHECK_LAUNCH();
+  if ((s = launch_dot(h, h->duL, h->wb, g.r, scal + 0, st))) return s;
+  if ((s = launch_axpy(h, h->duL, scal + 0, h->wb, g.r, st))) return s;
+  CU(cudaMemsetAsync(h->wbS, 0, kp * sizeof(double), st));
+  k_schur_rhs<<<(unsigned)g.nel, kElemThreads, elem_smem(g.n), st>>>(g, h->dfdx, h->dfdy, h->dD, h->wb, h->wbS);
+  CHECK_LAUNCH();
+  if ((s = launch_dot(h, h->duS, h->wbS, kp, scal + 1, st))) return s;
+  if ((s = launch_axpy(h, h->duS, scal + 1, h->wbS, kp, st))) return s;
+
+  // GMRES right-hand side: P b_S (Algorithm 3) or b_S
+  const bool defl = h->opts.precond == 2;
+  if (defl) {
+    if ((s = launch_zt(h, h->wbS, h->wcb, st))) return s;
+    if ((s = launch_coarse(h, h->wcb, h->wchatb, st))) return s;
+    if ((s = launch_defl(h, h->wbS, h->wchatb, -1, h->wrg, st))) return s;
+  } else {
+    CU(cudaMemcpyAsync(h->wrg, h->wbS, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  CU(cudaMemsetAsync(h->wx, 0, kp * sizeof(double), st));
+  CU(cudaMemcpyAsync(h->wV, h->wrg, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  k_cycle_init<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wpart, h->wcnt, h->wgs, tol, 1);
+  CHECK_LAUNCH();
+  GState hs;
+  if ((s = read_state(h, &hs, st))) return s;
+  int total = 0;
+  bool conv = hs.converged || hs.beta0 == 0.0;
+  bool stop = conv;
+  if (hs.nan) return fail(SMPM_ENAN, "non-finite right-hand side");
+  while (!stop) {
+    k_scale_vec<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wgs);
+    CHECK_LAUNCH();
+    int j = 0;
+    for (; j < m && total < h->opts.maxit; ++j) {
+      double* vj = h->wV + (size_t)j * kp;
+      if ((s = apply_gmres_op(h, vj, j + 1, h->ww, st))) return s;
+      k_cgs2<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, j + 1, h->ww, h->ww2, h->wpart, h->wcnt, h->wgs);
+      CHECK_LAUNCH();
+      k_cgs3<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, j + 1, h->ww2, h->wpart, h->wcnt, h->wgs);
+      CHECK_LAUNCH();
+      ++total;
+      if ((s = read_state(h, &hs, st))) return s;
+      if (hs.nan) return fail(SMPM_ENAN, "non-finite value in the Arnoldi process");
+      if (hs.converged || hs.breakdown) { ++j; break; }
+      k_scale_vec<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV + (size_t)(j + 1) * kp, h->wgs);
+      CHECK_LAUNCH();
+    }
+    k_trisolve<<<1, 32, 0, st>>>(h->wgs);
+    CHECK_LAUNCH();
+    k_update<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wgs, h->wx);
+    CHECK_LAUNCH();
+    conv = hs.converged;
+    if (conv || hs.breakdown || total >= h->opts.maxit) break;
+    // restart: r = rhs - op(x)
+    ++R.restarts;
+    if ((s = apply_gmres_op(h, h->wx, -1, h->ww, st))) return s;
+    k_sub<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wrg, h->ww, h->wV);
+    CHECK_LAUNCH();
+    k_cycle_init<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wpart, h->wcnt, h->wgs, tol, 0);
+    CHECK_LAUNCH();
+    if ((s = read_state(h, &hs, st))) return s;
+    if (hs.converged) { conv = true; break; }
+  }
+  if (hs.breakdown && !conv) {
+    // a happy breakdown solves the system exactly in the Krylov space
+    conv = true;
+  }
+  R.iterations = total;
+  R.converged = conv ? 1 : 0;
+  R.gmres_relres = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
+
+  // assembly of x_S and recovery of u (Algorithm 3 steps 5-9)
+  if (defl) {
+    if ((s = launch_precond(h, h->wx, h->wt, h->wy, h->wc, st))) return s;  // t = M^-1 x, y = S t, c = Z^T y
+    if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
+    k_assemble<<<nbs, kSlotsPerBlock, 0, st>>>(g, h->wt, h->wchat, h->wchatb, h->ww);
+    CHECK_LAUNCH();
+  } else if (h->opts.precond == 1) {
+    if ((s = launch_precond(h, h->wx, h->ww, nullptr, nullptr, st))) return s;
+  } else {
+    CU(cudaMemcpyAsync(h->ww, h->wx, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  k_recover<<<(unsigned)g.nel, kElemThreads, elem_smem(g.n), st>>>(g, h->dfdx, h->dfdy, h->wb, h->ww, u);
+  CHECK_LAUNCH();
+  if ((s = launch_dot(h, h->dwhat, u, g.r, scal + 2, st))) return s;  // GLL-weighted mean
+  k_sub_const<<<std::min<unsigned>(blocks_for(g.r, 256), 4096u), 256, 0, st>>>(u, scal + 2, g.r);
+  CHECK_LAUNCH();
+  // true Schur residual ||b_S - S x|| / ||b_S|| (FP64)
+  if ((s = launch_schur(h, h->ww, h->wtmp, st))) return s;
+  k_sub<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wbS, h->wtmp, h->wtmp);
+  CHECK_LAUNCH();
+  if ((s = launch_dot(h, h->wtmp, h->wtmp, kp, scal + 3, st))) return s;
+  if ((s = launch_dot(h, h->wbS, h->wbS, kp, scal + 4, st))) return s;
+  double sc[5];
+  CU(cudaMemcpyAsync(sc, scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  R.schur_relres = sc[4] > 0 ? std::sqrt(sc[3] / sc[4]) : 0.0;
+  R.launches = (int)(h->launches - launches0);
+  if (rep) *rep = R;
+  if (!conv) return fail(SMPM_ENOTCONV, "GMRES did not converge within maxit");
+  return SMPM_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+void smpm_default_opts(smpm_opts* o) {
+  if (!o) return;
+  o->tol = 1e-10;
+  o->restart = 50;
+  o->maxit = 1000;
+  o->precision = 0;
+  o->precond = 2;
+  o->tau_scale = 1.0;
+  o->robin_scale = 0.25;
+}
+
+const char* smpm_last_error(void) { return g_last_error.c_str(); }
+
+smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* out) {
+  if (!out) return fail(SMPM_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (mx < 1 || my < 1 || mx > 4096 || my > 4096 || n < 2 || n > kMaxN)
+    return fail(SMPM_EINVAL, "grid sizes out of range");
+  if (!(Lx > 0) || !(Ly > 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
+    return fail(SMPM_EINVAL, "domain lengths must be positive and finite");
+  smpm_handle h = new (std::nothrow) smpm_handle_s();
+  if (!h) return fail(SMPM_ENOMEM, "host allocation failed");
+  Geometry& g = h->g;
+  g.mx = mx; g.my = my; g.n = n; g.M = 4 * n;
+  g.Lx = Lx; g.Ly = Ly; g.hx = Lx / mx; g.hy = Ly / my;
+  g.nel = (long long)mx * my;
+  g.nn = (long long)n * n;
+  g.r = g.nn * g.nel;
+  g.kp = 4LL * n * g.nel;
+  g.d = (long long)(mx - 1) * my + (long long)mx * (my - 1);
+  g.k = 2LL * n * g.d;
+  smpm_default_opts(&h->opts);
+  *out = h;
+  return SMPM_OK;
+}
+
+smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d, long long* k, long long* nblack) {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  if (r) *r = h->g.r;
+  if (kp) *kp = h->g.kp;
+  if (d) *d = h->g.d;
+  if (k) *k = h->g.k;
+  if (nblack) {
+    long long c = 0;
+    for (long long e = 0; e < h->g.nel; ++e) c += h->g.black((int)e) ? 1 : 0;
+    *nblack = c;
+  }
+  return SMPM_OK;
+}
+
+smpm_status smpm_node_coords(smpm_handle h, double* x, double* y) {
+  if (!h || !x || !y) return fail(SMPM_EINVAL, "null argument");
+  const Geometry& g = h->g;
+  std::vector<double> xi, w;
+  gll(g.n, &xi, &w);
+  for (long long e = 0; e < g.nel; ++e) {
+    int ix = (int)(e % g.mx), iy = (int)(e / g.mx);
+    for (int b = 0; b < g.n; ++b)
+      for (int a = 0; a < g.n; ++a) {
+        long long q = e * g.nn + b * g.n + a;
+        x[q] = ix * g.hx + (xi[a] + 1.0) * g.hx / 2.0;
+        y[q] = iy * g.hy + (xi[b] + 1.0) * g.hy / 2.0;
+      }
+  }
+  return SMPM_OK;
+}
+
+smpm_status smpm_node_mass(smpm_handle h, double* wq) {
+  if (!h || !wq) return fail(SMPM_EINVAL, "null argument");
+  const Geometry& g = h->g;
+  std::vector<double> xi, w;
+  gll(g.n, &xi, &w);
+  for (long long e = 0; e < g.nel; ++e)
+    for (int b = 0; b < g.n; ++b)
+      for (int a = 0; a < g.n; ++a) wq[e * g.nn + b * g.n + a] = w[a] * w[b] * g.hx * g.hy / 4.0;
+  return SMPM_OK;
+}
+
+smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  smpm_opts opts;
+  smpm_default_opts(&opts);
+  if (o) opts = *o;
+  if (!(opts.tol > 0) || opts.restart < 1 || opts.restart > kMaxRestart || opts.maxit < 1 || opts.precond < 0 ||
+      opts.precond > 2 || opts.precision < 0 || opts.precision > 1 || !(opts.tau_scale > 0) ||
+      !(opts.robin_scale > 0))
+    return fail(SMPM_EINVAL, "bad solver options");
+  if (h->g.nel < 2) return fail(SMPM_ENOINTERFACE, "the Schur method needs mx*my >= 2 (one interface at least)");
+  cudaStream_t st = as_stream(stream);
+  free_all(h);
+  h->factored = false;
+  h->opts = opts;
+  h->f = Factors();
+  std::string err;
+  int rc = factor_host(h->g, opts, &h->f, &err);
+  if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
+  const Geometry& g = h->g;
+  DevGeo& dg = h->dg;
+  dg.mx = g.mx; dg.my = g.my; dg.n = g.n; dg.M = g.M;
+  dg.nel = g.nel; dg.kp = g.kp; dg.r = g.r; dg.d = g.d;
+  dg.tau_x = h->f.tau_x; dg.tau_y = h->f.tau_y; dg.p_x = h->f.p_x; dg.p_y = h->f.p_y;
+  dg.sx = 2.0 / g.hx; dg.sy = 2.0 / g.hy;
+  smpm_status s;
+  if ((s = upload(h, &h->dT, h->f.T, st)) || (s = upload(h, &h->dRs, h->f.Rs, st)) ||
+      (s = upload(h, &h->dG, h->f.G, st)) || (s = upload(h, &h->dX, h->f.X, st)) ||
+      (s = upload(h, &h->dH, h->f.H, st)) || (s = upload(h, &h->dfdx, h->f.fdx, st)) ||
+      (s = upload(h, &h->dfdy, h->f.fdy, st)) || (s = upload(h, &h->dD, h->f.D, st)) ||
+      (s = upload(h, &h->duL, h->f.uL, st)) || (s = upload(h, &h->duS, h->f.uS, st)) ||
+      (s = upload(h, &h->duC, h->f.uC, st)) || (s = upload(h, &h->dwhat, h->f.what, st)) ||
+      (s = upload(h, &h->dblack, h->f.black, st)) || (s = upload(h, &h->dwhite, h->f.white, st)))
+    return s;
+  const size_t kp = g.kp, r = g.r, d = g.d, m = opts.restart;
+  const size_t nbs = blocks_for(g.kp, kSlotsPerBlock);
+  if ((s = dalloc(h, &h->wb, r)) || (s = dalloc(h, &h->wbS, kp)) || (s = dalloc(h, &h->wV, (m + 1) * kp)) ||
+      (s = dalloc(h, &h->wt, kp)) || (s = dalloc(h, &h->wy, kp)) || (s = dalloc(h, &h->ww, kp)) ||
+      (s = dalloc(h, &h->ww2, kp)) || (s = dalloc(h, &h->wx, kp)) || (s = dalloc(h, &h->wrg, kp)) ||
+      (s = dalloc(h, &h->wtmp, kp)) || (s = dalloc(h, &h->wc, d)) || (s = dalloc(h, &h->wchat, d)) ||
+      (s = dalloc(h, &h->wcb, d)) || (s = dalloc(h, &h->wchatb, d)) ||
+      (s = dalloc(h, &h->wpart, (size_t)(kMaxRestart + 3) * std::max<size_t>(nbs, 1024))) ||
+      (s = dalloc(h, &h->wcnt, 8)) || (s = dalloc(h, &h->wgs, 1)))
+    return s;
+  CU(cudaMemsetAsync(h->wcnt, 0, 8 * sizeof(unsigned), st));
+  CU(cudaMemsetAsync(h->wgs, 0, sizeof(GState), st));
+  CU(cudaStreamSynchronize(st));
+  h->factored = true;
+  return SMPM_OK;
+}
+
+smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double tol, int nrhs, double* u,
+                        smpm_report* rep, void* stream) {
+  if (!h || !f || !u || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
+  if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
+  if (h->opts.precision != 0) return fail(SMPM_EINVAL, "precision mode not available in this build");
+  double t = tol > 0 ? tol : h->opts.tol;
+  cudaStream_t st = as_stream(stream);
+  smpm_status worst = SMPM_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    smpm_status s = solve_one(h, f + (size_t)k * h->g.r, gn ? gn + (size_t)k * h->g.kp : nullptr,
+                              u + (size_t)k * h->g.r, t, rep ? rep + k : nullptr, st);
+    if (s == SMPM_ENOTCONV) worst = s;
+    else if (s != SMPM_OK) return s;
+  }
+  return worst;
+}
+
+smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, double tol, int nrhs, double* u,
+                             smpm_report* rep, void* stream) {
+  if (!h || !f || !u || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
+  if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
+  cudaStream_t st = as_stream(stream);
+  const size_t rn = (size_t)h->g.r * nrhs, gnn = (size_t)h->g.kp * nrhs;
+  if (h->sf_n < (size_t)nrhs) {
+    smpm_status s;
+    if ((s = dalloc(h, &h->sf, rn)) || (s = dalloc(h, &h->sg, gnn)) || (s = dalloc(h, &h->su, rn))) return s;
+    h->sf_n = nrhs;
+  }
+  CU(cudaMemcpyAsync(h->sf, f, rn * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (gn) CU(cudaMemcpyAsync(h->sg, gn, gnn * sizeof(double), cudaMemcpyHostToDevice, st));
+  smpm_status s = schur_solve(h, h->sf, gn ? h->sg : nullptr, tol, nrhs, h->su, rep, stream);
+  if (s != SMPM_OK && s != SMPM_ENOTCONV) return s;
+  CU(cudaMemcpyAsync(u, h->su, rn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return s;
+}
+
+#define NEED_FACTOR()                                                              \
+  do {                                                                             \
+    if (!h) return fail(SMPM_EINVAL, "null handle");                               \
+    if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called"); \
+  } while (0)
+
+smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream) {
+  NEED_FACTOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  return launch_schur(h, v, y, as_stream(stream));
+}
+
+smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream) {
+  NEED_FACTOR();
+  if (!v || !t) return fail(SMPM_EINVAL, "null vector");
+  return launch_precond(h, v, t, nullptr, nullptr, as_stream(stream));
+}
+
+smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, void* stream) {
+  NEED_FACTOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  return launch_precond(h, v, h->wt, y, h->wc, as_stream(stream));
+}
+
+smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream) {
+  NEED_FACTOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  cudaStream_t st = as_stream(stream);
+  smpm_status s;
+  if ((s = launch_zt(h, v, h->wc, st))) return s;
+  if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
+  return launch_defl(h, v, h->wchat, -1, y, st);
+}
+
+smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream) {
+  NEED_FACTOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  cudaStream_t st = as_stream(stream);
+  smpm_status s;
+  if ((s = launch_schur(h, v, h->wtmp, st))) return s;
+  if ((s = launch_zt(h, h->wtmp, h->wc, st))) return s;
+  if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
+  k_assemble<<<blocks_for(h->g.kp, kSlotsPerBlock), kSlotsPerBlock, 0, st>>>(h->dg, v, h->wchat, nullptr, y);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream) {
+  NEED_FACTOR();
+  if (!b || !bS) return fail(SMPM_EINVAL, "null vector");
+  cudaStream_t st = as_stream(stream);
+  CU(cudaMemsetAsync(bS, 0, h->g.kp * sizeof(double), st));
+  k_schur_rhs<<<(unsigned)h->g.nel, kElemThreads, elem_smem(h->g.n), st>>>(h->dg, h->dfdx, h->dfdy, h->dD, b, bS);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status smpm_recover(smpm_handle h, const double* b, const double* x, double* u, void* stream) {
+  NEED_FACTOR();
+  if (!b || !x || !u) return fail(SMPM_EINVAL, "null vector");
+  k_recover<<<(unsigned)h->g.nel, kElemThreads, elem_smem(h->g.n), as_stream(stream)>>>(h->dg, h->dfdx, h->dfdy, b,
+                                                                                        x, u);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+smpm_status smpm_null_vectors(smpm_handle h, double* uL, double* uS, double* uC, void* stream) {
+  NEED_FACTOR();
+  cudaStream_t st = as_stream(stream);
+  if (uL) CU(cudaMemcpyAsync(uL, h->duL, h->g.r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (uS) CU(cudaMemcpyAsync(uS, h->duS, h->g.kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (uC) CU(cudaMemcpyAsync(uC, h->duC, h->g.d * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return SMPM_OK;
+}
+
+smpm_status smpm_coarse_matrix(smpm_handle h, double* C) {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  if (h->f.C.empty()) return fail(SMPM_ESTATE, "no factors: call schur_factor or smpm_factor_host_only");
+  if (!C) return fail(SMPM_EINVAL, "null pointer");
+  std::memcpy(C, h->f.C.data(), h->f.C.size() * sizeof(double));
+  return SMPM_OK;
+}
+
+smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o) {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  smpm_opts opts;
+  smpm_default_opts(&opts);
+  if (o) opts = *o;
+  if (!(opts.tau_scale > 0) || !(opts.robin_scale > 0)) return fail(SMPM_EINVAL, "bad solver options");
+  if (h->g.nel < 2) return fail(SMPM_ENOINTERFACE, "the Schur method needs mx*my >= 2 (one interface at least)");
+  Factors f;
+  std::string err;
+  int rc = factor_host(h->g, opts, &f, &err);
+  if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
+  h->f = std::move(f);
+  return SMPM_OK;
+}
+
+smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long long count, long long* len) {
+  if (!h || !name) return fail(SMPM_EINVAL, "null argument");
+  const Factors& f = h->f;
+  std::vector<double> tmp;
+  const std::vector<double>* src = nullptr;
+  std::string nm(name);
+  if (nm == "x1d") src = &f.x1d;
+  else if (nm == "w1d") src = &f.w1d;
+  else if (nm == "D") src = &f.D;
+  else if (nm == "T") src = &f.T;
+  else if (nm == "G") src = &f.G;
+  else if (nm == "X") src = &f.X;
+  else if (nm == "C") src = &f.C;
+  else if (nm == "H") src = &f.H;
+  else if (nm == "c0") src = &f.c0;
+  else if (nm == "uC") src = &f.uC;
+  else if (nm == "uS") src = &f.uS;
+  else if (nm == "B1") src = &f.B1;
+  else if (nm == "uL") src = &f.uL;
+  else if (nm == "what") src = &f.what;
+  else if (nm == "black") { tmp.assign(f.black.begin(), f.black.end()); src = &tmp; }
+  else if (nm == "null_iterations") { tmp.assign(1, (double)f.null_iterations); src = &tmp; }
+  else return fail(SMPM_EINVAL, "unknown factor name " + nm);
+  if (len) *len = (long long)src->size();
+  if (!out) return SMPM_OK;
+  if (count != (long long)src->size()) return fail(SMPM_EINVAL, "count does not match the factor length");
+  std::memcpy(out, src->data(), src->size() * sizeof(double));
+  return SMPM_OK;
+}
+
+void smpm_destroy(smpm_handle h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+"""GPU parity: every operator of the CUDA path and the whole solve, called
+through the C ABI, against the oracle on the same seeded inputs.
+
+Tolerances: single operators agree to 1e-12 relative (FP64, different
+summation order); solutions to a relative L2 error of 1e-10 (FP64 path), with
+GMRES iteration counts within one of the oracle's."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1601_03432_gb300 import Grid, inputs
+from paper_1601_03432_gb300 import _binding as B
+from oracle.smpm import SMPMGrid
+from oracle.schur import SchurSystem
+from oracle import methods
+
+GRIDS = [(2, 2, 8, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (5, 4, 7, 1.0, 1.0), (2, 1, 6, 1.0, 1.0), (1, 3, 4, 1.0, 2.0),
+         (6, 5, 2, 1.0, 1.0)]
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1601_03432_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module", params=GRIDS, ids=lambda p: "x".join(map(str, p[:3])))
+def pair(request, built):
+    mx, my, n, Lx, Ly = request.param
+    og = SMPMGrid(mx, my, n, Lx, Ly)
+    osys = SchurSystem(og)
+    lg = Grid(mx, my, n, Lx, Ly)
+    lg.factor()
+    return og, osys, lg
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_operators(pair):
+    og, osys, lg = pair
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(og.k)
+    vp = dev(og.to_padded(v))
+    out = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    lg.apply_schur(vp, out)
+    assert rel(og.from_padded(host(out)), osys.apply_S(v)) < 1e-12
+    assert np.all(host(out)[np.setdiff1d(np.arange(og.kp), og.padded_index)] == 0)
+    lg.apply_precond(vp, out)
+    assert rel(og.from_padded(host(out)), osys.apply_Minv(v)) < 1e-12
+    lg.apply_schur_precond(vp, out)
+    assert rel(og.from_padded(host(out)), osys.apply_S(osys.apply_Minv(v))) < 1e-12
+    lg.apply_deflation(vp, out)
+    assert rel(og.from_padded(host(out)), osys.apply_P(v)) < 1e-11
+    lg.apply_deflation_q(vp, out)
+    assert rel(og.from_padded(host(out)), osys.apply_Q(v)) < 1e-11
+    b = rng.standard_normal(og.r)
+    lg.schur_rhs(dev(b), out)
+    assert rel(og.from_padded(host(out)), osys.schur_rhs(b)) < 1e-12
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    lg.recover(dev(b), vp, u)
+    assert rel(host(u), osys.recover(b, v)) < 1e-12
+
+
+def test_null_vectors(pair):
+    og, osys, lg = pair
+    uL = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    uS = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    uC = torch.zeros(og.d, dtype=torch.float64, device="cuda")
+    lg.null_vectors(uL, uS, uC)
+    for got, ref in ((host(uL), osys.u_L), (og.from_padded(host(uS)), osys.u_S), (host(uC), osys.u_C)):
+        got = got * np.sign(got @ ref)
+        assert np.linalg.norm(got - ref) < 1e-12
+
+
+@pytest.mark.parametrize("precond", [0, 1, 2])
+def test_solve_matches_oracle(pair, precond):
+    og, osys, lg = pair
+    x, y = og.coords()
+    f = inputs.white_noise(og.r, 21)
+    gslots = np.random.default_rng(22).standard_normal(og.kp)
+    b = og.rhs(f, gslots)
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, b)
+    alg = [methods.algorithm1, methods.algorithm2, methods.algorithm3][precond]
+    uo, info = alg(osys, b, tol=1e-12, restart=50)
+    lg.factor(precond=precond, tol=1e-12)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(dev(f), u, g=dev(gslots), tol=1e-12)[0]
+    uh = host(u)
+    assert rep["converged"] == 1
+    assert rel(uh, ud) < 1e-10
+    assert rel(uh, uo) < 1e-10
+    assert abs(rep["iterations"] - info["iterations"]) <= 1, (rep, info["iterations"])
+    assert rep["schur_relres"] < 1e-10
+    lg.factor()
+
+
+def test_config1_cos_problem(built):
+    og = SMPMGrid(2, 2, 8)
+    osys = SchurSystem(og)
+    lg = Grid(2, 2, 8)
+    lg.factor(tol=1e-12)
+    x, y = lg.node_coords()
+    f, uex = inputs.cos_problem(*og.coords())
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(dev(f), u)[0]
+    uo, info = methods.algorithm3(osys, f, tol=1e-12)
+    assert rel(host(u), uo) < 1e-10
+    assert rep["iterations"] == info["iterations"] or abs(rep["iterations"] - info["iterations"]) <= 1
+    assert np.abs(host(u) - og.zero_mean(uex)).max() < 1e-6
+
+
+def test_polynomial_neumann_data_exact(built):
+    og = SMPMGrid(3, 2, 5, 1.5, 1.0)
+    lg = Grid(3, 2, 5, 1.5, 1.0)
+    lg.factor(tol=1e-13)
+    x, y = og.coords()
+    f, uex, gfun = inputs.polynomial_problem(x, y)
+    gs = og.boundary_g(gfun)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    lg.solve(dev(f), u, g=dev(gs))
+    np.testing.assert_allclose(host(u), og.zero_mean(uex), atol=1e-9 * np.abs(uex).max())
+
+
+def test_host_entry_and_batch(built):
+    og = SMPMGrid(4, 3, 6)
+    lg = Grid(4, 3, 6)
+    lg.factor()
+    fs = np.stack([inputs.white_noise(og.r, s) for s in (1, 2, 3)])
+    ud = torch.zeros(3 * og.r, dtype=torch.float64, device="cuda")
+    reps = lg.solve(dev(fs.ravel()), ud, nrhs=3)
+    uh = np.zeros(3 * og.r)
+    reps_h = lg.solve_host(np.ascontiguousarray(fs.ravel()), uh, nrhs=3)
+    np.testing.assert_allclose(uh, host(ud), rtol=0, atol=1e-13 * np.abs(uh).max())
+    assert [r["iterations"] for r in reps] == [r["iterations"] for r in reps_h]
+    osys = SchurSystem(og)
+    for k in range(3):
+        uo, _ = methods.algorithm3(osys, fs[k])
+        assert rel(uh[k * og.r:(k + 1) * og.r], uo) < 1e-9
+
+
+def test_degenerate_inputs(built):
+    lg = Grid(3, 3, 5)
+    lg.factor()
+    u = torch.ones(lg.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(torch.zeros(lg.r, dtype=torch.float64, device="cuda"), u)[0]
+    assert float(u.abs().max()) == 0.0 and rep["iterations"] == 0
+    f = torch.zeros(lg.r, dtype=torch.float64, device="cuda")
+    f[7] = float("nan")
+    with pytest.raises(B.SmpmError) as ei:
+        lg.solve(f, u)
+    assert ei.value.status == B.SMPM_ENAN
+    # a constant right-hand side is removed by the u_L projection up to rounding
+    rep = lg.solve(torch.ones(lg.r, dtype=torch.float64, device="cuda"), u, allow_notconv=True)[0]
+    assert float(u.abs().max()) < 1e-6
+
+
+@pytest.mark.slow
+def test_config2_full_size(built):
+    """16 x 16 elements, n = 16, seeded Fourier right-hand side, restart 50,
+    tol 1e-10: the bench workload."""
+    og = SMPMGrid(16, 16, 16)
+    osys = SchurSystem(og)
+    lg = Grid(16, 16, 16)
+    lg.factor(tol=1e-10, restart=50)
+    f, _ = inputs.fourier_rhs(*og.coords(), seed=1000)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(dev(f), u)[0]
+    uo, info = methods.algorithm3(osys, f, tol=1e-10, restart=50)
+    assert rep["converged"] == 1
+    assert abs(rep["iterations"] - info["iterations"]) <= 1
+    assert rel(host(u), uo) < 1e-9
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, f)
+    assert rel(host(u), ud) < 1e-8

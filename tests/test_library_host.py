@@ -1,0 +1,161 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol that
+include/smpm.h declares, rejects bad arguments, and its host factor step
+(Sec. 1.2 - 2, computed in C++ with its own GLL nodes, eigen-solver and LU)
+matches the oracle.  No GPU is needed: only host entry points are called."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_03432_gb300 import _binding as B
+from oracle.smpm import SMPMGrid, OPPOSITE
+from oracle.schur import SchurSystem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1601_03432_gb300.build import build
+    build()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "smpm.h")).read()
+    declared = set(re.findall(r"^\s*(?:smpm_status|void|const char\*)\s+(\w+)\s*\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(B.EXPORTS)
+    L = B.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_bad_arguments():
+    import ctypes
+    h = ctypes.c_void_p()
+    assert B.lib().smpm_setup(0, 2, 5, 1.0, 1.0, ctypes.byref(h)) == B.SMPM_EINVAL
+    assert B.lib().smpm_setup(2, 2, 1, 1.0, 1.0, ctypes.byref(h)) == B.SMPM_EINVAL
+    assert B.lib().smpm_setup(2, 2, 33, 1.0, 1.0, ctypes.byref(h)) == B.SMPM_EINVAL
+    assert B.lib().smpm_setup(2, 2, 5, -1.0, 1.0, ctypes.byref(h)) == B.SMPM_EINVAL
+    g = B.Grid(1, 1, 5)
+    with pytest.raises(B.SmpmError) as ei:
+        g.factor_host_only()
+    assert ei.value.status == B.SMPM_ENOINTERFACE
+    g2 = B.Grid(2, 2, 5)
+    import torch
+    f = torch.zeros(g2.r, dtype=torch.float64)
+    with pytest.raises(B.SmpmError) as ei:
+        g2.solve(f, f)                      # no factor yet
+    assert ei.value.status == B.SMPM_ESTATE
+
+
+GRIDS = [(2, 2, 6, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (4, 3, 7, 1.0, 2.0), (5, 4, 4, 1.0, 1.0)]
+
+
+@pytest.fixture(scope="module", params=GRIDS, ids=lambda p: "x".join(map(str, p[:3])))
+def pair(request):
+    mx, my, n, Lx, Ly = request.param
+    og = SMPMGrid(mx, my, n, Lx, Ly)
+    osys = SchurSystem(og)
+    lg = B.Grid(mx, my, n, Lx, Ly)
+    lg.factor_host_only()
+    return og, osys, lg
+
+
+def test_sizes_and_coords(pair):
+    og, osys, lg = pair
+    assert (lg.r, lg.kp, lg.d, lg.k) == (og.r, og.kp, og.d, og.k)
+    x, y = lg.node_coords()
+    ox, oy = og.coords()
+    np.testing.assert_allclose(x, ox, atol=1e-14)
+    np.testing.assert_allclose(y, oy, atol=1e-14)
+    np.testing.assert_allclose(lg.node_mass(), og.mass(), rtol=1e-13)
+
+
+def test_gll_and_D(pair):
+    og, osys, lg = pair
+    np.testing.assert_allclose(lg.host_factor("x1d"), og.x1d, atol=1e-15)
+    np.testing.assert_allclose(lg.host_factor("w1d"), og.w1d, rtol=1e-13)
+    n = og.n
+    np.testing.assert_allclose(lg.host_factor("D").reshape(n, n), og.D, atol=1e-12 * n * n)
+
+
+def test_T_blocks_are_S_entries(pair):
+    """T_e[(F,t),(G,s)] = S[slot (nbr(e,F), opp F, t), slot (e,G,s)]."""
+    og, osys, lg = pair
+    n, M = og.n, 4 * og.n
+    T = lg.host_factor("T").reshape(og.nel, M, M)
+    Sd = osys.S.toarray()
+    scale = np.abs(Sd).max()
+    for e in range(og.nel):
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            for G in range(4):
+                for t in range(n):
+                    for s in range(n):
+                        val = T[e, F * n + t, G * n + s]
+                        if e2 < 0 or og.neighbour(e, G) < 0:
+                            assert val == 0.0
+                            continue
+                        ref = Sd[og.slot_of[(e2, OPPOSITE[F], t)], og.slot_of[(e, G, s)]]
+                        assert abs(val - ref) <= 1e-11 * scale
+
+
+def test_block_jacobi_reduced_form(pair):
+    """M_b^-1 through G = (I - X Y)^-1: a = G (p - X q), b = q - T_e a."""
+    og, osys, lg = pair
+    n, M = og.n, 4 * og.n
+    T = lg.host_factor("T").reshape(og.nel, M, M)
+    G = lg.host_factor("G").reshape(-1, M, M)
+    X = lg.host_factor("X").reshape(-1, 4, n, n)
+    black = lg.host_factor("black").astype(int)
+    assert list(black) == osys.black
+    v = np.random.default_rng(4).standard_normal(og.k)
+    ref = osys.apply_Minv(v)
+    vp = og.to_padded(v)
+    out = np.zeros(og.kp)
+    for ib, e in enumerate(black):
+        p = vp[e * M:(e + 1) * M].copy()
+        q = np.zeros(M)
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            if e2 >= 0:
+                q[F * n:(F + 1) * n] = vp[e2 * M + OPPOSITE[F] * n: e2 * M + OPPOSITE[F] * n + n]
+        Xq = np.concatenate([X[ib, F] @ q[F * n:(F + 1) * n] for F in range(4)])
+        a = G[ib] @ (p - Xq)
+        b = q - T[e] @ a
+        out[e * M:(e + 1) * M] = a
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            if e2 >= 0:
+                out[e2 * M + OPPOSITE[F] * n: e2 * M + OPPOSITE[F] * n + n] = b[F * n:(F + 1) * n]
+    np.testing.assert_allclose(og.from_padded(out), ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_coarse_objects(pair):
+    og, osys, lg = pair
+    d = og.d
+    C = lg.coarse_matrix()
+    np.testing.assert_allclose(C, osys.C, atol=1e-11 * np.abs(osys.C).max())
+    c0 = lg.host_factor("c0")
+    assert abs(abs(c0 @ osys.c0) / (np.linalg.norm(c0) * np.linalg.norm(osys.c0)) - 1) < 1e-13
+    uC = lg.host_factor("uC")
+    assert abs(abs(uC @ osys.u_C) - 1) < 1e-11
+    H = lg.host_factor("H").reshape(d, d)
+    r = np.random.default_rng(5).standard_normal(d)
+    np.testing.assert_allclose(H @ r, osys.coarse_solve(r), atol=1e-9 * np.abs(osys.coarse_solve(r)).max())
+
+
+def test_null_vectors(pair):
+    """u_S and u_L to round-off: a direction error leaves an inconsistent
+    component in b_S that stalls GMRES near the tolerance."""
+    og, osys, lg = pair
+    uS = og.from_padded(lg.host_factor("uS"))
+    uS *= np.sign(uS @ osys.u_S)
+    assert np.linalg.norm(uS - osys.u_S) < 1e-12
+    assert np.linalg.norm(osys.S.T @ uS) < 1e-13 * abs(osys.S).max() * np.sqrt(og.k)
+    uL = lg.host_factor("uL")
+    uL *= np.sign(uL @ osys.u_L)
+    assert np.linalg.norm(uL - osys.u_L) < 1e-12
+    np.testing.assert_allclose(lg.host_factor("what").sum(), 1.0, rtol=1e-14)
