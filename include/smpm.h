@@ -44,7 +44,8 @@ typedef enum {
   SMPM_ENOTCONV = 5,      /* GMRES did not reach tol within maxit (u = best)    */
   SMPM_EBREAKDOWN = 6,    /* Arnoldi breakdown before tol                       */
   SMPM_ENAN = 7,          /* NaN/Inf met in the input or the iteration          */
-  SMPM_ESTATE = 8         /* call order violated (e.g. solve before factor)     */
+  SMPM_ESTATE = 8,        /* call order violated (e.g. solve before factor)     */
+  SMPM_ETIMEOUT = 9       /* a bounded device-side wait gave up (no hang)       */
 } smpm_status;
 
 /* Solver options.  precond: 0 = none (Algorithm 1), 1 = block-Jacobi
@@ -72,6 +73,7 @@ typedef struct {
   double gmres_relres;   /* final GMRES residual estimate / ||P b_S||            */
   double schur_relres;   /* ||b_S - S x_S|| / ||b_S|| recomputed in FP64          */
   int launches;          /* CUDA kernels launched by this solve                  */
+  double gmres_ms;       /* device time of the GMRES kernel (CUDA events)        */
 } smpm_report;
 
 /* Fill o with the defaults listed above. */
@@ -100,8 +102,9 @@ smpm_status smpm_node_mass(smpm_handle h, double* w);
  * G_b = (I - X_b Y_b)^-1, the coarse matrix C = Z^T S Z and its regularised
  * inverse, and the null vectors u_L, u_S, u_C (Sec. 1.4).  Computed on the
  * host in FP64 and uploaded; o may be null for the defaults.  stream is a
- * cudaStream_t (null = legacy default stream).  Errors: EINVAL,
- * ENOINTERFACE, ENOMEM, ECUDA. */
+ * cudaStream_t (null = legacy default stream).  Errors: EINVAL (also for
+ * precond > 0 on a grid with a single interface, whose only block-Jacobi
+ * block is the whole singular S), ENOINTERFACE, ENOMEM, ECUDA. */
 smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream);
 
 /* Algorithm 3 (or 1/2 per opts.precond) for nrhs right-hand sides.

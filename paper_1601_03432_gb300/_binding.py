@@ -14,8 +14,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmpm.so")
 
 SMPM_OK, SMPM_EINVAL, SMPM_ENOINTERFACE, SMPM_ENOMEM, SMPM_ECUDA, SMPM_ENOTCONV, SMPM_EBREAKDOWN, SMPM_ENAN, \
-    SMPM_ESTATE = range(9)
-STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "EBREAKDOWN", "ENAN", "ESTATE"]
+    SMPM_ESTATE, SMPM_ETIMEOUT = range(10)
+STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "EBREAKDOWN", "ENAN", "ESTATE",
+                "ETIMEOUT"]
 
 # every symbol include/smpm.h declares
 EXPORTS = [
@@ -35,7 +36,7 @@ class SmpmOpts(ctypes.Structure):
 class SmpmReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("converged", ctypes.c_int), ("gmres_relres", ctypes.c_double), ("schur_relres", ctypes.c_double),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("gmres_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

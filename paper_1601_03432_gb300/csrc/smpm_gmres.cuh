@@ -1,0 +1,673 @@
+// Persistent GMRES kernel for x := GMRES(op, rhs) with op one of
+//   S            (Algorithm 1),
+//   S M^-1       (Algorithm 2),
+//   P S M^-1     (Algorithm 3),
+// run as ONE cooperative launch per solve: restarted GMRES(m), classical
+// Gram-Schmidt with one re-orthogonalisation (CGS2), FP64 Givens rotations,
+// the convergence test on the rotated residual, restarts from the true
+// residual.
+//
+// Work is owned, not redistributed per phase: CTA c owns the checkerboard
+// blocks ib = c, c + G, ... (G = grid size) -- the black elements and the
+// slots of their blocks, which partition Gamma -- and the white elements
+// iw = c, c + G, ...  The owner keeps its blocks' operator matrices (G_b, T_e,
+// X_b and the white T_e, column-major) and its slice of the Krylov basis in
+// shared memory when they fit, so an Arnoldi step touches L2/HBM only for the
+// vectors exchanged between neighbouring elements.  One step:
+//   A  owner: v_j = w2 - V h2 on its block slots (lazy, see E), then the
+//      block solve t = M^-1 v_j: a = G (p - X q), b = q - T_e a
+//   B  white elements: y = S t (y = v on white-owned slots), c = Z^T y
+//   C  c_hat = C^+ c (dense FP64 rows spread over all CTAs; Algorithm 3)
+//   D  owner: w = y - S Z c_hat; V^T w and ||w||^2, accumulated with FP64
+//      atomics in L2
+//   E  owner: w2 = w - V h1; V^T w2 and ||w2||^2 likewise; every CTA forms
+//      ||v_{j+1}||^2 = ||w2||^2 - ||h2||^2 and applies the same Givens
+//      rotations to its own copy, so all CTAs take the same decision.
+// Phases are separated by a grid barrier (5 per step for Algorithm 3).  The
+// basis is kept unnormalised with the inverse norms replicated in every CTA.
+// FP64 products are plain per-thread FMA chains (thread per matrix row, per
+// basis vector, per slot): FP64 issue slots are scarce on this part, so the
+// hot path uses no warp-shuffle reduction trees.
+//
+// Data written by other CTAs inside the kernel is read with ld.global.cg: L1
+// is not coherent across SMs.  The grid barrier spins with a bound and raises
+// an error flag instead of hanging.
+#pragma once
+// Included inside the anonymous namespace of smpm_solver.cu.
+
+template <typename S>
+struct GmresArgs {
+  DevGeo g;
+  const int* black;
+  const int* white;
+  int nblack, nwhite;
+  const S* Tc;      // nel * M*M, column-major T_e
+  const S* Gc;      // nblack * M*M, column-major G_b
+  const S* Xc;      // nblack * 4*n*n, column-major X_F blocks
+  const S* Rs;      // nel * M*4 row sums of T_e (deflation)
+  const double* H;  // d*d row-major coarse inverse
+  S* vglob;         // kp : current basis vector (raw), exchanged between CTAs
+  S* vown;          // G * (m+1) * ES : basis slices when not resident in smem
+  S* t;             // kp
+  S* y;             // kp
+  double* c;        // d
+  double* chat;     // d
+  const S* rhs;     // kp
+  S* x;             // kp (zero on entry)
+  double* acc;      // (2m + 1) * (m + 3) FP64 accumulators (zero on entry)
+  GState* gs;
+  unsigned* bar;    // barrier counter (zero on entry)
+  int* err;
+  int precond, m, maxit;
+  double tol;
+  int nown_b, nown_w;  // blocks / white elements per CTA (ceil)
+  int ES;              // entries per CTA in the basis slice (odd, >= 2M nown_b)
+  int mats_smem;       // 1: owned matrices resident in shared memory
+  int basis_smem;      // 1: basis slice resident in shared memory
+  long long* trace;
+  int trace_cap;
+};
+
+#define GM_TRACE(tag)                                                                   \
+  do {                                                                                  \
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && trace_n + 2 <= a.trace_cap) { \
+      a.trace[trace_n++] = (tag);                                                       \
+      a.trace[trace_n++] = clock64();                                                   \
+    }                                                                                   \
+  } while (0)
+
+template <typename S>
+__device__ __forceinline__ S ldcg(const S* p) {
+  return __ldcg(p);
+}
+
+// Grid barrier on a monotonic counter: thread 0 of each CTA adds one with
+// release semantics and polls with acquire loads until the counter reaches
+// the CTA's next epoch (a multiple of the grid size).  Bounded spin; err is
+// set on timeout and the caller unwinds.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    epoch += gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+    long long spins = 0;
+    while ((int)(ld_acquire(bar) - epoch) < 0) {
+      if (++spins > (1LL << 28) || ((spins & 4095) == 0 && *((volatile int*)err))) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// slot of entry i (< 2M) of the block of black element e: own slots first,
+// then the neighbours' slots facing e; -1 where a face has no neighbour.
+__device__ __forceinline__ long long block_slot(const DevGeo& g, int e, int i) {
+  const int M = g.M, n = g.n;
+  if (i < M) return (long long)e * M + i;
+  i -= M;
+  int F = i / n, t = i % n;
+  int e2 = dev_neighbour(g, e, F);
+  return e2 >= 0 ? (long long)e2 * M + (F ^ 1) * n + t : -1;
+}
+
+template <typename S>
+struct Smem {
+  double *h1, *h2, *hs1, *hs2, *gcs, *gsn, *gg, *col, *invb, *misc, *cs;
+  S *p, *r1, *av, *z, *red;
+  S *w, *w2;
+  double* cst;  // staged coarse vector c (d)
+  S* V;     // (m+1) * ES when resident
+  S* mats;  // resident matrices
+};
+
+template <typename S>
+__device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
+  Smem<S> s;
+  const int m = a.m, M = a.g.M;
+  double* d = reinterpret_cast<double*>(raw);
+  s.h1 = d; d += m + 3;
+  s.h2 = d; d += m + 3;
+  s.hs1 = d; d += m + 3;
+  s.hs2 = d; d += m + 3;
+  s.gcs = d; d += m + 3;
+  s.gsn = d; d += m + 3;
+  s.gg = d; d += m + 3;
+  s.col = d; d += m + 3;
+  s.invb = d; d += m + 3;
+  s.misc = d; d += 16;
+  s.cs = d; d += M;
+  s.cst = d; d += a.g.d + 1;
+  S* q = reinterpret_cast<S*>(d);
+  s.p = q; q += M;
+  s.r1 = q; q += M;
+  s.av = q; q += M;
+  s.z = q; q += M;
+  s.red = q; q += 256;
+  s.w = q; q += a.ES + 1;
+  s.w2 = q; q += a.ES + 1;
+  s.V = q;
+  if (a.basis_smem) q += (size_t)(m + 1) * a.ES;
+  s.mats = q;
+  return s;
+}
+
+template <typename S>
+inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
+                               long long d) {
+  size_t dbl = 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
+  size_t sel = 4 * (size_t)M + 256 + 2 * (size_t)(ES + 1);
+  if (basis_smem) sel += (size_t)(m + 1) * ES;
+  if (mats_smem) sel += (size_t)nown_b * (2 * (size_t)M * M + 4 * (size_t)n * n) + (size_t)nown_w * M * M;
+  return dbl * sizeof(double) + sel * sizeof(S) + 64;
+}
+
+// pointers to the owned matrices (shared-memory copies or global)
+template <typename S>
+__device__ __forceinline__ const S* mat_G(const GmresArgs<S>& a, const Smem<S>& s, int k, int ib) {
+  const int M = a.g.M, n = a.g.n;
+  return a.mats_smem ? s.mats + (size_t)k * (2 * M * M + 4 * n * n) : a.Gc + (size_t)ib * M * M;
+}
+template <typename S>
+__device__ __forceinline__ const S* mat_Tb(const GmresArgs<S>& a, const Smem<S>& s, int k, int e) {
+  const int M = a.g.M, n = a.g.n;
+  return a.mats_smem ? s.mats + (size_t)k * (2 * M * M + 4 * n * n) + M * M : a.Tc + (size_t)e * M * M;
+}
+template <typename S>
+__device__ __forceinline__ const S* mat_X(const GmresArgs<S>& a, const Smem<S>& s, int k, int ib) {
+  const int M = a.g.M, n = a.g.n;
+  return a.mats_smem ? s.mats + (size_t)k * (2 * M * M + 4 * n * n) + 2 * M * M : a.Xc + (size_t)ib * 4 * n * n;
+}
+template <typename S>
+__device__ __forceinline__ const S* mat_Tw(const GmresArgs<S>& a, const Smem<S>& s, int k, int e) {
+  const int M = a.g.M, n = a.g.n;
+  return a.mats_smem ? s.mats + (size_t)a.nown_b * (2 * M * M + 4 * n * n) + (size_t)k * M * M
+                     : a.Tc + (size_t)e * M * M;
+}
+
+template <typename S>
+__device__ __forceinline__ S* basis(const GmresArgs<S>& a, const Smem<S>& s, int l) {
+  return a.basis_smem ? s.V + (size_t)l * a.ES : a.vown + ((size_t)blockIdx.x * (a.m + 1) + l) * a.ES;
+}
+
+// ---- element phases ---------------------------------------------------------
+// Block solve of the owned black block k from the block-slot values vb[0..2M)
+// (already scaled): t = M^-1 v on the block.
+template <typename S>
+__device__ void block_solve(const GmresArgs<S>& a, const Smem<S>& s, int k, int ib, int e, const S* vb) {
+  const int M = a.g.M, n = a.g.n;
+  const S* X = mat_X(a, s, k, ib);
+  {
+    // r1 = p - X q, X = blockdiag(X_F), X_F column-major: P parts per row
+    int P = 1;
+    while (P * 2 * M <= (int)blockDim.x && P < 8) P *= 2;
+    const int t = threadIdx.x, r = t % M, part = t / M;
+    if (part < P) {
+      const int F = r / n, tt = r % n;
+      const S* xf = X + (size_t)F * n * n;
+      const S* xq = vb + M + F * n;
+      S acc = 0;
+      for (int c = part; c < n; c += P) acc += xf[c * n + tt] * xq[c];
+      s.red[part * M + r] = acc;
+    }
+    __syncthreads();
+    for (int i = t; i < M; i += blockDim.x) {
+      S sum = s.red[i];
+      for (int p = 1; p < P; ++p) sum += s.red[p * M + i];
+      s.r1[i] = vb[i] - sum;
+    }
+    __syncthreads();
+  }
+  gemv_split(mat_G(a, s, k, ib), M, s.r1, s.av, M, M, s.red);
+  gemv_split(mat_Tb(a, s, k, e), M, s.av, s.z, M, M, s.red);
+  for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
+    long long sl = block_slot(a.g, e, i);
+    if (sl < 0) continue;
+    a.t[sl] = i < M ? s.av[i] : (S)(vb[i] - s.z[i - M]);
+  }
+  __syncthreads();
+}
+
+// White element: y = S t on the black slots facing e, y = sc*v on e's slots,
+// c = Z^T y on e's interfaces (with_c).
+template <typename S>
+__device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, int k, int e, const S* v, double sc, bool with_c) {
+  const DevGeo& g = a.g;
+  const int M = g.M, n = g.n;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = ldcg(a.t + (size_t)e * M + i);
+  __syncthreads();
+  gemv_split(mat_Tw(a, s, k, e), M, s.p, s.z, M, M, s.red);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    S vo = (S)(sc * (double)ldcg(v + (size_t)e * M + i));
+    a.y[(size_t)e * M + i] = vo;
+    double ci = 0;
+    if (e2 >= 0) {
+      size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
+      S ys = ldcg(a.t + sl) + s.z[i];
+      a.y[sl] = ys;
+      ci = (double)vo + (double)ys;
+    }
+    s.cs[i] = ci;
+  }
+  __syncthreads();
+  if (with_c && threadIdx.x < 4) {
+    int F = threadIdx.x;
+    int j = dev_iface(g, e, F);
+    if (j >= 0) {
+      double sum = 0;
+      for (int tt = 0; tt < n; ++tt) sum += s.cs[F * n + tt];
+      a.c[j] = sum;
+    }
+  }
+  __syncthreads();
+}
+
+// Push form y = S (sc*v) for element e (Algorithm 1).
+template <typename S>
+__device__ void push_step(const GmresArgs<S>& a, const Smem<S>& s, int e, const S* v, double sc) {
+  const DevGeo& g = a.g;
+  const int M = g.M, n = g.n;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = (S)(sc * (double)ldcg(v + (size_t)e * M + i));
+  __syncthreads();
+  gemv_split(a.Tc + (size_t)e * M * M, M, s.p, s.z, M, M, s.red);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    int F = i / n, tt = i % n;
+    int e2 = dev_neighbour(g, e, F);
+    if (e2 >= 0) {
+      size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
+      a.y[sl] = (S)(sc * (double)ldcg(v + sl)) + s.z[i];
+    } else {
+      a.y[(size_t)e * M + i] = s.p[i];
+    }
+  }
+  __syncthreads();
+}
+
+// c_hat = H c: CTA c takes a contiguous range of rows; c is staged in shared
+// memory and P lanes split each row (H row-major: lanes read consecutive
+// columns), partial sums meet in warp shuffles.
+template <typename S>
+__device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
+  const int d = (int)a.g.d;
+  const int per = (d + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * per, r1 = min(d, r0 + per);
+  if (r0 >= r1) return;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s.cst[j] = __ldcg(a.c + j);
+  __syncthreads();
+  const int rows = r1 - r0;
+  int P = 32;
+  while (P > 1 && P * rows > 2 * (int)blockDim.x) P >>= 1;
+  const int lane = threadIdx.x % P, grp = threadIdx.x / P, ngrp = blockDim.x / P;
+  for (int rb = 0; rb < rows; rb += ngrp) {  // uniform trip count per warp
+    const int r = r0 + rb + grp;
+    double sum = 0;
+    if (r < r1) {
+      const double* hr = a.H + (size_t)r * d;
+      double s0 = 0, s1 = 0;
+      int j = lane;
+      for (; j + P < d; j += 2 * P) {
+        s0 += __ldg(hr + j) * s.cst[j];
+        s1 += __ldg(hr + j + P) * s.cst[j + P];
+      }
+      if (j < d) s0 += __ldg(hr + j) * s.cst[j];
+      sum = s0 + s1;
+    }
+    for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
+    if (lane == 0 && r < r1) a.chat[r] = sum;
+  }
+}
+
+// w = y - S Z chat for one slot (pull form); chat == nullptr gives w = y.
+template <typename S>
+__device__ __forceinline__ double deflate_slot_cg(const DevGeo& g, const S* y, const double* chat,
+                                                  const S* __restrict__ Rs, long long sl) {
+  const int M = g.M, n = g.n;
+  int e = (int)(sl / M), i = (int)(sl % M), F = i / n, t = i % n;
+  int e2 = dev_neighbour(g, e, F);
+  if (e2 < 0) return 0.0;
+  double ys = (double)ldcg(y + sl);
+  if (!chat) return ys;
+  double acc = __ldcg(chat + dev_iface(g, e, F));
+  const S* R = Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
+#pragma unroll
+  for (int G = 0; G < 4; ++G) {
+    int jj = dev_iface(g, e2, G);
+    if (jj >= 0) acc += (double)__ldg(R + G) * __ldcg(chat + jj);
+  }
+  return ys - acc;
+}
+
+// Dot products of the owned basis slice with vec (ES entries) for l < nl,
+// l == nl - 1 giving vec.vec: P lanes per l (P a power of two <= 32, P*nl <=
+// blockDim when possible) read consecutive entries; partial sums meet in warp
+// shuffles and are added atomically to out[l] (FP64, in L2).
+template <typename S>
+__device__ void owned_dots(const GmresArgs<S>& a, const Smem<S>& s, const S* vec, int nl, double* out) {
+  const int E = a.ES;
+  int P = 32;
+  while (P > 1 && P * nl > (int)blockDim.x) P >>= 1;
+  const int ngrp = blockDim.x / P, lane = threadIdx.x % P, grp = threadIdx.x / P;
+  for (int lb = 0; lb < nl; lb += ngrp) {  // uniform trip count per warp
+    const int l = lb + grp;
+    double sum = 0;
+    if (l < nl) {
+      const S* vl = (l == nl - 1) ? vec : basis(a, s, l);
+      double s0 = 0, s1 = 0;
+      int i = lane;
+      for (; i + P < E; i += 2 * P) {
+        s0 += (double)vl[i] * (double)vec[i];
+        s1 += (double)vl[i + P] * (double)vec[i + P];
+      }
+      if (i < E) s0 += (double)vl[i] * (double)vec[i];
+      sum = s0 + s1;
+    }
+    for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
+    if (l < nl && lane == 0 && sum != 0.0) atomicAdd(out + l, sum);
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
+  const int M2 = 2 * a.g.M;
+  int k = i / M2, ii = i % M2;
+  int ib = blockIdx.x + k * gridDim.x;
+  if (k >= a.nown_b || ib >= a.nblack) return -1;
+  return block_slot(a.g, a.black[ib], ii);
+}
+
+// op(sc * src) -> y (and c, chat).  With t_done the owners have already
+// written t = M^-1 v for their blocks.
+template <typename S>
+__device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, double sc, bool t_done,
+                         int& trace_n, unsigned& epoch) {
+  const DevGeo& g = a.g;
+  const int M = g.M, G = gridDim.x;
+  if (a.precond == 0) {
+    for (long long e = blockIdx.x; e < g.nel; e += G) push_step(a, s, (int)e, src, sc);
+    return grid_sync(a.bar, a.err, epoch);
+  }
+  if (!t_done) {
+    for (int k = 0; k < a.nown_b; ++k) {
+      int ib = blockIdx.x + k * G;
+      if (ib >= a.nblack) break;
+      int e = a.black[ib];
+      for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
+        long long sl = block_slot(g, e, i);
+        s.w[i] = sl >= 0 ? (S)(sc * (double)ldcg(src + sl)) : S(0);
+      }
+      __syncthreads();
+      block_solve(a, s, k, ib, e, s.w);
+    }
+  }
+  GM_TRACE(20);
+  if (!grid_sync(a.bar, a.err, epoch)) return false;
+  GM_TRACE(21);
+  for (int k = 0; k < a.nown_w; ++k) {
+    int iw = blockIdx.x + k * G;
+    if (iw >= a.nwhite) break;
+    white_step(a, s, k, a.white[iw], src, sc, a.precond == 2);
+  }
+  GM_TRACE(22);
+  if (!grid_sync(a.bar, a.err, epoch)) return false;
+  GM_TRACE(23);
+  if (a.precond == 2) {
+    coarse_rows(a, s);
+    GM_TRACE(24);
+    if (!grid_sync(a.bar, a.err, epoch)) return false;
+    GM_TRACE(25);
+  }
+  return true;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Smem<S> s = carve(a, smraw);
+  const DevGeo& g = a.g;
+  const int M = g.M, n = g.n, m = a.m;
+  const int ES = a.ES, G = gridDim.x;
+  const int m3 = m + 3;
+  int trace_n = 0;
+  unsigned epoch = 0;
+
+  // ---- resident copies of the owned matrices
+  if (a.mats_smem) {
+    for (int k = 0; k < a.nown_b; ++k) {
+      int ib = blockIdx.x + k * G;
+      if (ib >= a.nblack) break;
+      int e = a.black[ib];
+      S* dst = s.mats + (size_t)k * (2 * M * M + 4 * n * n);
+      for (int i = threadIdx.x; i < M * M; i += blockDim.x) {
+        dst[i] = a.Gc[(size_t)ib * M * M + i];
+        dst[M * M + i] = a.Tc[(size_t)e * M * M + i];
+      }
+      for (int i = threadIdx.x; i < 4 * n * n; i += blockDim.x) dst[2 * M * M + i] = a.Xc[(size_t)ib * 4 * n * n + i];
+    }
+    for (int k = 0; k < a.nown_w; ++k) {
+      int iw = blockIdx.x + k * G;
+      if (iw >= a.nwhite) break;
+      int e = a.white[iw];
+      S* dst = s.mats + (size_t)a.nown_b * (2 * M * M + 4 * n * n) + (size_t)k * M * M;
+      for (int i = threadIdx.x; i < M * M; i += blockDim.x) dst[i] = a.Tc[(size_t)e * M * M + i];
+    }
+  }
+
+  int total = 0, cycle = 0, jlast = 0;
+  bool converged = false, breakdown = false, nan = false;
+  double tolabs = 0, beta0 = 0, resid = 0;
+  __syncthreads();
+  while (true) {
+    double* accN = a.acc + (size_t)(2 * m) * m3;
+    // ---- cycle start: V[0] = rhs - op(x)
+    if (cycle > 0) {
+      if (!apply_op(a, s, a.x, 1.0, false, trace_n, epoch)) return;
+    }
+    {
+      S* v0 = basis(a, s, 0);
+      double nn = 0;
+      for (int i = threadIdx.x; i < ES; i += blockDim.x) {
+        long long sl = entry_slot(a, i);
+        S rv = 0;
+        if (sl >= 0) {
+          double r = (double)ldcg(a.rhs + sl);
+          if (cycle > 0) r -= deflate_slot_cg(g, a.y, a.precond == 2 ? a.chat : nullptr, a.Rs, sl);
+          rv = (S)r;
+          a.vglob[sl] = rv;
+        }
+        v0[i] = rv;
+        nn += (double)rv * (double)rv;
+      }
+      nn = warp_sum(nn);
+      if ((threadIdx.x & 31) == 0 && nn != 0.0) atomicAdd(accN, nn);
+    }
+    if (!grid_sync(a.bar, a.err, epoch)) return;
+    const double beta = sqrt(__ldcg(accN));
+    if (cycle == 0) {
+      beta0 = beta;
+      tolabs = a.tol * beta;
+    }
+    resid = beta;
+    if (!isfinite(beta)) { nan = true; break; }
+    if (beta <= tolabs || beta == 0.0) { converged = true; break; }
+    if (threadIdx.x == 0) {
+      s.gg[0] = beta;
+      s.invb[0] = 1.0 / beta;
+    }
+    __syncthreads();
+    int j = 0;
+    for (; j < m && total < a.maxit; ++j) {
+      double* accD = a.acc + (size_t)(2 * j) * m3;
+      double* accE = a.acc + (size_t)(2 * j + 1) * m3;
+      const double ivj = s.invb[j];
+      GM_TRACE(1);
+      // ---- A: finalize V[j] on the owned entries (j > 0), then block solves
+      S* vj = basis(a, s, j);
+      if (j > 0) {
+        for (int i = threadIdx.x; i < ES; i += blockDim.x) {
+          double r = (double)s.w2[i];
+          for (int l = 0; l < j; ++l) r -= s.hs2[l] * (double)basis(a, s, l)[i];
+          S rv = (S)r;
+          vj[i] = rv;
+          long long sl = entry_slot(a, i);
+          if (sl >= 0) a.vglob[sl] = rv;
+        }
+        __syncthreads();
+      }
+      if (a.precond == 0) {
+        if (!grid_sync(a.bar, a.err, epoch)) return;  // neighbours read v_j
+        if (!apply_op(a, s, a.vglob, ivj, false, trace_n, epoch)) return;
+      } else {
+        for (int k = 0; k < a.nown_b; ++k) {
+          int ib = blockIdx.x + k * G;
+          if (ib >= a.nblack) break;
+          for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) s.w[i] = (S)(ivj * (double)vj[k * 2 * M + i]);
+          __syncthreads();
+          block_solve(a, s, k, ib, a.black[ib], s.w);
+        }
+        if (!apply_op(a, s, a.vglob, ivj, true, trace_n, epoch)) return;
+      }
+      GM_TRACE(4);
+      // ---- D: w = y - S Z chat on owned entries; V^T w, ||w||^2
+      for (int i = threadIdx.x; i < ES; i += blockDim.x) {
+        long long sl = entry_slot(a, i);
+        s.w[i] = sl >= 0 ? (S)deflate_slot_cg(g, a.y, a.precond == 2 ? a.chat : nullptr, a.Rs, sl) : S(0);
+      }
+      __syncthreads();
+      owned_dots(a, s, s.w, j + 2, accD);
+      GM_TRACE(5);
+      if (!grid_sync(a.bar, a.err, epoch)) return;
+      GM_TRACE(6);
+      for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
+        double v = __ldcg(accD + l);
+        if (l <= j) {
+          v *= s.invb[l];
+          s.h1[l] = v;
+          s.hs1[l] = v * s.invb[l];
+        } else {
+          s.misc[0] = v;  // ||w||^2
+        }
+      }
+      __syncthreads();
+      // ---- E: w2 = w - V h1; V^T w2, ||w2||^2
+      for (int i = threadIdx.x; i < ES; i += blockDim.x) {
+        double r = (double)s.w[i];
+        for (int l = 0; l <= j; ++l) r -= s.hs1[l] * (double)basis(a, s, l)[i];
+        s.w2[i] = (S)r;
+      }
+      __syncthreads();
+      owned_dots(a, s, s.w2, j + 2, accE);
+      GM_TRACE(8);
+      if (!grid_sync(a.bar, a.err, epoch)) return;
+      GM_TRACE(9);
+      for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
+        double v = __ldcg(accE + l);
+        if (l <= j) {
+          v *= s.invb[l];
+          s.h2[l] = v;
+          s.hs2[l] = v * s.invb[l];
+        } else {
+          s.misc[1] = v;  // ||w2||^2
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) {  // ||h2||^2 and h1 + h2 in warp 0
+        double q = 0;
+        for (int l = threadIdx.x; l <= j; l += 32) {
+          q += s.h2[l] * s.h2[l];
+          s.col[l] = s.h1[l] + s.h2[l];
+        }
+        q = warp_sum(q);
+        if (threadIdx.x == 0) s.misc[5] = q;
+      }
+      __syncthreads();
+      // ---- Givens update, replicated in every CTA (serial chain in thread 0)
+      if (threadIdx.x == 0) {
+        double bsq = s.misc[1] - s.misc[5];
+        double ib = bsq > 0 ? rsqrt(bsq) : 0.0;
+        double bnext = bsq > 0 ? bsq * ib : 0.0;
+        for (int i = 0; i < j; ++i) {
+          double x0 = s.col[i], x1 = s.col[i + 1];
+          s.col[i] = s.gcs[i] * x0 + s.gsn[i] * x1;
+          s.col[i + 1] = -s.gsn[i] * x0 + s.gcs[i] * x1;
+        }
+        double hh = s.col[j] * s.col[j] + bnext * bnext;
+        double iden = hh > 0 ? rsqrt(hh) : 0.0;
+        double cc = hh > 0 ? s.col[j] * iden : 1.0, ss = bnext * iden;
+        s.gcs[j] = cc;
+        s.gsn[j] = ss;
+        s.col[j] = hh * iden;
+        s.gg[j + 1] = -ss * s.gg[j];
+        s.gg[j] = cc * s.gg[j];
+        s.invb[j + 1] = ib;
+        s.misc[2] = fabs(s.gg[j + 1]);
+        s.misc[3] = (bsq <= 1e-28 * s.misc[0]) ? 1.0 : 0.0;
+        s.misc[4] = bnext;
+        if (blockIdx.x == 0) {
+          double* Rc = a.gs->R + (size_t)j * (kMaxRestart + 1);
+          for (int l = 0; l <= j; ++l) Rc[l] = s.col[l];
+          a.gs->g[j] = s.gg[j];
+          a.gs->g[j + 1] = s.gg[j + 1];
+        }
+      }
+      __syncthreads();
+      GM_TRACE(13);
+      ++total;
+      resid = s.misc[2];
+      if (!isfinite(resid) || !isfinite(s.misc[4])) { nan = true; ++j; break; }
+      if (resid <= tolabs) { converged = true; ++j; break; }
+      if (s.misc[3] != 0.0) { breakdown = true; ++j; break; }
+    }
+    jlast = j;
+    if (nan) break;
+    // ---- end of cycle: y = R^-1 g (CTA 0), x += V diag(invb) y on owned entries
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const int m1 = kMaxRestart + 1;
+      for (int i = j - 1; i >= 0; --i) {
+        double sum = a.gs->g[i];
+        for (int k = i + 1; k < j; ++k) sum -= a.gs->R[(size_t)k * m1 + i] * a.gs->y[k];
+        a.gs->y[i] = sum / a.gs->R[(size_t)i * m1 + i];
+      }
+    }
+    // the accumulators are consumed: zero them for the next cycle
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)(2 * m + 1) * m3;
+         i += (size_t)G * blockDim.x)
+      a.acc[i] = 0.0;
+    if (!grid_sync(a.bar, a.err, epoch)) return;
+    for (int l = threadIdx.x; l < j; l += blockDim.x) s.hs1[l] = __ldcg(a.gs->y + l) * s.invb[l];
+    __syncthreads();
+    for (int i = threadIdx.x; i < ES; i += blockDim.x) {
+      long long sl = entry_slot(a, i);
+      if (sl < 0) continue;
+      double r = (double)ldcg(a.x + sl);
+      for (int l = 0; l < j; ++l) r += s.hs1[l] * (double)basis(a, s, l)[i];
+      a.x[sl] = (S)r;
+    }
+    if (!grid_sync(a.bar, a.err, epoch)) return;
+    ++cycle;
+    if (converged || breakdown || total >= a.maxit) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.gs->beta0 = beta0;
+    a.gs->tolabs = tolabs;
+    a.gs->resid = resid;
+    a.gs->j = total;
+    a.gs->converged = converged ? 1 : 0;
+    a.gs->breakdown = breakdown ? 1 : 0;
+    a.gs->nan = nan ? 1 : 0;
+    a.gs->scal[7] = cycle;
+    a.gs->scal[6] = jlast;
+  }
+}

@@ -5,8 +5,8 @@
 // faces W,E,S,N, face node t increasing along the face; slots on physical
 // boundary faces are kept at zero).  Every per-element kernel runs one CTA per
 // element (or per checkerboard block) and stages the element's small vectors
-// in shared memory; the element matrices are streamed once from HBM/L2 with
-// row-per-warp, lane-per-column coalesced loads.
+// in shared memory; the element matrices are stored column-major and read
+// once, coalesced across the threads that own consecutive rows.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -46,18 +46,56 @@ __device__ __forceinline__ S warp_sum(S v) {
   return v;
 }
 
-// y[row] = sum_col A[row*M + col] x[col] (A row-major in global memory, x and
-// y in shared memory); one warp per row, lanes stride the columns.
-template <typename S, typename Acc>
-__device__ __forceinline__ void gemv_rows(const S* __restrict__ A, const S* x, Acc* y, int M) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int row = warp; row < M; row += nw) {
-    const S* a = A + (size_t)row * M;
-    Acc acc = 0;
-    for (int c = lane; c < M; c += 32) acc += (Acc)__ldg(a + c) * (Acc)x[c];
-    acc = warp_sum(acc);
-    if (lane == 0) y[row] = acc;
+// y[r] = sum_c A[c*M + r] x[c] for r < M: A column-major (shared or global
+// memory; consecutive threads read consecutive rows), x in shared memory.
+// One thread per row with four independent partial sums: every FP64 product
+// is a plain FMA (no warp-shuffle reduction adds on the scarce FP64 pipe).
+template <typename S>
+__device__ __forceinline__ void gemv_cm(const S* A, const S* x, S* y, int M) {
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    S s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int c = 0;
+    for (; c + 3 < M; c += 4) {
+      s0 += A[(size_t)c * M + r] * x[c];
+      s1 += A[(size_t)(c + 1) * M + r] * x[c + 1];
+      s2 += A[(size_t)(c + 2) * M + r] * x[c + 2];
+      s3 += A[(size_t)(c + 3) * M + r] * x[c + 3];
+    }
+    for (; c < M; ++c) s0 += A[(size_t)c * M + r] * x[c];
+    y[r] = (s0 + s1) + (s2 + s3);
   }
+}
+
+// y[r] = sum_{c < cols} A[c*ld + r] x[c] for r < rows, A column-major with
+// leading dimension ld.  The CTA splits the columns into P = blockDim / rows
+// parts (P <= 8, a power of two): thread (part, r) with r fastest reads
+// consecutive rows (conflict-free in shared memory, coalesced in global), and
+// the P partial sums meet in the scratch buffer red (>= P*rows entries).  FP64
+// work thus spreads over all warps of the CTA, with P-1 adds per row on top
+// of the rows*cols FMAs.  Ends with __syncthreads.
+template <typename S>
+__device__ __forceinline__ void gemv_split(const S* A, int ld, const S* x, S* y, int rows, int cols, S* red,
+                                           bool accumulate = false, S alpha = S(1)) {
+  int P = 1;
+  while (P * 2 * rows <= (int)blockDim.x && P < 8) P *= 2;
+  const int t = threadIdx.x, r = t % rows, part = t / rows;
+  if (part < P) {
+    S s0 = 0, s1 = 0;
+    int c = part;
+    for (; c + P < cols; c += 2 * P) {
+      s0 += A[(size_t)c * ld + r] * x[c];
+      s1 += A[(size_t)(c + P) * ld + r] * x[c + P];
+    }
+    if (c < cols) s0 += A[(size_t)c * ld + r] * x[c];
+    red[part * rows + r] = s0 + s1;
+  }
+  __syncthreads();
+  for (int i = t; i < rows; i += blockDim.x) {
+    S sum = red[i];
+    for (int p = 1; p < P; ++p) sum += red[p * rows + i];
+    y[i] = accumulate ? y[i] + alpha * sum : sum;
+  }
+  __syncthreads();
 }
 
 }  // namespace smpm

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -36,6 +37,8 @@ thread_local std::string g_last_error;
 
 constexpr int kSlotsPerBlock = 256;   // slots per CTA in the vector kernels
 constexpr int kElemThreads = 256;     // threads per element CTA
+constexpr int kTraceCap = 1 << 16;    // entries of the optional phase trace
+constexpr int kGmresThreads = 256;    // threads per CTA of the persistent GMRES kernel
 
 struct GState {
   double tolabs, beta0, beta, wnorm0sq, resid;
@@ -47,6 +50,7 @@ struct GState {
   double y[kMaxRestart];
   double scal[8];
 };
+
 
 // ------------------------------------------------------------ reductions
 __device__ bool last_block_done(unsigned* cnt) {
@@ -272,7 +276,7 @@ __global__ void k_schur(DevGeo g, const S* __restrict__ T, const S* __restrict__
   const int e = blockIdx.x, M = g.M, n = g.n;
   for (int i = threadIdx.x; i < M; i += blockDim.x) ve[i] = v[(size_t)e * M + i];
   __syncthreads();
-  gemv_rows<S, S>(T + (size_t)e * M * M, ve, z, M);
+  gemv_cm(T + (size_t)e * M * M, ve, z, M);
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     int F = i / n, t = i % n;
@@ -309,15 +313,15 @@ __global__ void k_black(DevGeo g, const int* __restrict__ black, const S* __rest
   const S* Xb = X + (size_t)ib * 4 * n * n;
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     int F = i / n, tt = i % n;
-    const S* xr = Xb + (size_t)(F * n + tt) * n;
+    const S* xf = Xb + (size_t)F * n * n;  // X_F column-major
     S s = p[i];
-    for (int s2 = 0; s2 < n; ++s2) s -= __ldg(xr + s2) * q[F * n + s2];
+    for (int s2 = 0; s2 < n; ++s2) s -= __ldg(xf + s2 * n + tt) * q[F * n + s2];
     r1[i] = s;
   }
   __syncthreads();
-  gemv_rows<S, S>(G + (size_t)ib * M * M, r1, a, M);
+  gemv_cm(G + (size_t)ib * M * M, r1, a, M);
   __syncthreads();
-  gemv_rows<S, S>(T + (size_t)e * M * M, a, z, M);
+  gemv_cm(T + (size_t)e * M * M, a, z, M);
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     int F = i / n, tt = i % n;
@@ -340,7 +344,7 @@ __global__ void k_white(DevGeo g, const int* __restrict__ white, const S* __rest
   double* cs = reinterpret_cast<double*>(z + M + (M & 1));
   for (int i = threadIdx.x; i < M; i += blockDim.x) tb[i] = t[(size_t)e * M + i];
   __syncthreads();
-  gemv_rows<S, S>(T + (size_t)e * M * M, tb, z, M);
+  gemv_cm(T + (size_t)e * M * M, tb, z, M);
   __syncthreads();
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     int F = i / n, tt = i % n;
@@ -445,162 +449,6 @@ __global__ void k_defl_dots(DevGeo g, const S* __restrict__ y, const double* __r
   }
 }
 
-// Second Gram-Schmidt pass: w2 = w - V h1, h2 = V^T w2.
-template <typename S>
-__global__ void k_cgs2(long long kp, const S* __restrict__ V, int nvec, const S* __restrict__ w, S* w2, double* part,
-                       unsigned* cnt, GState* gs) {
-  __shared__ double wsh[kSlotsPerBlock];
-  __shared__ double hs[kMaxRestart + 2];
-  for (int l = threadIdx.x; l < nvec; l += blockDim.x) hs[l] = gs->h1[l];
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * blockDim.x, s = base + threadIdx.x;
-  double ws = 0;
-  if (s < kp) {
-    double acc = (double)w[s];
-    for (int l = 0; l < nvec; ++l) acc -= hs[l] * (double)__ldg(V + (size_t)l * kp + s);
-    S wv = (S)acc;
-    w2[s] = wv;
-    ws = (double)wv;
-  }
-  wsh[threadIdx.x] = ws;
-  __syncthreads();
-  block_multidot(V, kp, nvec, base, wsh, false, part);
-  if (last_block_done(cnt)) {
-    finalize_partials(part, gridDim.x, nvec, gs->h2);
-    __syncthreads();
-    if (threadIdx.x == 0) *cnt = 0;
-  }
-}
-
-// Third pass: v_{j+1} = w2 - V h2 (stored unnormalised in V[nvec]), its norm,
-// and the FP64 Givens update of Hessenberg column j = nvec - 1.
-template <typename S>
-__global__ void k_cgs3(long long kp, S* V, int nvec, const S* __restrict__ w2, double* part, unsigned* cnt,
-                       GState* gs) {
-  __shared__ double hs[kMaxRestart + 2];
-  __shared__ double red[32];
-  for (int l = threadIdx.x; l < nvec; l += blockDim.x) hs[l] = gs->h2[l];
-  __syncthreads();
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc2 = 0;
-  if (s < kp) {
-    double acc = (double)w2[s];
-    for (int l = 0; l < nvec; ++l) acc -= hs[l] * (double)V[(size_t)l * kp + s];
-    S wv = (S)acc;
-    V[(size_t)nvec * kp + s] = wv;
-    acc2 = (double)wv * (double)wv;
-  }
-  acc2 = warp_sum(acc2);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-  }
-  if (last_block_done(cnt)) {
-    __shared__ double bsq;
-    finalize_partials(part, gridDim.x, 1, &bsq);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      *cnt = 0;
-      const int j = nvec - 1, m1 = kMaxRestart + 1;
-      double beta = sqrt(bsq);
-      double* col = gs->R + (size_t)j * m1;
-      for (int l = 0; l <= j; ++l) col[l] = gs->h1[l] + gs->h2[l];
-      double hsub = beta;
-      for (int i = 0; i < j; ++i) {
-        double a = col[i], b = col[i + 1];
-        col[i] = gs->cs[i] * a + gs->sn[i] * b;
-        col[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
-      }
-      double den = hypot(col[j], hsub);
-      double c = den > 0 ? col[j] / den : 1.0, sn = den > 0 ? hsub / den : 0.0;
-      gs->cs[j] = c;
-      gs->sn[j] = sn;
-      col[j] = den;
-      gs->g[j + 1] = -sn * gs->g[j];
-      gs->g[j] = c * gs->g[j];
-      gs->resid = fabs(gs->g[j + 1]);
-      gs->beta = beta;
-      gs->j = j + 1;
-      gs->converged = gs->resid <= gs->tolabs;
-      gs->breakdown = beta <= 1e-14 * sqrt(gs->wnorm0sq);
-      gs->nan = !(isfinite(gs->resid) && isfinite(beta));
-    }
-  }
-}
-
-template <typename S>
-__global__ void k_scale_vec(long long kp, S* v, const GState* gs) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double beta = gs->beta;
-  if (s < kp && beta > 0) v[s] = (S)((double)v[s] / beta);
-}
-
-// ||x||: initialises a GMRES cycle (g = beta e_1, j = 0); with set_tol the
-// absolute target tol * beta is fixed (first cycle only).
-template <typename S>
-__global__ void k_cycle_init(long long kp, S* v0, double* part, unsigned* cnt, GState* gs, double tol, int set_tol) {
-  __shared__ double red[32];
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double acc = 0;
-  if (s < kp) acc = (double)v0[s] * (double)v0[s];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-  }
-  if (last_block_done(cnt)) {
-    __shared__ double bsq;
-    finalize_partials(part, gridDim.x, 1, &bsq);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      *cnt = 0;
-      double beta = sqrt(bsq);
-      if (set_tol) {
-        gs->beta0 = beta;
-        gs->tolabs = tol * beta;
-      }
-      gs->beta = beta;
-      gs->g[0] = beta;
-      gs->j = 0;
-      gs->resid = beta;
-      gs->converged = beta <= gs->tolabs;
-      gs->breakdown = 0;
-      gs->nan = !isfinite(beta);
-    }
-  }
-}
-
-// Back substitution R y = g for the j columns of the current cycle.
-__global__ void k_trisolve(GState* gs) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int j = gs->j, m1 = kMaxRestart + 1;
-  for (int i = j - 1; i >= 0; --i) {
-    double s = gs->g[i];
-    for (int k = i + 1; k < j; ++k) s -= gs->R[(size_t)k * m1 + i] * gs->y[k];
-    gs->y[i] = s / gs->R[(size_t)i * m1 + i];
-  }
-}
-
-// x += V[0..j) y
-template <typename S>
-__global__ void k_update(long long kp, const S* __restrict__ V, const GState* gs, S* x) {
-  __shared__ double ys[kMaxRestart];
-  const int j = gs->j;
-  for (int l = threadIdx.x; l < j; l += blockDim.x) ys[l] = gs->y[l];
-  __syncthreads();
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (s >= kp) return;
-  double acc = (double)x[s];
-  for (int l = 0; l < j; ++l) acc += ys[l] * (double)V[(size_t)l * kp + s];
-  x[s] = (S)acc;
-}
-
 // out = a - b
 template <typename S>
 __global__ void k_sub(long long n, const S* __restrict__ a, const S* __restrict__ b, S* out) {
@@ -620,6 +468,8 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
   double cb = chat_b ? chat_b[j] : 0.0;
   x[s] = t[s] - (chat ? chat[j] : 0.0) + cb;
 }
+
+#include "smpm_gmres.cuh"
 
 // ------------------------------------------------------------- host side
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -642,9 +492,19 @@ struct smpm_handle_s {
   double *wb = nullptr, *wbS = nullptr, *wV = nullptr, *wt = nullptr, *wy = nullptr, *ww = nullptr;
   double *ww2 = nullptr, *wx = nullptr, *wrg = nullptr, *wtmp = nullptr;
   double *wc = nullptr, *wchat = nullptr, *wcb = nullptr, *wchatb = nullptr;
-  double *wpart = nullptr;
+  double *wpart = nullptr, *winvb = nullptr;
   unsigned* wcnt = nullptr;
+  unsigned* wbar = nullptr;
+  int* werr = nullptr;
   GState* wgs = nullptr;
+  struct {
+    int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0;
+    size_t smem = 0;
+  } gm;  // launch shape of the persistent GMRES kernel
+  double* wvown = nullptr;
+  double* wacc = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the GMRES kernel of each solve
+  long long* wtrace = nullptr;                // phase trace buffer (SMPM_TRACE set)
   // staging for the host-pointer entry point
   double *sf = nullptr, *sg = nullptr, *su = nullptr;
   size_t sf_n = 0;
@@ -694,9 +554,21 @@ smpm_status upload(smpm_handle h, P** p, const std::vector<P>& src, cudaStream_t
 void free_all(smpm_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  h->ev0 = h->ev1 = nullptr;
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// count square blocks of size b x b, each transposed (row-major -> column-major)
+std::vector<double> transpose_blocks(const std::vector<double>& src, int b, size_t count) {
+  std::vector<double> out(src.size());
+  for (size_t k = 0; k < count; ++k)
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) out[k * b * b + (size_t)j * b + i] = src[k * b * b + (size_t)i * b + j];
+  return out;
+}
 
 size_t elem_smem(int n) { return 3 * (size_t)n * n * sizeof(double); }
 
@@ -763,22 +635,25 @@ smpm_status launch_axpy(smpm_handle h, const double* x, const double* alpha, dou
   return SMPM_OK;
 }
 
-// y = op(v) for the GMRES of the chosen algorithm, followed by the first
-// Gram-Schmidt pass against V[0..nvec) (nvec < 0: no dots).  Output in w.
-smpm_status apply_gmres_op(smpm_handle h, const double* v, int nvec, double* w, cudaStream_t st) {
-  smpm_status s;
-  switch (h->opts.precond) {
-    case 0:
-      if ((s = launch_schur(h, v, h->wy, st))) return s;
-      return launch_defl(h, h->wy, nullptr, nvec, w, st);
-    case 1:
-      if ((s = launch_precond(h, v, h->wt, h->wy, nullptr, st))) return s;
-      return launch_defl(h, h->wy, nullptr, nvec, w, st);
-    default:
-      if ((s = launch_precond(h, v, h->wt, h->wy, h->wc, st))) return s;
-      if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
-      return launch_defl(h, h->wy, h->wchat, nvec, w, st);
+// SMPM_TRACE: per-tag mean SM cycles between consecutive trace points of CTA 0.
+smpm_status print_trace(smpm_handle h, cudaStream_t st) {
+  std::vector<long long> tr(kTraceCap);
+  CU(cudaMemcpyAsync(tr.data(), h->wtrace, kTraceCap * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  double sum[64] = {0};
+  long long cnt[64] = {0};
+  for (int i = 0; i + 3 < kTraceCap && tr[i + 2] != 0; i += 2) {
+    int tag = (int)tr[i];
+    if (tag >= 0 && tag < 64) {
+      sum[tag] += (double)(tr[i + 3] - tr[i + 1]);
+      cnt[tag] += 1;
+    }
   }
+  std::fprintf(stderr, "[smpm trace] mean SM cycles from tag to next trace point (CTA 0)\n");
+  for (int t = 0; t < 64; ++t)
+    if (cnt[t]) std::fprintf(stderr, "  tag %2d  n %5lld  cycles %10.0f\n", t, cnt[t], sum[t] / cnt[t]);
+  CU(cudaMemsetAsync(h->wtrace, 0, kTraceCap * sizeof(long long), st));
+  return SMPM_OK;
 }
 
 smpm_status read_state(smpm_handle h, GState* hs, cudaStream_t st) {
@@ -819,54 +694,54 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   } else {
     CU(cudaMemcpyAsync(h->wrg, h->wbS, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
+  // x_1 := GMRES(op, rhs): one persistent cooperative launch (smpm_gmres.cuh)
   CU(cudaMemsetAsync(h->wx, 0, kp * sizeof(double), st));
-  CU(cudaMemcpyAsync(h->wV, h->wrg, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  k_cycle_init<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wpart, h->wcnt, h->wgs, tol, 1);
-  CHECK_LAUNCH();
+  CU(cudaMemsetAsync(h->wt, 0, kp * sizeof(double), st));
+  CU(cudaMemsetAsync(h->wy, 0, kp * sizeof(double), st));
+  CU(cudaMemsetAsync(h->werr, 0, sizeof(int), st));
+  CU(cudaMemsetAsync(h->wbar, 0, 2 * sizeof(unsigned), st));
+  CU(cudaMemsetAsync(h->wacc, 0, (size_t)(2 * m + 1) * (m + 3) * sizeof(double), st));
+  CU(cudaEventRecord(h->ev0, st));
+  {
+    GmresArgs<double> a;
+    a.g = g;
+    a.black = h->dblack;
+    a.white = h->dwhite;
+    a.nblack = (int)h->f.black.size();
+    a.nwhite = (int)h->f.white.size();
+    a.Tc = h->dT; a.Gc = h->dG; a.Xc = h->dX; a.Rs = h->dRs; a.H = h->dH;
+    a.vglob = h->wV; a.vown = h->wvown; a.t = h->wt; a.y = h->wy;
+    a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg; a.x = h->wx;
+    a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
+    a.precond = h->opts.precond; a.m = m; a.maxit = h->opts.maxit; a.tol = tol;
+    a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
+    a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
+    a.trace = h->wtrace;
+    a.trace_cap = h->wtrace ? kTraceCap : 0;
+    void* args[] = {&a};
+    CU(cudaLaunchCooperativeKernel((const void*)k_gmres<double>, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                   h->gm.smem, st));
+    CHECK_LAUNCH();
+  }
+  CU(cudaEventRecord(h->ev1, st));
+  if (h->wtrace) print_trace(h, st);
   GState hs;
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, h->werr, sizeof(int), cudaMemcpyDeviceToHost, st));
   if ((s = read_state(h, &hs, st))) return s;
-  int total = 0;
-  bool conv = hs.converged || hs.beta0 == 0.0;
-  bool stop = conv;
-  if (hs.nan) return fail(SMPM_ENAN, "non-finite right-hand side");
-  while (!stop) {
-    k_scale_vec<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wgs);
-    CHECK_LAUNCH();
-    int j = 0;
-    for (; j < m && total < h->opts.maxit; ++j) {
-      double* vj = h->wV + (size_t)j * kp;
-      if ((s = apply_gmres_op(h, vj, j + 1, h->ww, st))) return s;
-      k_cgs2<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, j + 1, h->ww, h->ww2, h->wpart, h->wcnt, h->wgs);
-      CHECK_LAUNCH();
-      k_cgs3<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, j + 1, h->ww2, h->wpart, h->wcnt, h->wgs);
-      CHECK_LAUNCH();
-      ++total;
-      if ((s = read_state(h, &hs, st))) return s;
-      if (hs.nan) return fail(SMPM_ENAN, "non-finite value in the Arnoldi process");
-      if (hs.converged || hs.breakdown) { ++j; break; }
-      k_scale_vec<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV + (size_t)(j + 1) * kp, h->wgs);
-      CHECK_LAUNCH();
-    }
-    k_trisolve<<<1, 32, 0, st>>>(h->wgs);
-    CHECK_LAUNCH();
-    k_update<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wgs, h->wx);
-    CHECK_LAUNCH();
-    conv = hs.converged;
-    if (conv || hs.breakdown || total >= h->opts.maxit) break;
-    // restart: r = rhs - op(x)
-    ++R.restarts;
-    if ((s = apply_gmres_op(h, h->wx, -1, h->ww, st))) return s;
-    k_sub<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wrg, h->ww, h->wV);
-    CHECK_LAUNCH();
-    k_cycle_init<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wV, h->wpart, h->wcnt, h->wgs, tol, 0);
-    CHECK_LAUNCH();
-    if ((s = read_state(h, &hs, st))) return s;
-    if (hs.converged) { conv = true; break; }
+  if (herr) return fail(SMPM_ETIMEOUT, "grid barrier of the GMRES kernel timed out");
+  if (hs.nan) return fail(SMPM_ENAN, "non-finite value in the right-hand side or the Arnoldi process");
+  const int total = hs.j;
+  double cycles_d = 0;
+  CU(cudaMemcpy(&cycles_d, reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal) + 7 * sizeof(double),
+                sizeof(double), cudaMemcpyDeviceToHost));
+  R.restarts = cycles_d > 1 ? (int)cycles_d - 1 : 0;
+  {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    R.gmres_ms = ms;
   }
-  if (hs.breakdown && !conv) {
-    // a happy breakdown solves the system exactly in the Krylov space
-    conv = true;
-  }
+  bool conv = hs.converged || hs.beta0 == 0.0 || hs.breakdown;
   R.iterations = total;
   R.converged = conv ? 1 : 0;
   R.gmres_relres = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
@@ -996,6 +871,9 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
       !(opts.robin_scale > 0))
     return fail(SMPM_EINVAL, "bad solver options");
   if (h->g.nel < 2) return fail(SMPM_ENOINTERFACE, "the Schur method needs mx*my >= 2 (one interface at least)");
+  if (h->g.d < 2 && opts.precond > 0)
+    return fail(SMPM_EINVAL, "with a single interface the only block-Jacobi block is all of the singular S; "
+                             "use precond = 0");
   cudaStream_t st = as_stream(stream);
   free_all(h);
   h->factored = false;
@@ -1011,8 +889,11 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   dg.tau_x = h->f.tau_x; dg.tau_y = h->f.tau_y; dg.p_x = h->f.p_x; dg.p_y = h->f.p_y;
   dg.sx = 2.0 / g.hx; dg.sy = 2.0 / g.hy;
   smpm_status s;
-  if ((s = upload(h, &h->dT, h->f.T, st)) || (s = upload(h, &h->dRs, h->f.Rs, st)) ||
-      (s = upload(h, &h->dG, h->f.G, st)) || (s = upload(h, &h->dX, h->f.X, st)) ||
+  // device copies of T_e, G_b and the X_F blocks are column-major
+  std::vector<double> Tc = transpose_blocks(h->f.T, g.M, g.nel), Gc = transpose_blocks(h->f.G, g.M, h->f.black.size()),
+                      Xc = transpose_blocks(h->f.X, g.n, 4 * h->f.black.size());
+  if ((s = upload(h, &h->dT, Tc, st)) || (s = upload(h, &h->dRs, h->f.Rs, st)) ||
+      (s = upload(h, &h->dG, Gc, st)) || (s = upload(h, &h->dX, Xc, st)) ||
       (s = upload(h, &h->dH, h->f.H, st)) || (s = upload(h, &h->dfdx, h->f.fdx, st)) ||
       (s = upload(h, &h->dfdy, h->f.fdy, st)) || (s = upload(h, &h->dD, h->f.D, st)) ||
       (s = upload(h, &h->duL, h->f.uL, st)) || (s = upload(h, &h->duS, h->f.uS, st)) ||
@@ -1026,11 +907,49 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
       (s = dalloc(h, &h->ww2, kp)) || (s = dalloc(h, &h->wx, kp)) || (s = dalloc(h, &h->wrg, kp)) ||
       (s = dalloc(h, &h->wtmp, kp)) || (s = dalloc(h, &h->wc, d)) || (s = dalloc(h, &h->wchat, d)) ||
       (s = dalloc(h, &h->wcb, d)) || (s = dalloc(h, &h->wchatb, d)) ||
-      (s = dalloc(h, &h->wpart, (size_t)(kMaxRestart + 3) * std::max<size_t>(nbs, 1024))) ||
-      (s = dalloc(h, &h->wcnt, 8)) || (s = dalloc(h, &h->wgs, 1)))
+      (s = dalloc(h, &h->wpart, (size_t)3 * (kMaxRestart + 3) * std::max<size_t>(nbs, 1024))) ||
+      (s = dalloc(h, &h->wcnt, 8)) || (s = dalloc(h, &h->wgs, 1)) || (s = dalloc(h, &h->winvb, kMaxRestart + 2)) ||
+      (s = dalloc(h, &h->wbar, 2)) || (s = dalloc(h, &h->werr, 1)))
     return s;
   CU(cudaMemsetAsync(h->wcnt, 0, 8 * sizeof(unsigned), st));
-  CU(cudaMemsetAsync(h->wgs, 0, sizeof(GState), st));
+  CU(cudaMemsetAsync(h->wbar, 0, 2 * sizeof(unsigned), st));
+  CU(cudaEventCreate(&h->ev0));
+  CU(cudaEventCreate(&h->ev1));
+  if (std::getenv("SMPM_TRACE")) {
+    if ((s = dalloc(h, &h->wtrace, kTraceCap))) return s;
+    CU(cudaMemsetAsync(h->wtrace, 0, kTraceCap * sizeof(long long), st));
+  }
+  {
+    // persistent GMRES kernel: one CTA per SM at most (all CTAs co-resident);
+    // CTA c owns blocks c, c+G, ... and keeps their matrices and its basis
+    // slice in shared memory when they fit.
+    int dev = 0, sms = 0, smem_optin = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int nb = (int)h->f.black.size(), nw = (int)h->f.white.size();
+    auto& gm = h->gm;
+    gm.grid = std::max(1, std::min(sms, std::max(nb, nw)));
+    gm.nown_b = (nb + gm.grid - 1) / gm.grid;
+    gm.nown_w = (nw + gm.grid - 1) / gm.grid;
+    gm.ES = 2 * g.M * gm.nown_b;
+    if (gm.ES % 2 == 0) gm.ES += 1;
+    const int m = opts.restart;
+    gm.basis_smem = gm.mats_smem = 1;
+    auto need = [&]() {
+      return gmres_smem_bytes<double>(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, gm.basis_smem, gm.mats_smem, g.d);
+    };
+    if (need() > (size_t)smem_optin) gm.mats_smem = 0;
+    if (need() > (size_t)smem_optin) gm.basis_smem = 0;
+    if (need() > (size_t)smem_optin) return fail(SMPM_EINVAL, "restart length too large for the GMRES kernel");
+    gm.smem = need();
+    CU(cudaFuncSetAttribute(k_gmres<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem));
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<double>, kGmresThreads, gm.smem));
+    if (per_sm < 1) return fail(SMPM_ECUDA, "the GMRES kernel does not fit on an SM");
+    if ((s = dalloc(h, &h->wacc, (size_t)(2 * m + 1) * (m + 3)))) return s;
+    if (!gm.basis_smem && (s = dalloc(h, &h->wvown, (size_t)gm.grid * (m + 1) * gm.ES))) return s;
+  }
   CU(cudaStreamSynchronize(st));
   h->factored = true;
   return SMPM_OK;

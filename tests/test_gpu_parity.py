@@ -16,8 +16,8 @@ from oracle.smpm import SMPMGrid
 from oracle.schur import SchurSystem
 from oracle import methods
 
-GRIDS = [(2, 2, 8, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (5, 4, 7, 1.0, 1.0), (2, 1, 6, 1.0, 1.0), (1, 3, 4, 1.0, 2.0),
-         (6, 5, 2, 1.0, 1.0)]
+GRIDS = [(2, 2, 8, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (5, 4, 7, 1.0, 1.0), (3, 1, 6, 1.0, 1.0), (1, 3, 4, 1.0, 2.0),
+         (6, 5, 2, 1.0, 1.0), (9, 7, 5, 1.0, 1.0)]
 
 
 def dev(a):
@@ -152,6 +152,22 @@ def test_host_entry_and_batch(built):
         assert rel(uh[k * og.r:(k + 1) * og.r], uo) < 1e-9
 
 
+def test_single_interface_grid(built):
+    """2 x 1 elements: one interface, so the only block-Jacobi block is the
+    whole (singular) S; block-Jacobi is refused, Algorithm 1 still solves."""
+    lg = Grid(2, 1, 6)
+    with pytest.raises(B.SmpmError) as ei:
+        lg.factor(precond=2)
+    assert ei.value.status == B.SMPM_EINVAL
+    lg.factor(precond=0, tol=1e-12)
+    og = SMPMGrid(2, 1, 6)
+    osys_u = methods.direct_solve(og, og.assemble_L(), methods.left_null_L_dense(og.assemble_L())[0],
+                                  og.rhs(inputs.white_noise(og.r, 3)))
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    lg.solve(dev(inputs.white_noise(og.r, 3)), u)
+    assert rel(host(u), osys_u) < 1e-10
+
+
 def test_degenerate_inputs(built):
     lg = Grid(3, 3, 5)
     lg.factor()
@@ -163,9 +179,13 @@ def test_degenerate_inputs(built):
     with pytest.raises(B.SmpmError) as ei:
         lg.solve(f, u)
     assert ei.value.status == B.SMPM_ENAN
-    # a constant right-hand side is removed by the u_L projection up to rounding
-    rep = lg.solve(torch.ones(lg.r, dtype=torch.float64, device="cuda"), u, allow_notconv=True)[0]
-    assert float(u.abs().max()) < 1e-6
+    # a constant f is not in the left null space (u_L is not constant): its
+    # projected part gives a genuine solution, the oracle's
+    og = SMPMGrid(3, 3, 5)
+    osys = SchurSystem(og)
+    rep = lg.solve(torch.ones(lg.r, dtype=torch.float64, device="cuda"), u)[0]
+    uo, _ = methods.algorithm3(osys, np.ones(og.r))
+    assert rel(host(u), uo) < 1e-9
 
 
 @pytest.mark.slow
