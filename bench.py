@@ -249,6 +249,8 @@ def run_ours(args):
     per_step_fixed_flops = 2 * (M * M * (nel + nblack) + 4 * n * n * nblack + d * d)
     per_step_fixed_bytes = 8 * (M * M * (nel + nblack) + 4 * n * n * nblack + d * d + 10 * kp)
     tot_flops = tot_bytes = tot_ms = 0.0
+    pre_ms = sum(r_["pre_ms"] for r_ in reps_timed) / len(reps_timed)
+    post_ms = sum(r_["post_ms"] for r_ in reps_timed) / len(reps_timed)
     for r_ in reps_timed:
         J, m = r_["iterations"], W["restart"]
         cyc = [m] * (J // m) + ([J % m] if J % m else [])
@@ -282,7 +284,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, **W, "precision": "fp64", "precond": "block-Jacobi + deflation",
                        "l2": "flushed between steps (512 MiB write, not timed)", "factor_s": round(factor_s, 3),
-                       "gmres_iterations": iters[-1], "wall_s": round(wall, 3)},
+                       "gmres_iterations": iters[-1], "wall_s": round(wall, 3),
+                       "device_ms": {"pre": round(pre_ms, 4), "gmres": round(tot_ms / len(reps_timed), 4),
+                                     "post": round(post_ms, 4)}},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},

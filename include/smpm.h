@@ -74,6 +74,8 @@ typedef struct {
   double schur_relres;   /* ||b_S - S x_S|| / ||b_S|| recomputed in FP64          */
   int launches;          /* CUDA kernels launched by this solve                  */
   double gmres_ms;       /* device time of the GMRES kernel (CUDA events)        */
+  double pre_ms;         /* device time of the right-hand-side kernel            */
+  double post_ms;        /* device time of the assembly/recovery kernel          */
 } smpm_report;
 
 /* Fill o with the defaults listed above. */

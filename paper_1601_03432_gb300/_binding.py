@@ -36,7 +36,8 @@ class SmpmOpts(ctypes.Structure):
 class SmpmReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("converged", ctypes.c_int), ("gmres_relres", ctypes.c_double), ("schur_relres", ctypes.c_double),
-                ("launches", ctypes.c_int), ("gmres_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int), ("gmres_ms", ctypes.c_double),
+                ("pre_ms", ctypes.c_double), ("post_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,0 +1,278 @@
+// Cooperative kernels around the GMRES kernel (FP64): the right-hand side
+// steps before it and the assembly/recovery steps after it, each one launch
+// with grid barriers between its phases.  Ownership follows smpm_gmres.cuh:
+// CTA c owns the checkerboard blocks and white elements c, c+G, ..., and for
+// node-level work the elements e = c, c+G, ...
+//
+// k_pre (Algorithm 3 steps 1-3 and the GMRES right-hand side):
+//   P1  b = f + tau g on the owned elements; u_L^T b accumulated
+//   P2  b <- b - u_L (u_L^T b); w = A_e^-1 b_e (fast diagonalisation); the
+//       Robin fluxes of w are pushed into the neighbours' facing slots
+//       (b_S = B A^-1 b); the same pass accumulates u_S^T b_S and, per face,
+//       the interface sums Z^T b_S
+//   P3  b_S <- b_S - u_S (u_S^T b_S) enters through Z^T b_S - (u_S^T b_S) Z^T u_S;
+//       c_hat_b = C^+ Z^T b_S (coarse rows)
+//   P4  owner entries: b_S projected in place, rhs = P b_S = b_S - S Z c_hat_b
+// k_post (steps 5-9 and the zero-mean normalisation):
+//   Q1  t = M^-1 x on the owned blocks
+//   Q2  white elements: y = S t, c = Z^T y
+//   Q3  c_hat = C^+ c
+//   Q4  owner entries: x_S = t - Z (c_hat - c_hat_b)       [Eq. deflated_schur]
+//   Q5  owned elements: u_e = A_e^-1 (b_e - E_e x_S); the pushed products
+//       T_e x_S also give the true residual ||b_S - S x_S||^2; GLL-weighted
+//       mean of u accumulated
+//   Q6  u <- u - mean
+#pragma once
+// Included inside the anonymous namespace of smpm_solver.cu.
+
+struct PrePostArgs {
+  GmresArgs<double> ga;  // geometry, ownership, operator matrices, t/y/c/chat buffers
+  const double* fdx;
+  const double* fdy;
+  const double* D;
+  const double* uL;
+  const double* uS;
+  const double* what;
+  const double* ZtuS;  // d : Z^T u_S
+  const double* f;
+  const double* gn;
+  double* b;      // r
+  double* bS;     // kp
+  double* rg;     // kp
+  double* cb;     // d : Z^T b_S (accumulated)
+  double* chatb;  // d
+  double* xs;     // kp
+  double* u;      // r
+  double* acc;    // 8 FP64 accumulators
+  double* zero[7];  // kp-long buffers zeroed in P1 (x, t, y, vglob, b_S, rhs, x_S)
+  double* gacc;     // GMRES accumulators, zeroed in P1
+  long long gacc_n;
+};
+
+// accumulator slots
+enum { ACC_ULB = 0, ACC_USBS = 1, ACC_MEAN = 2, ACC_RES = 3, ACC_BSN = 4 };
+
+__device__ double* fd_scratch(const Smem<double>& s) { return s.mats; }
+
+// b_e (projected or not) is in B; solves U = A_e^-1 B.
+__device__ void elem_fd(const PrePostArgs& P, int e, double* B, double* U, double* t1) {
+  const DevGeo& g = P.ga.g;
+  elem_solve_dev(g.n, fd_x(g, P.fdx, e), fd_y(g, P.fdy, e), B, U, t1);
+}
+
+__global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const GmresArgs<double>& a = P.ga;
+  const Smem<double> s = carve(a, smraw);
+  const DevGeo& g = a.g;
+  const int n = g.n, nn = n * n, M = g.M, G = gridDim.x;
+  double* B = fd_scratch(s);
+  double* U = B + nn;
+  double* t1 = U + nn;
+  unsigned epoch = 0;
+  // ---- P1: zero the work vectors; b = f + tau g; u_L^T b
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
+    for (int v = 0; v < 7; ++v) P.zero[v][i] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.gacc_n; i += (long long)G * blockDim.x)
+    P.gacc[i] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x)
+    P.cb[i] = 0.0;
+  double part = 0;
+  for (long long e = blockIdx.x; e < g.nel; e += G) {
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+      const int aa = q % n, bb = q / n;
+      const long long gq = e * nn + q;
+      double v = P.f[gq];
+      if (P.gn) {
+        const long long s0 = e * M;
+        if (aa == 0 && dev_neighbour(g, (int)e, 0) < 0) v += g.tau_x * P.gn[s0 + bb];
+        if (aa == n - 1 && dev_neighbour(g, (int)e, 1) < 0) v += g.tau_x * P.gn[s0 + n + bb];
+        if (bb == 0 && dev_neighbour(g, (int)e, 2) < 0) v += g.tau_y * P.gn[s0 + 2 * n + aa];
+        if (bb == n - 1 && dev_neighbour(g, (int)e, 3) < 0) v += g.tau_y * P.gn[s0 + 3 * n + aa];
+      }
+      P.b[gq] = v;
+      part += P.uL[gq] * v;
+    }
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(P.acc + ACC_ULB, part);
+  if (!grid_sync(a.bar, a.err, epoch)) return;
+  // ---- P2: project b; w = A_e^-1 b_e; push fluxes into b_S; u_S^T b_S; Z^T b_S
+  const double alpha = __ldcg(P.acc + ACC_ULB);
+  double pus = 0;
+  for (long long e = blockIdx.x; e < g.nel; e += G) {
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+      const long long gq = e * nn + q;
+      double v = P.b[gq] - alpha * P.uL[gq];
+      P.b[gq] = v;
+      B[q] = v;
+    }
+    __syncthreads();
+    elem_fd(P, (int)e, B, U, t1);
+    // flux of w into the slot (nbr, opp F, t): -tau_F (p_F w - n_F . grad w)
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const int F = i / n, t = i % n;
+      const int e2 = dev_neighbour(g, (int)e, F);
+      double val = 0;
+      if (e2 >= 0) {
+        int aa, bb;
+        face_node(n, F, t, &aa, &bb);
+        const double tau = F < 2 ? g.tau_x : g.tau_y, pw = F < 2 ? g.p_x : g.p_y;
+        val = -tau * (pw * U[bb * n + aa] - normal_deriv(g, P.D, U, F, t));
+        const size_t sl = (size_t)e2 * M + (F ^ 1) * n + t;
+        P.bS[sl] = val;
+        pus += P.uS[sl] * val;
+      }
+      s.cs[i] = val;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      const int F = threadIdx.x, j = dev_iface(g, (int)e, F);
+      if (j >= 0) {
+        double sum = 0;
+        for (int t = 0; t < n; ++t) sum += s.cs[F * n + t];
+        atomicAdd(P.cb + j, sum);
+      }
+    }
+    __syncthreads();
+  }
+  pus = warp_sum(pus);
+  if ((threadIdx.x & 31) == 0 && pus != 0.0) atomicAdd(P.acc + ACC_USBS, pus);
+  if (!grid_sync(a.bar, a.err, epoch)) return;
+  // ---- P3: c_hat_b = C^+ Z^T (b_S - beta u_S)
+  const double beta = __ldcg(P.acc + ACC_USBS);
+  if (a.precond == 2) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
+      a.c[j] = __ldcg(P.cb + j) - beta * P.ZtuS[j];
+    if (!grid_sync(a.bar, a.err, epoch)) return;
+    coarse_rows(a, s);  // a.c -> a.chat
+    if (!grid_sync(a.bar, a.err, epoch)) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
+      P.chatb[j] = __ldcg(a.chat + j);
+  }
+  // ---- P4: owner entries: project b_S, rhs = P b_S
+  double bsn = 0;
+  for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
+    const long long sl = entry_slot(a, i);
+    if (sl < 0) continue;
+    const int e = (int)(sl / M), F = (int)(sl % M) / n;
+    if (dev_neighbour(g, e, F) < 0) {
+      P.bS[sl] = 0.0;
+      P.rg[sl] = 0.0;
+      continue;
+    }
+    double v = __ldcg(P.bS + sl) - beta * P.uS[sl];
+    P.bS[sl] = v;
+    bsn += v * v;
+    double r = v;
+    if (a.precond == 2) {
+      // - (S Z c_hat_b) at the slot (pull form), as in the GMRES deflation
+      const int ii = (int)(sl % M), t = ii % n, e2 = dev_neighbour(g, e, F);
+      double acc = __ldcg(a.chat + dev_iface(g, e, F));
+      const double* R = a.Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
+      for (int G2 = 0; G2 < 4; ++G2) {
+        const int jj = dev_iface(g, e2, G2);
+        if (jj >= 0) acc += __ldg(R + G2) * __ldcg(a.chat + jj);
+      }
+      r -= acc;
+    }
+    P.rg[sl] = r;
+  }
+  bsn = warp_sum(bsn);
+  if ((threadIdx.x & 31) == 0 && bsn != 0.0) atomicAdd(P.acc + ACC_BSN, bsn);
+}
+
+__global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const GmresArgs<double>& a = P.ga;
+  const Smem<double> s = carve(a, smraw);
+  const DevGeo& g = a.g;
+  const int n = g.n, nn = n * n, M = g.M, G = gridDim.x;
+  double* B = fd_scratch(s);
+  double* U = B + nn;
+  double* t1 = U + nn;
+  unsigned epoch = 0;
+  int trace_n = 0;
+  // ---- Q1-Q4: x_S
+  if (a.precond == 0) {
+    for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
+      const long long sl = entry_slot(a, i);
+      if (sl >= 0) P.xs[sl] = __ldcg(a.x + sl);
+    }
+  } else {
+    for (int k = 0; k < a.nown_b; ++k) {
+      const int ib = blockIdx.x + k * G;
+      if (ib >= a.nblack) break;
+      const int e = a.black[ib];
+      for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
+        const long long sl = block_slot(g, e, i);
+        s.w[i] = sl >= 0 ? __ldcg(a.x + sl) : 0.0;
+      }
+      __syncthreads();
+      block_solve(a, s, k, ib, e, s.w);
+    }
+    if (a.precond == 1) {
+      if (!grid_sync(a.bar, a.err, epoch)) return;
+      for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
+        const long long sl = entry_slot(a, i);
+        if (sl >= 0) P.xs[sl] = __ldcg(a.t + sl);
+      }
+    } else {
+      // white step and coarse solve of y = S t, then x_S = t - Z (c_hat - c_hat_b)
+      if (!apply_op(a, s, a.x, 1.0, true, trace_n, epoch)) return;
+      for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
+        const long long sl = entry_slot(a, i);
+        if (sl < 0) continue;
+        const int e = (int)(sl / M), F = (int)(sl % M) / n, j = dev_iface(g, e, F);
+        P.xs[sl] = j < 0 ? 0.0 : __ldcg(a.t + sl) - (__ldcg(a.chat + j) - P.chatb[j]);
+      }
+    }
+  }
+  if (!grid_sync(a.bar, a.err, epoch)) return;
+  // ---- Q5: recovery u_e = A_e^-1 (b_e - E_e x_S), residual b_S - S x_S, mean
+  double pm = 0, pr = 0;
+  for (long long e = blockIdx.x; e < g.nel; e += G) {
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) B[q] = P.b[e * nn + q];
+    for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = __ldcg(P.xs + e * M + i);
+    __syncthreads();
+    for (int F = 0; F < 4; ++F) {  // faces in turn: a corner node takes both slots
+      if (dev_neighbour(g, (int)e, F) >= 0)
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+          int aa, bb;
+          face_node(n, F, t, &aa, &bb);
+          B[bb * n + aa] -= s.p[F * n + t];
+        }
+      __syncthreads();
+    }
+    elem_fd(P, (int)e, B, U, t1);
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+      P.u[e * nn + q] = U[q];
+      pm += P.what[e * nn + q] * U[q];
+    }
+    // (S x_S) on the slots facing e: x_S + T_e x_S,e
+    gemv_split(a.Tc + (size_t)e * M * M, M, s.p, s.z, M, M, s.red);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const int F = i / n, t = i % n, e2 = dev_neighbour(g, (int)e, F);
+      if (e2 < 0) continue;
+      const size_t sl = (size_t)e2 * M + (F ^ 1) * n + t;
+      const double rr = P.bS[sl] - (__ldcg(P.xs + sl) + s.z[i]);
+      pr += rr * rr;
+    }
+    __syncthreads();
+  }
+  pm = warp_sum(pm);
+  pr = warp_sum(pr);
+  if ((threadIdx.x & 31) == 0) {
+    if (pm != 0.0) atomicAdd(P.acc + ACC_MEAN, pm);
+    if (pr != 0.0) atomicAdd(P.acc + ACC_RES, pr);
+  }
+  if (!grid_sync(a.bar, a.err, epoch)) return;
+  // ---- Q6: zero GLL-weighted mean
+  const double mean = __ldcg(P.acc + ACC_MEAN);
+  for (long long e = blockIdx.x; e < g.nel; e += G)
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean;
+}
+
+inline size_t prepost_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d) {
+  return gmres_smem_bytes<double>(m, M, n, ES, nown_b, nown_w, 0, 0, d) + (3 * (size_t)n * n + 64) * sizeof(double);
+}

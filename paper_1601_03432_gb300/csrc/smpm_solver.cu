@@ -39,6 +39,7 @@ constexpr int kSlotsPerBlock = 256;   // slots per CTA in the vector kernels
 constexpr int kElemThreads = 256;     // threads per element CTA
 constexpr int kTraceCap = 1 << 16;    // entries of the optional phase trace
 constexpr int kGmresThreads = 256;    // threads per CTA of the persistent GMRES kernel
+constexpr size_t kCtlBytes = 32 + 8 * sizeof(double);  // barrier counters, error flag, accumulators
 
 struct GState {
   double tolabs, beta0, beta, wnorm0sq, resid;
@@ -96,41 +97,6 @@ __device__ void block_multidot(const S* __restrict__ V, long long kp, int nvec, 
     acc = warp_sum(acc);
     if (lane == 0) part[(size_t)l * gridDim.x + blockIdx.x] = acc;
   }
-}
-
-// *out = x . y over n entries (FP64), via partials and the last block.
-__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, long long n, double* part,
-                      unsigned* cnt, double* out) {
-  double acc = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    acc += x[i] * y[i];
-  __shared__ double red[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-  }
-  if (last_block_done(cnt)) {
-    finalize_partials(part, gridDim.x, 1, out);
-    if (threadIdx.x == 0) *cnt = 0;
-  }
-}
-
-// u -= *c (removes the GLL-weighted mean, the constant Sec. 1.4 leaves open)
-__global__ void k_sub_const(double* u, const double* c, long long n) {
-  double m = *c;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    u[i] -= m;
-}
-
-// y -= (*alpha) * x
-__global__ void k_axpy_dev(const double* __restrict__ x, const double* alpha, double* y, long long n) {
-  double a = *alpha;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] -= a * x[i];
 }
 
 // ------------------------------------------------------- element solves
@@ -201,23 +167,6 @@ __device__ __forceinline__ const double* fd_y(const DevGeo& g, const double* fdy
   int iy = e / g.mx;
   int cls = (iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0);
   return fdy + (size_t)cls * (2 * g.n * g.n + g.n);
-}
-
-// b = f + tau_F g on physical-boundary face nodes (Eq. smpm_poisson).
-__global__ void k_rhs(DevGeo g, const double* __restrict__ f, const double* __restrict__ gn, double* b) {
-  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= g.r) return;
-  const int n = g.n, nn = n * n;
-  int e = (int)(q / nn), loc = (int)(q % nn), a = loc % n, bb = loc / n;
-  double v = f[q];
-  if (gn) {
-    const long long s0 = (long long)e * g.M;
-    if (a == 0 && dev_neighbour(g, e, 0) < 0) v += g.tau_x * gn[s0 + 0 * n + bb];
-    if (a == n - 1 && dev_neighbour(g, e, 1) < 0) v += g.tau_x * gn[s0 + 1 * n + bb];
-    if (bb == 0 && dev_neighbour(g, e, 2) < 0) v += g.tau_y * gn[s0 + 2 * n + a];
-    if (bb == n - 1 && dev_neighbour(g, e, 3) < 0) v += g.tau_y * gn[s0 + 3 * n + a];
-  }
-  b[q] = v;
 }
 
 // b_S = B A^-1 b (Algorithm 1 step 2): one CTA per element; the flux of
@@ -470,6 +419,7 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
 }
 
 #include "smpm_gmres.cuh"
+#include "smpm_prepost.cuh"
 
 // ------------------------------------------------------------- host side
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -490,20 +440,23 @@ struct smpm_handle_s {
   int *dblack = nullptr, *dwhite = nullptr;
   // workspace
   double *wb = nullptr, *wbS = nullptr, *wV = nullptr, *wt = nullptr, *wy = nullptr, *ww = nullptr;
-  double *ww2 = nullptr, *wx = nullptr, *wrg = nullptr, *wtmp = nullptr;
+  double *wx = nullptr, *wrg = nullptr, *wtmp = nullptr;
   double *wc = nullptr, *wchat = nullptr, *wcb = nullptr, *wchatb = nullptr;
-  double *wpart = nullptr, *winvb = nullptr;
+  double* wpart = nullptr;
   unsigned* wcnt = nullptr;
   unsigned* wbar = nullptr;
   int* werr = nullptr;
   GState* wgs = nullptr;
   struct {
     int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0;
-    size_t smem = 0;
+    size_t smem = 0, smem_pp = 0;
   } gm;  // launch shape of the persistent GMRES kernel
   double* wvown = nullptr;
   double* wacc = nullptr;
+  double *wacc8 = nullptr, *wxs = nullptr, *dZtuS = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the GMRES kernel of each solve
+  cudaEvent_t evp = nullptr, evq = nullptr;  // start of k_pre, end of k_post
+  unsigned char* wctl = nullptr;              // [bar x4 | err | pad | acc8] zeroed per solve
   long long* wtrace = nullptr;                // phase trace buffer (SMPM_TRACE set)
   // staging for the host-pointer entry point
   double *sf = nullptr, *sg = nullptr, *su = nullptr;
@@ -554,9 +507,10 @@ smpm_status upload(smpm_handle h, P** p, const std::vector<P>& src, cudaStream_t
 void free_all(smpm_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
-  if (h->ev0) cudaEventDestroy(h->ev0);
-  if (h->ev1) cudaEventDestroy(h->ev1);
-  h->ev0 = h->ev1 = nullptr;
+  for (cudaEvent_t* ev : {&h->ev0, &h->ev1, &h->evp, &h->evq}) {
+    if (*ev) cudaEventDestroy(*ev);
+    *ev = nullptr;
+  }
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -621,20 +575,6 @@ smpm_status launch_defl(smpm_handle h, const double* y, const double* chat, int 
   return SMPM_OK;
 }
 
-smpm_status launch_dot(smpm_handle h, const double* x, const double* y, long long n, double* out, cudaStream_t st) {
-  unsigned nb = std::min<unsigned>(blocks_for(n, 256), 1024u);
-  k_dot<<<nb, 256, 0, st>>>(x, y, n, h->wpart, h->wcnt, out);
-  CHECK_LAUNCH();
-  return SMPM_OK;
-}
-
-smpm_status launch_axpy(smpm_handle h, const double* x, const double* alpha, double* y, long long n, cudaStream_t st) {
-  unsigned nb = std::min<unsigned>(blocks_for(n, 256), 4096u);
-  k_axpy_dev<<<nb, 256, 0, st>>>(x, alpha, y, n);
-  CHECK_LAUNCH();
-  return SMPM_OK;
-}
-
 // SMPM_TRACE: per-tag mean SM cycles between consecutive trace points of CTA 0.
 smpm_status print_trace(smpm_handle h, cudaStream_t st) {
   std::vector<long long> tr(kTraceCap);
@@ -656,122 +596,102 @@ smpm_status print_trace(smpm_handle h, cudaStream_t st) {
   return SMPM_OK;
 }
 
-smpm_status read_state(smpm_handle h, GState* hs, cudaStream_t st) {
-  CU(cudaMemcpyAsync(hs, h->wgs, offsetof(GState, g), cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  return SMPM_OK;
+// Kernel arguments shared by the three cooperative kernels of a solve.
+GmresArgs<double> gmres_args(smpm_handle h, double tol) {
+  GmresArgs<double> a;
+  a.g = h->dg;
+  a.black = h->dblack;
+  a.white = h->dwhite;
+  a.nblack = (int)h->f.black.size();
+  a.nwhite = (int)h->f.white.size();
+  a.Tc = h->dT; a.Gc = h->dG; a.Xc = h->dX; a.Rs = h->dRs; a.H = h->dH;
+  a.vglob = h->wV; a.vown = h->wvown; a.t = h->wt; a.y = h->wy;
+  a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg; a.x = h->wx;
+  a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
+  a.precond = h->opts.precond; a.m = h->opts.restart; a.maxit = h->opts.maxit; a.tol = tol;
+  a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
+  a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
+  a.trace = h->wtrace;
+  a.trace_cap = h->wtrace ? kTraceCap : 0;
+  return a;
 }
 
-// One right-hand side, FP64, Algorithms 1-3.
+// One right-hand side, FP64, Algorithms 1-3: three cooperative launches
+// (k_pre, k_gmres, k_post) and one host synchronisation for the report.
 smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* u, double tol, smpm_report* rep,
                       cudaStream_t st) {
-  const DevGeo& g = h->dg;
-  const long long kp = g.kp;
   const int m = h->opts.restart;
-  const unsigned nbs = blocks_for(kp, kSlotsPerBlock);
-  smpm_status s;
   smpm_report R{};
   const long long launches0 = h->launches;
-  double* scal = reinterpret_cast<double*>(reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal));
-
-  // Algorithm steps 1-3: b = f + tau g; b -= u_L (u_L^T b); b_S = B A^-1 b; b_S -= u_S (u_S^T b_S)
-  k_rhs<<<blocks_for(g.r, 256), 256, 0, st>>>(g, f, gn, h->wb);
-  CHECK_LAUNCH();
-  if ((s = launch_dot(h, h->duL, h->wb, g.r, scal + 0, st))) return s;
-  if ((s = launch_axpy(h, h->duL, scal + 0, h->wb, g.r, st))) return s;
-  CU(cudaMemsetAsync(h->wbS, 0, kp * sizeof(double), st));
-  k_schur_rhs<<<(unsigned)g.nel, kElemThreads, elem_smem(g.n), st>>>(g, h->dfdx, h->dfdy, h->dD, h->wb, h->wbS);
-  CHECK_LAUNCH();
-  if ((s = launch_dot(h, h->duS, h->wbS, kp, scal + 1, st))) return s;
-  if ((s = launch_axpy(h, h->duS, scal + 1, h->wbS, kp, st))) return s;
-
-  // GMRES right-hand side: P b_S (Algorithm 3) or b_S
-  const bool defl = h->opts.precond == 2;
-  if (defl) {
-    if ((s = launch_zt(h, h->wbS, h->wcb, st))) return s;
-    if ((s = launch_coarse(h, h->wcb, h->wchatb, st))) return s;
-    if ((s = launch_defl(h, h->wbS, h->wchatb, -1, h->wrg, st))) return s;
-  } else {
-    CU(cudaMemcpyAsync(h->wrg, h->wbS, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // one memset per solve: barrier counters of the three kernels, error flag,
+  // pre/post accumulators (contiguous); everything else is zeroed in k_pre
+  CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
+  PrePostArgs P;
+  P.ga = gmres_args(h, tol);
+  P.ga.mats_smem = 0;
+  P.ga.basis_smem = 0;
+  P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
+  P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
+  P.chatb = h->wchatb; P.xs = h->wxs; P.u = u; P.acc = h->wacc8;
+  P.ga.trace = nullptr;
+  P.ga.bar = h->wbar + 0;
+  double* zs[7] = {h->wx, h->wt, h->wy, h->wV, h->wbS, h->wrg, h->wxs};
+  for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+  P.gacc = h->wacc;
+  P.gacc_n = (long long)(2 * m + 1) * (m + 3);
+  {
+    void* args[] = {&P};
+    CU(cudaEventRecord(h->evp, st));
+    CU(cudaLaunchCooperativeKernel((const void*)k_pre, dim3(h->gm.grid), dim3(kGmresThreads), args, h->gm.smem_pp,
+                                   st));
+    CHECK_LAUNCH();
   }
-  // x_1 := GMRES(op, rhs): one persistent cooperative launch (smpm_gmres.cuh)
-  CU(cudaMemsetAsync(h->wx, 0, kp * sizeof(double), st));
-  CU(cudaMemsetAsync(h->wt, 0, kp * sizeof(double), st));
-  CU(cudaMemsetAsync(h->wy, 0, kp * sizeof(double), st));
-  CU(cudaMemsetAsync(h->werr, 0, sizeof(int), st));
-  CU(cudaMemsetAsync(h->wbar, 0, 2 * sizeof(unsigned), st));
-  CU(cudaMemsetAsync(h->wacc, 0, (size_t)(2 * m + 1) * (m + 3) * sizeof(double), st));
   CU(cudaEventRecord(h->ev0, st));
   {
-    GmresArgs<double> a;
-    a.g = g;
-    a.black = h->dblack;
-    a.white = h->dwhite;
-    a.nblack = (int)h->f.black.size();
-    a.nwhite = (int)h->f.white.size();
-    a.Tc = h->dT; a.Gc = h->dG; a.Xc = h->dX; a.Rs = h->dRs; a.H = h->dH;
-    a.vglob = h->wV; a.vown = h->wvown; a.t = h->wt; a.y = h->wy;
-    a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg; a.x = h->wx;
-    a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
-    a.precond = h->opts.precond; a.m = m; a.maxit = h->opts.maxit; a.tol = tol;
-    a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
-    a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
-    a.trace = h->wtrace;
-    a.trace_cap = h->wtrace ? kTraceCap : 0;
+    GmresArgs<double> a = gmres_args(h, tol);
+    a.bar = h->wbar + 1;
     void* args[] = {&a};
     CU(cudaLaunchCooperativeKernel((const void*)k_gmres<double>, dim3(h->gm.grid), dim3(kGmresThreads), args,
                                    h->gm.smem, st));
     CHECK_LAUNCH();
   }
   CU(cudaEventRecord(h->ev1, st));
+  {
+    P.ga.bar = h->wbar + 2;
+    void* args[] = {&P};
+    CU(cudaLaunchCooperativeKernel((const void*)k_post, dim3(h->gm.grid), dim3(kGmresThreads), args, h->gm.smem_pp,
+                                   st));
+    CHECK_LAUNCH();
+    CU(cudaEventRecord(h->evq, st));
+  }
   if (h->wtrace) print_trace(h, st);
   GState hs;
   int herr = 0;
+  double acc8[8];
   CU(cudaMemcpyAsync(&herr, h->werr, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if ((s = read_state(h, &hs, st))) return s;
-  if (herr) return fail(SMPM_ETIMEOUT, "grid barrier of the GMRES kernel timed out");
+  CU(cudaMemcpyAsync(acc8, h->wacc8, sizeof(acc8), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&hs, h->wgs, offsetof(GState, g), cudaMemcpyDeviceToHost, st));
+  double scal[8];
+  CU(cudaMemcpyAsync(scal, reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal), sizeof(scal),
+                     cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (herr) return fail(SMPM_ETIMEOUT, "a grid barrier of the solve kernels timed out");
   if (hs.nan) return fail(SMPM_ENAN, "non-finite value in the right-hand side or the Arnoldi process");
-  const int total = hs.j;
-  double cycles_d = 0;
-  CU(cudaMemcpy(&cycles_d, reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal) + 7 * sizeof(double),
-                sizeof(double), cudaMemcpyDeviceToHost));
-  R.restarts = cycles_d > 1 ? (int)cycles_d - 1 : 0;
+  R.iterations = hs.j;
+  R.restarts = scal[7] > 1 ? (int)scal[7] - 1 : 0;
+  const bool conv = hs.converged || hs.beta0 == 0.0 || hs.breakdown;
+  R.converged = conv ? 1 : 0;
+  R.gmres_relres = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
+  R.schur_relres = acc8[ACC_BSN] > 0 ? std::sqrt(acc8[ACC_RES] / acc8[ACC_BSN]) : 0.0;
   {
     float ms = 0;
     CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     R.gmres_ms = ms;
+    CU(cudaEventElapsedTime(&ms, h->evp, h->ev0));
+    R.pre_ms = ms;
+    CU(cudaEventElapsedTime(&ms, h->ev1, h->evq));
+    R.post_ms = ms;
   }
-  bool conv = hs.converged || hs.beta0 == 0.0 || hs.breakdown;
-  R.iterations = total;
-  R.converged = conv ? 1 : 0;
-  R.gmres_relres = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
-
-  // assembly of x_S and recovery of u (Algorithm 3 steps 5-9)
-  if (defl) {
-    if ((s = launch_precond(h, h->wx, h->wt, h->wy, h->wc, st))) return s;  // t = M^-1 x, y = S t, c = Z^T y
-    if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
-    k_assemble<<<nbs, kSlotsPerBlock, 0, st>>>(g, h->wt, h->wchat, h->wchatb, h->ww);
-    CHECK_LAUNCH();
-  } else if (h->opts.precond == 1) {
-    if ((s = launch_precond(h, h->wx, h->ww, nullptr, nullptr, st))) return s;
-  } else {
-    CU(cudaMemcpyAsync(h->ww, h->wx, kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  }
-  k_recover<<<(unsigned)g.nel, kElemThreads, elem_smem(g.n), st>>>(g, h->dfdx, h->dfdy, h->wb, h->ww, u);
-  CHECK_LAUNCH();
-  if ((s = launch_dot(h, h->dwhat, u, g.r, scal + 2, st))) return s;  // GLL-weighted mean
-  k_sub_const<<<std::min<unsigned>(blocks_for(g.r, 256), 4096u), 256, 0, st>>>(u, scal + 2, g.r);
-  CHECK_LAUNCH();
-  // true Schur residual ||b_S - S x|| / ||b_S|| (FP64)
-  if ((s = launch_schur(h, h->ww, h->wtmp, st))) return s;
-  k_sub<double><<<nbs, kSlotsPerBlock, 0, st>>>(kp, h->wbS, h->wtmp, h->wtmp);
-  CHECK_LAUNCH();
-  if ((s = launch_dot(h, h->wtmp, h->wtmp, kp, scal + 3, st))) return s;
-  if ((s = launch_dot(h, h->wbS, h->wbS, kp, scal + 4, st))) return s;
-  double sc[5];
-  CU(cudaMemcpyAsync(sc, scal, sizeof(sc), cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  R.schur_relres = sc[4] > 0 ? std::sqrt(sc[3] / sc[4]) : 0.0;
   R.launches = (int)(h->launches - launches0);
   if (rep) *rep = R;
   if (!conv) return fail(SMPM_ENOTCONV, "GMRES did not converge within maxit");
@@ -904,17 +824,17 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   const size_t nbs = blocks_for(g.kp, kSlotsPerBlock);
   if ((s = dalloc(h, &h->wb, r)) || (s = dalloc(h, &h->wbS, kp)) || (s = dalloc(h, &h->wV, (m + 1) * kp)) ||
       (s = dalloc(h, &h->wt, kp)) || (s = dalloc(h, &h->wy, kp)) || (s = dalloc(h, &h->ww, kp)) ||
-      (s = dalloc(h, &h->ww2, kp)) || (s = dalloc(h, &h->wx, kp)) || (s = dalloc(h, &h->wrg, kp)) ||
+      (s = dalloc(h, &h->wx, kp)) || (s = dalloc(h, &h->wrg, kp)) ||
       (s = dalloc(h, &h->wtmp, kp)) || (s = dalloc(h, &h->wc, d)) || (s = dalloc(h, &h->wchat, d)) ||
       (s = dalloc(h, &h->wcb, d)) || (s = dalloc(h, &h->wchatb, d)) ||
       (s = dalloc(h, &h->wpart, (size_t)3 * (kMaxRestart + 3) * std::max<size_t>(nbs, 1024))) ||
-      (s = dalloc(h, &h->wcnt, 8)) || (s = dalloc(h, &h->wgs, 1)) || (s = dalloc(h, &h->winvb, kMaxRestart + 2)) ||
-      (s = dalloc(h, &h->wbar, 2)) || (s = dalloc(h, &h->werr, 1)))
+      (s = dalloc(h, &h->wcnt, 8)) || (s = dalloc(h, &h->wgs, 1)))
     return s;
   CU(cudaMemsetAsync(h->wcnt, 0, 8 * sizeof(unsigned), st));
-  CU(cudaMemsetAsync(h->wbar, 0, 2 * sizeof(unsigned), st));
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));
+  CU(cudaEventCreate(&h->evp));
+  CU(cudaEventCreate(&h->evq));
   if (std::getenv("SMPM_TRACE")) {
     if ((s = dalloc(h, &h->wtrace, kTraceCap))) return s;
     CU(cudaMemsetAsync(h->wtrace, 0, kTraceCap * sizeof(long long), st));
@@ -947,6 +867,27 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<double>, kGmresThreads, gm.smem));
     if (per_sm < 1) return fail(SMPM_ECUDA, "the GMRES kernel does not fit on an SM");
+    gm.smem_pp = prepost_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
+    if (gm.smem_pp > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the solve kernels");
+    CU(cudaFuncSetAttribute(k_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem_pp));
+    CU(cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem_pp));
+    for (const void* fn : {(const void*)k_pre, (const void*)k_post}) {
+      int per = 0;
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kGmresThreads, gm.smem_pp));
+      if (per < 1) return fail(SMPM_ECUDA, "the solve kernels do not fit on an SM");
+    }
+    std::vector<double> ztus(g.d, 0.0);
+    for (long long e = 0; e < g.nel; ++e)
+      for (int F = 0; F < 4; ++F) {
+        int j = h->g.iface((int)e, F);
+        if (j < 0) continue;
+        for (int t = 0; t < g.n; ++t) ztus[j] += h->f.uS[e * g.M + F * g.n + t];
+      }
+    if ((s = upload(h, &h->dZtuS, ztus, st))) return s;
+    if ((s = dalloc(h, &h->wctl, kCtlBytes)) || (s = dalloc(h, &h->wxs, g.kp))) return s;
+    h->wbar = reinterpret_cast<unsigned*>(h->wctl);
+    h->werr = reinterpret_cast<int*>(h->wctl + 16);
+    h->wacc8 = reinterpret_cast<double*>(h->wctl + 32);
     if ((s = dalloc(h, &h->wacc, (size_t)(2 * m + 1) * (m + 3)))) return s;
     if (!gm.basis_smem && (s = dalloc(h, &h->wvown, (size_t)gm.grid * (m + 1) * gm.ES))) return s;
   }
