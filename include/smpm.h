@@ -163,6 +163,25 @@ smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o);
  * "null_iterations" (1 value). */
 smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long long count, long long* len);
 
+/* y = P v exactly as smpm_apply_deflation, for callers that cannot allocate
+ * device memory when they call: code inside a framework whose caching
+ * allocator already owns the free device memory, latency-critical loops that
+ * must not hit the implicit device synchronisation of cudaMalloc/cudaFree,
+ * or callers with a fixed memory budget.  The paper has no counterpart; this
+ * is a property of the library interface only.
+ *   v, y : device, kp doubles (caller-owned; y must not alias v)
+ * The call allocates nothing: its scratch (Z^T v, C^+ Z^T v and a barrier
+ * word) is a file-scope device array of 2*32768 + 32 doubles (~512 KiB) that
+ * every GPU loading this library holds until exit.  Grids with more than
+ * 32768 interfaces are rejected with SMPM_EINVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the one array: calls that overlap on the GPU (different streams, threads or
+ * handles) race and must be serialised by the caller.  Asynchronous on
+ * stream; a failed internal grid barrier (not expected) leaves y = NaN.
+ * Errors: EINVAL, ESTATE, ECUDA. */
+smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream);
+
 /* Release every resource of h (null is ignored). */
 void smpm_destroy(smpm_handle h);
 

@@ -24,6 +24,7 @@ EXPORTS = [
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
+    "smpm_apply_deflation_noalloc",
 ]
 
 
@@ -71,7 +72,7 @@ def lib():
         L.schur_solve.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
         L.schur_solve_host.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
         for name in ["smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond", "smpm_apply_deflation",
-                     "smpm_apply_deflation_q", "smpm_schur_rhs"]:
+                     "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_apply_deflation_noalloc"]:
             getattr(L, name).argtypes = [P, P, P, P]
         L.smpm_recover.argtypes = [P, P, P, P, P]
         L.smpm_null_vectors.argtypes = [P, P, P, P, P]
@@ -216,6 +217,11 @@ class Grid:
 
     def apply_deflation(self, v, out, stream=None):
         return self._op("smpm_apply_deflation", v, out, stream)
+
+    def apply_deflation_noalloc(self, v, out, stream=None):
+        """y = P v through the entry point that allocates nothing (scratch in a
+        static device array shared by all calls on a device)."""
+        return self._op("smpm_apply_deflation_noalloc", v, out, stream)
 
     def apply_deflation_q(self, v, out, stream=None):
         return self._op("smpm_apply_deflation_q", v, out, stream)

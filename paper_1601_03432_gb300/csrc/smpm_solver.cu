@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1068,3 +1069,95 @@ void smpm_destroy(smpm_handle h) {
 }
 
 }  // extern "C"
+
+// ============================================ allocation-free deflation
+// A variant of the deflation operator y = P v for callers that cannot
+// allocate device memory at the time of the call: code running inside a
+// framework whose caching allocator owns the free device memory, code that
+// must not trigger the implicit device synchronisation of cudaMalloc/cudaFree
+// (latency-critical loops), or callers with a fixed memory budget.  Its
+// scratch (Z^T v, C^+ Z^T v and a barrier word) lives in the file-scope array
+// below, which every GPU that loads this library holds until exit.
+namespace {
+
+constexpr long long kNoAllocMaxInterfaces = 32768;  // d limit: 2 x 32768 doubles = 512 KiB
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxInterfaces + 32];
+
+// Device address of g_noalloc_scratch per device, taken once with that device current.
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+// One cooperative launch: c = Z^T v | c_hat = C^+ c | y = v - S Z c_hat.
+// On a barrier timeout (not expected: all CTAs are co-resident) y is NaN.
+__global__ void __launch_bounds__(256) k_deflate_noalloc(DevGeo g, const double* __restrict__ H,
+                                                         const double* __restrict__ Rs, const double* v, double* y,
+                                                         double* scratch) {
+  double* c = scratch;
+  double* chat = scratch + kNoAllocMaxInterfaces;
+  unsigned* bar = reinterpret_cast<unsigned*>(scratch + 2 * kNoAllocMaxInterfaces);
+  int* err = reinterpret_cast<int*>(bar + 4);
+  unsigned epoch = 0;
+  const int n = g.n, M = g.M, row = 2 * g.mx - 1;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nthr = (long long)gridDim.x * blockDim.x;
+  for (long long j = tid; j < g.d; j += nthr) {  // interface sums, as k_zt
+    int iy = (int)(j / row), rem = (int)(j % row), e1, F1;
+    if (rem < g.mx - 1) { e1 = iy * g.mx + rem; F1 = 1; }
+    else { e1 = iy * g.mx + rem - (g.mx - 1); F1 = 3; }
+    int e2 = dev_neighbour(g, e1, F1);
+    double s = 0;
+    for (int t = 0; t < n; ++t) s += v[(size_t)e1 * M + F1 * n + t] + v[(size_t)e2 * M + (F1 ^ 1) * n + t];
+    c[j] = s;
+  }
+  bool ok = grid_sync(bar, err, epoch);
+  if (ok) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = nthr >> 5;
+    for (long long r = tid >> 5; r < g.d; r += nw) {
+      const double* h = H + r * g.d;
+      double acc = 0;
+      for (long long j = lane; j < g.d; j += 32) acc += __ldg(h + j) * __ldcg(c + j);
+      acc = warp_sum(acc);
+      if (lane == 0) chat[r] = acc;
+    }
+    ok = grid_sync(bar, err, epoch);
+  }
+  for (long long s = tid; s < g.kp; s += nthr) y[s] = ok ? deflate_slot_cg(g, v, chat, Rs, s) : nan("");
+}
+
+}  // namespace
+
+extern "C" smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream) {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  if (h->g.d > kNoAllocMaxInterfaces)
+    return fail(SMPM_EINVAL, "smpm_apply_deflation_noalloc supports at most " +
+                                 std::to_string(kNoAllocMaxInterfaces) + " interfaces; this grid has " +
+                                 std::to_string(h->g.d));
+  if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  cudaStream_t st = as_stream(stream);
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(SMPM_EINVAL, "device ordinal out of range");
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      CU(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  // the barrier word and the error flag must start at zero; c and c_hat are
+  // fully written before they are read
+  CU(cudaMemsetAsync(scratch + 2 * kNoAllocMaxInterfaces, 0, 32 * sizeof(double), st));
+  int sms = 0;
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevGeo g = h->dg;
+  const double* H = h->dH;
+  const double* Rs = h->dRs;
+  void* args[] = {&g, &H, &Rs, &v, &y, &scratch};
+  CU(cudaLaunchCooperativeKernel((const void*)k_deflate_noalloc, dim3(sms), dim3(256), args, 0, st));
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
