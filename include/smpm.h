@@ -62,7 +62,15 @@ typedef struct {
   int precond;         /* 0, 1, 2 as above                                    */
   double tau_scale;    /* default 1.0                                         */
   double robin_scale;  /* default 0.25                                        */
+  int flags;           /* SMPM_FLAG_* bits (default 0)                        */
 } smpm_opts;
+
+/* flags: keep the GMRES operator matrices and Krylov basis in global memory
+ * even when they fit in shared memory; stream the operator matrices through
+ * shared memory with bulk copies even when they would fit resident (the
+ * large-grid layouts, selectable for testing). */
+#define SMPM_FLAG_NO_SMEM_RESIDENCY 1
+#define SMPM_FLAG_STREAM_MATRICES 2
 
 /* Per-solve report, written by schur_solve when the pointer is non-null. */
 typedef struct {

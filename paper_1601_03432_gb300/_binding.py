@@ -31,7 +31,7 @@ EXPORTS = [
 class SmpmOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("precond", ctypes.c_int), ("tau_scale", ctypes.c_double),
-                ("robin_scale", ctypes.c_double)]
+                ("robin_scale", ctypes.c_double), ("flags", ctypes.c_int)]
 
 
 class SmpmReport(ctypes.Structure):

@@ -64,6 +64,8 @@ struct GmresArgs {
   int ES;              // entries per CTA in the basis slice (odd, >= 2M nown_b)
   int mats_smem;       // 1: owned matrices resident in shared memory
   int basis_smem;      // 1: basis slice resident in shared memory
+  int stream_mats;     // 1: owned matrices streamed through two shared buffers (bulk copies)
+  int buf_elems;       // elements of S per stream buffer (>= M*M + 4*n*n, multiple of 16 bytes)
   long long* trace;
   int trace_cap;
 };
@@ -129,7 +131,8 @@ struct Smem {
   S *w, *w2;
   double* cst;  // staged coarse vector c (d)
   S* V;     // (m+1) * ES when resident
-  S* mats;  // resident matrices
+  S* mats;  // resident matrices, or the two stream buffers
+  unsigned long long* mbar;  // two mbarriers of the matrix stream
 };
 
 template <typename S>
@@ -137,6 +140,7 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
   Smem<S> s;
   const int m = a.m, M = a.g.M;
   double* d = reinterpret_cast<double*>(raw);
+  s.mbar = reinterpret_cast<unsigned long long*>(d); d += 2;
   s.h1 = d; d += m + 3;
   s.h2 = d; d += m + 3;
   s.hs1 = d; d += m + 3;
@@ -159,18 +163,20 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
   s.w2 = q; q += a.ES + 1;
   s.V = q;
   if (a.basis_smem) q += (size_t)(m + 1) * a.ES;
+  q = reinterpret_cast<S*>((reinterpret_cast<size_t>(q) + 15) & ~size_t(15));
   s.mats = q;
   return s;
 }
 
 template <typename S>
 inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
-                               long long d) {
-  size_t dbl = 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
+                               long long d, int stream_elems = 0) {
+  size_t dbl = 2 + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
   size_t sel = 4 * (size_t)M + 256 + 2 * (size_t)(ES + 1);
   if (basis_smem) sel += (size_t)(m + 1) * ES;
   if (mats_smem) sel += (size_t)nown_b * (2 * (size_t)M * M + 4 * (size_t)n * n) + (size_t)nown_w * M * M;
-  return dbl * sizeof(double) + sel * sizeof(S) + 64;
+  sel += 2 * (size_t)stream_elems;
+  return dbl * sizeof(double) + sel * sizeof(S) + 128;
 }
 
 // pointers to the owned matrices (shared-memory copies or global)
@@ -201,36 +207,139 @@ __device__ __forceinline__ S* basis(const GmresArgs<S>& a, const Smem<S>& s, int
   return a.basis_smem ? s.V + (size_t)l * a.ES : a.vown + ((size_t)blockIdx.x * (a.m + 1) + l) * a.ES;
 }
 
-// ---- element phases ---------------------------------------------------------
-// Block solve of the owned black block k from the block-slot values vb[0..2M)
-// (already scaled): t = M^-1 v on the block.
-template <typename S>
-__device__ void block_solve(const GmresArgs<S>& a, const Smem<S>& s, int k, int ib, int e, const S* vb) {
-  const int M = a.g.M, n = a.g.n;
-  const S* X = mat_X(a, s, k, ib);
-  {
-    // r1 = p - X q, X = blockdiag(X_F), X_F column-major: P parts per row
-    int P = 1;
-    while (P * 2 * M <= (int)blockDim.x && P < 8) P *= 2;
-    const int t = threadIdx.x, r = t % M, part = t / M;
-    if (part < P) {
-      const int F = r / n, tt = r % n;
-      const S* xf = X + (size_t)F * n * n;
-      const S* xq = vb + M + F * n;
-      S acc = 0;
-      for (int c = part; c < n; c += P) acc += xf[c * n + tt] * xq[c];
-      s.red[part * M + r] = acc;
-    }
-    __syncthreads();
-    for (int i = t; i < M; i += blockDim.x) {
-      S sum = s.red[i];
-      for (int p = 1; p < P; ++p) sum += s.red[p * M + i];
-      s.r1[i] = vb[i] - sum;
-    }
-    __syncthreads();
+// ---- matrix stream: bulk copies into two shared-memory buffers ------------
+// Item sequence of a CTA (cyclic, the order in which the phases use them):
+// for each owned block k: [G_k | X_k], [T_e(k)]; then for each owned white
+// element: [T_e].  Item i lives in buffer i % 2; while it is used the next
+// item is in flight.  Thread 0 issues; waits are bounded.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long spins = 0; spins < (1LL << 22); ++spins) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
-  gemv_split(mat_G(a, s, k, ib), M, s.r1, s.av, M, M, s.red);
-  gemv_split(mat_Tb(a, s, k, e), M, s.av, s.z, M, M, s.red);
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <typename S>
+struct MatStream {
+  int nb, nw, nitems;
+  long long issued, consumed;
+};
+
+template <typename S>
+__device__ void ms_issue(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
+  if (ms.nitems == 0) return;
+  const long long i = ms.issued++;
+  if (threadIdx.x != 0) return;
+  const int M = a.g.M, n = a.g.n, G = gridDim.x;
+  const int it = (int)(i % ms.nitems), b = (int)(i & 1);
+  S* dst = s.mats + (size_t)b * a.buf_elems;
+  unsigned long long* bar = s.mbar + b;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const unsigned mm = (unsigned)(M * M * sizeof(S)), xx = (unsigned)(4 * n * n * sizeof(S));
+  if (it < 2 * ms.nb) {
+    const int k = it >> 1, ib = blockIdx.x + k * G;
+    if ((it & 1) == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(mm + xx)
+                   : "memory");
+      bulk_g2s(dst, a.Gc + (size_t)ib * M * M, mm, bar);
+      bulk_g2s(dst + (size_t)M * M, a.Xc + (size_t)ib * 4 * n * n, xx, bar);
+    } else {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(mm) : "memory");
+      bulk_g2s(dst, a.Tc + (size_t)a.black[ib] * M * M, mm, bar);
+    }
+  } else {
+    const int k = it - 2 * ms.nb, iw = blockIdx.x + k * G;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(mm) : "memory");
+    bulk_g2s(dst, a.Tc + (size_t)a.white[iw] * M * M, mm, bar);
+  }
+}
+
+// wait for the next item; returns its buffer (null on timeout, err set)
+template <typename S>
+__device__ const S* ms_acquire(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
+  const long long i = ms.consumed;
+  const int b = (int)(i & 1);
+  const unsigned parity = (unsigned)((i >> 1) & 1);
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = mbar_wait(s.mbar + b, parity) ? 1 : 0;
+  __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    return nullptr;
+  }
+  return s.mats + (size_t)b * a.buf_elems;
+}
+
+// done with the current item: the buffer is refilled with item consumed + 2
+template <typename S>
+__device__ void ms_release(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
+  __syncthreads();
+  ++ms.consumed;
+  ms_issue(a, s, ms);
+}
+
+// wait (bounded) for the copies still in flight before the kernel returns
+template <typename S>
+__device__ void ms_drain(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
+  if (!a.stream_mats) return;
+  while (ms.consumed < ms.issued) {
+    const long long i = ms.consumed++;
+    if (threadIdx.x == 0) mbar_wait(s.mbar + (i & 1), (unsigned)((i >> 1) & 1));
+  }
+  __syncthreads();
+}
+
+// ---- element phases ---------------------------------------------------------
+// Block solve of one black block from the block-slot values vb[0..2M)
+// (already scaled), t = M^-1 v on the block, in two halves around the
+// matrix stream: (1) r1 = p - X q, a = G r1; (2) z = T_e a, write t.
+template <typename S>
+__device__ void block_solve_a(const GmresArgs<S>& a, const Smem<S>& s, const S* G, const S* X, const S* vb) {
+  const int M = a.g.M, n = a.g.n;
+  int P = 1;
+  while (P * 2 * M <= (int)blockDim.x && P < 8) P *= 2;
+  const int t = threadIdx.x, r = t % M, part = t / M;
+  if (part < P) {
+    const int F = r / n, tt = r % n;
+    const S* xf = X + (size_t)F * n * n;
+    const S* xq = vb + M + F * n;
+    S acc = 0;
+    for (int c = part; c < n; c += P) acc += xf[c * n + tt] * xq[c];
+    s.red[part * M + r] = acc;
+  }
+  __syncthreads();
+  for (int i = t; i < M; i += blockDim.x) {
+    S sum = s.red[i];
+    for (int p = 1; p < P; ++p) sum += s.red[p * M + i];
+    s.r1[i] = vb[i] - sum;
+  }
+  __syncthreads();
+  gemv_split(G, M, s.r1, s.av, M, M, s.red);
+}
+
+template <typename S>
+__device__ void block_solve_b(const GmresArgs<S>& a, const Smem<S>& s, int e, const S* T, const S* vb) {
+  const int M = a.g.M;
+  gemv_split(T, M, s.av, s.z, M, M, s.red);
   for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
     long long sl = block_slot(a.g, e, i);
     if (sl < 0) continue;
@@ -239,15 +348,22 @@ __device__ void block_solve(const GmresArgs<S>& a, const Smem<S>& s, int k, int 
   __syncthreads();
 }
 
+template <typename S>
+__device__ void block_solve(const GmresArgs<S>& a, const Smem<S>& s, int k, int ib, int e, const S* vb) {
+  block_solve_a(a, s, mat_G(a, s, k, ib), mat_X(a, s, k, ib), vb);
+  block_solve_b(a, s, e, mat_Tb(a, s, k, e), vb);
+}
+
 // White element: y = S t on the black slots facing e, y = sc*v on e's slots,
 // c = Z^T y on e's interfaces (with_c).
 template <typename S>
-__device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, int k, int e, const S* v, double sc, bool with_c) {
+__device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, const S* Tw, int e, const S* v, double sc,
+                           bool with_c) {
   const DevGeo& g = a.g;
   const int M = g.M, n = g.n;
   for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = ldcg(a.t + (size_t)e * M + i);
   __syncthreads();
-  gemv_split(mat_Tw(a, s, k, e), M, s.p, s.z, M, M, s.red);
+  gemv_split(Tw, M, s.p, s.z, M, M, s.red);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     int F = i / n, tt = i % n;
     int e2 = dev_neighbour(g, e, F);
@@ -388,37 +504,67 @@ __device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
   return block_slot(a.g, a.black[ib], ii);
 }
 
+// black block solves of this CTA from the global vector sc * src
+template <typename S>
+__device__ bool black_phase(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>* ms, const S* src, double sc,
+                            const S* own) {
+  const DevGeo& g = a.g;
+  const int M = g.M, G = gridDim.x;
+  for (int k = 0; k < a.nown_b; ++k) {
+    int ib = blockIdx.x + k * G;
+    if (ib >= a.nblack) break;
+    int e = a.black[ib];
+    for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
+      if (own) {
+        s.w[i] = (S)(sc * (double)own[k * 2 * M + i]);
+      } else {
+        long long sl = block_slot(g, e, i);
+        s.w[i] = sl >= 0 ? (S)(sc * (double)ldcg(src + sl)) : S(0);
+      }
+    }
+    __syncthreads();
+    if (ms) {
+      const S* GX = ms_acquire(a, s, *ms);
+      if (!GX) return false;
+      block_solve_a(a, s, GX, GX + (size_t)M * M, s.w);
+      ms_release(a, s, *ms);
+      const S* T = ms_acquire(a, s, *ms);
+      if (!T) return false;
+      block_solve_b(a, s, e, T, s.w);
+      ms_release(a, s, *ms);
+    } else {
+      block_solve(a, s, k, ib, e, s.w);
+    }
+  }
+  return true;
+}
+
 // op(sc * src) -> y (and c, chat).  With t_done the owners have already
 // written t = M^-1 v for their blocks.
 template <typename S>
 __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, double sc, bool t_done,
-                         int& trace_n, unsigned& epoch) {
+                         int& trace_n, unsigned& epoch, MatStream<S>* ms = nullptr) {
   const DevGeo& g = a.g;
-  const int M = g.M, G = gridDim.x;
+  const int G = gridDim.x;
   if (a.precond == 0) {
     for (long long e = blockIdx.x; e < g.nel; e += G) push_step(a, s, (int)e, src, sc);
     return grid_sync(a.bar, a.err, epoch);
   }
-  if (!t_done) {
-    for (int k = 0; k < a.nown_b; ++k) {
-      int ib = blockIdx.x + k * G;
-      if (ib >= a.nblack) break;
-      int e = a.black[ib];
-      for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
-        long long sl = block_slot(g, e, i);
-        s.w[i] = sl >= 0 ? (S)(sc * (double)ldcg(src + sl)) : S(0);
-      }
-      __syncthreads();
-      block_solve(a, s, k, ib, e, s.w);
-    }
-  }
+  if (!t_done && !black_phase(a, s, ms, src, sc, (const S*)nullptr)) return false;
   GM_TRACE(20);
   if (!grid_sync(a.bar, a.err, epoch)) return false;
   GM_TRACE(21);
   for (int k = 0; k < a.nown_w; ++k) {
     int iw = blockIdx.x + k * G;
     if (iw >= a.nwhite) break;
-    white_step(a, s, k, a.white[iw], src, sc, a.precond == 2);
+    if (ms) {
+      const S* T = ms_acquire(a, s, *ms);
+      if (!T) return false;
+      white_step(a, s, T, a.white[iw], src, sc, a.precond == 2);
+      ms_release(a, s, *ms);
+    } else {
+      white_step(a, s, mat_Tw(a, s, k, a.white[iw]), a.white[iw], src, sc, a.precond == 2);
+    }
   }
   GM_TRACE(22);
   if (!grid_sync(a.bar, a.err, epoch)) return false;
@@ -442,6 +588,31 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
   const int m3 = m + 3;
   int trace_n = 0;
   unsigned epoch = 0;
+
+  // ---- matrix stream (owned matrices too large for shared memory)
+  MatStream<S> msd;
+  msd.nb = 0;
+  msd.nw = 0;
+  for (int k = 0; k < a.nown_b; ++k) msd.nb += (blockIdx.x + k * G < a.nblack) ? 1 : 0;
+  for (int k = 0; k < a.nown_w; ++k) msd.nw += (blockIdx.x + k * G < a.nwhite) ? 1 : 0;
+  msd.nitems = 2 * msd.nb + msd.nw;
+  msd.issued = msd.consumed = 0;
+  MatStream<S>* ms = a.stream_mats ? &msd : nullptr;
+  if (ms) {
+    if (threadIdx.x == 0) {
+      mbar_init(s.mbar);
+      mbar_init(s.mbar + 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    ms_issue(a, s, msd);
+    ms_issue(a, s, msd);
+  }
+#define GM_FAIL()           \
+  do {                      \
+    ms_drain(a, s, msd);    \
+    return;                 \
+  } while (0)
 
   // ---- resident copies of the owned matrices
   if (a.mats_smem) {
@@ -473,7 +644,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     double* accN = a.acc + (size_t)(2 * m) * m3;
     // ---- cycle start: V[0] = rhs - op(x)
     if (cycle > 0) {
-      if (!apply_op(a, s, a.x, 1.0, false, trace_n, epoch)) return;
+      if (!apply_op(a, s, a.x, 1.0, false, trace_n, epoch, ms)) GM_FAIL();
     }
     {
       S* v0 = basis(a, s, 0);
@@ -493,7 +664,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       nn = warp_sum(nn);
       if ((threadIdx.x & 31) == 0 && nn != 0.0) atomicAdd(accN, nn);
     }
-    if (!grid_sync(a.bar, a.err, epoch)) return;
+    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
     const double beta = sqrt(__ldcg(accN));
     if (cycle == 0) {
       beta0 = beta;
@@ -527,17 +698,11 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
         __syncthreads();
       }
       if (a.precond == 0) {
-        if (!grid_sync(a.bar, a.err, epoch)) return;  // neighbours read v_j
-        if (!apply_op(a, s, a.vglob, ivj, false, trace_n, epoch)) return;
+        if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();  // neighbours read v_j
+        if (!apply_op(a, s, a.vglob, ivj, false, trace_n, epoch, ms)) GM_FAIL();
       } else {
-        for (int k = 0; k < a.nown_b; ++k) {
-          int ib = blockIdx.x + k * G;
-          if (ib >= a.nblack) break;
-          for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) s.w[i] = (S)(ivj * (double)vj[k * 2 * M + i]);
-          __syncthreads();
-          block_solve(a, s, k, ib, a.black[ib], s.w);
-        }
-        if (!apply_op(a, s, a.vglob, ivj, true, trace_n, epoch)) return;
+        if (!black_phase(a, s, ms, (const S*)nullptr, ivj, vj)) GM_FAIL();
+        if (!apply_op(a, s, a.vglob, ivj, true, trace_n, epoch, ms)) GM_FAIL();
       }
       GM_TRACE(4);
       // ---- D: w = y - S Z chat on owned entries; V^T w, ||w||^2
@@ -548,7 +713,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       __syncthreads();
       owned_dots(a, s, s.w, j + 2, accD);
       GM_TRACE(5);
-      if (!grid_sync(a.bar, a.err, epoch)) return;
+      if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
       GM_TRACE(6);
       for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
         double v = __ldcg(accD + l);
@@ -570,7 +735,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       __syncthreads();
       owned_dots(a, s, s.w2, j + 2, accE);
       GM_TRACE(8);
-      if (!grid_sync(a.bar, a.err, epoch)) return;
+      if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
       GM_TRACE(9);
       for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
         double v = __ldcg(accE + l);
@@ -645,7 +810,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)(2 * m + 1) * m3;
          i += (size_t)G * blockDim.x)
       a.acc[i] = 0.0;
-    if (!grid_sync(a.bar, a.err, epoch)) return;
+    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
     for (int l = threadIdx.x; l < j; l += blockDim.x) s.hs1[l] = __ldcg(a.gs->y + l) * s.invb[l];
     __syncthreads();
     for (int i = threadIdx.x; i < ES; i += blockDim.x) {
@@ -655,7 +820,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       for (int l = 0; l < j; ++l) r += s.hs1[l] * (double)basis(a, s, l)[i];
       a.x[sl] = (S)r;
     }
-    if (!grid_sync(a.bar, a.err, epoch)) return;
+    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
     ++cycle;
     if (converged || breakdown || total >= a.maxit) break;
   }
@@ -670,4 +835,6 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     a.gs->scal[7] = cycle;
     a.gs->scal[6] = jlast;
   }
+  ms_drain(a, s, msd);
+#undef GM_FAIL
 }

@@ -449,7 +449,7 @@ struct smpm_handle_s {
   int* werr = nullptr;
   GState* wgs = nullptr;
   struct {
-    int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0;
+    int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0, stream_mats = 0, buf_elems = 0;
     size_t smem = 0, smem_pp = 0;
   } gm;  // launch shape of the persistent GMRES kernel
   double* wvown = nullptr;
@@ -612,6 +612,7 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol) {
   a.precond = h->opts.precond; a.m = h->opts.restart; a.maxit = h->opts.maxit; a.tol = tol;
   a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
   a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
+  a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems;
   a.trace = h->wtrace;
   a.trace_cap = h->wtrace ? kTraceCap : 0;
   return a;
@@ -631,6 +632,7 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   P.ga = gmres_args(h, tol);
   P.ga.mats_smem = 0;
   P.ga.basis_smem = 0;
+  P.ga.stream_mats = 0;
   P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
   P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
   P.chatb = h->wchatb; P.xs = h->wxs; P.u = u; P.acc = h->wacc8;
@@ -713,6 +715,7 @@ void smpm_default_opts(smpm_opts* o) {
   o->precond = 2;
   o->tau_scale = 1.0;
   o->robin_scale = 0.25;
+  o->flags = 0;
 }
 
 const char* smpm_last_error(void) { return g_last_error.c_str(); }
@@ -856,13 +859,27 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
     gm.ES = 2 * g.M * gm.nown_b;
     if (gm.ES % 2 == 0) gm.ES += 1;
     const int m = opts.restart;
-    gm.basis_smem = gm.mats_smem = 1;
+    // shared-memory layout of the owned data, in order of preference:
+    // resident matrices + basis; streamed matrices (two bulk-copy buffers) +
+    // basis; streamed matrices, basis in global memory; all global.
+    const bool no_smem = (opts.flags & SMPM_FLAG_NO_SMEM_RESIDENCY) != 0;
+    const bool force_stream = (opts.flags & SMPM_FLAG_STREAM_MATRICES) != 0;
+    const int buf = g.M * g.M + 4 * g.n * g.n;
     auto need = [&]() {
-      return gmres_smem_bytes<double>(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, gm.basis_smem, gm.mats_smem, g.d);
+      return gmres_smem_bytes<double>(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, gm.basis_smem, gm.mats_smem, g.d,
+                                      gm.stream_mats ? gm.buf_elems : 0);
     };
+    gm.basis_smem = no_smem ? 0 : 1;
+    gm.mats_smem = (no_smem || force_stream) ? 0 : 1;
+    gm.stream_mats = 0;
+    gm.buf_elems = buf;
     if (need() > (size_t)smem_optin) gm.mats_smem = 0;
+    if (!gm.mats_smem && !no_smem && opts.precond > 0) {
+      gm.stream_mats = 1;
+      if (need() > (size_t)smem_optin) gm.basis_smem = 0;
+      if (need() > (size_t)smem_optin) gm.stream_mats = 0;
+    }
     if (need() > (size_t)smem_optin) gm.basis_smem = 0;
-    if (need() > (size_t)smem_optin) return fail(SMPM_EINVAL, "restart length too large for the GMRES kernel");
     gm.smem = need();
     CU(cudaFuncSetAttribute(k_gmres<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem));
     int per_sm = 0;

@@ -86,8 +86,9 @@ def test_null_vectors(pair):
         assert np.linalg.norm(got - ref) < 1e-12
 
 
+@pytest.mark.parametrize("flags", [0, 1, 2], ids=["smem", "global", "stream"])
 @pytest.mark.parametrize("precond", [0, 1, 2])
-def test_solve_matches_oracle(pair, precond):
+def test_solve_matches_oracle(pair, precond, flags):
     og, osys, lg = pair
     x, y = og.coords()
     f = inputs.white_noise(og.r, 21)
@@ -96,7 +97,7 @@ def test_solve_matches_oracle(pair, precond):
     ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, b)
     alg = [methods.algorithm1, methods.algorithm2, methods.algorithm3][precond]
     uo, info = alg(osys, b, tol=1e-12, restart=50)
-    lg.factor(precond=precond, tol=1e-12)
+    lg.factor(precond=precond, tol=1e-12, flags=flags)
     u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
     rep = lg.solve(dev(f), u, g=dev(gslots), tol=1e-12)[0]
     uh = host(u)
