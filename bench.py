@@ -269,6 +269,61 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     gm_share = tot_ms / dev_ms
 
+    # ---- mixed precision (FP32 inner GMRES + FP64 refinement), same workload
+    g.factor(tol=W["tol"], restart=W["restart"], precision=1)
+    for _ in range(args.warmup):
+        g.solve(fd, ud)
+    barrier()
+    mix_ms = 0.0
+    mix_rep = None
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        mix_rep = g.solve(fd, ud)[0]
+        b_.record(stream)
+        torch.cuda.synchronize()
+        mix_ms += a_.elapsed_time(b_)
+    t = torch.tensor([mix_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mixed = {"value": world * args.steps / (float(t.item()) / 1e3), "unit": "solves/s",
+             "ms_per_step": float(t.item()) / args.steps, "inner_iterations": mix_rep["iterations"],
+             "refinements": mix_rep["refinements"], "schur_relres": mix_rep["schur_relres"],
+             "precision": "FP32 inner GMRES (FP32 operator, FP64 coarse/Givens/dot accumulation) + FP64 refinement"}
+
+    # ---- Schur apply y = S v (push form, one CTA per element) at a size
+    # whose factor does not stay in L2 between launches: 32x32 elements,
+    # n = 24 (T_e: 75.5 MB FP64, 37.7 MB FP32); L2 flushed before each launch.
+    ga = Grid(32, 32, 24)
+    ga.factor(precision=1, tol=W["tol"], restart=W["restart"])
+    Ma, nela = 4 * 24, 32 * 32
+    apply = {}
+    for name, dt, fn, sz in (("fp64", torch.float64, ga.apply_schur, 8), ("fp32", torch.float32, ga.apply_schur32, 4)):
+        va = torch.randn(ga.kp, dtype=dt, device="cuda")
+        ya = torch.empty_like(va)
+        for _ in range(3):
+            fn(va, ya)
+        times = []
+        for i in range(20):
+            flush.fill_(float(i))
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            fn(va, ya)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            times.append(a_.elapsed_time(b_))
+        us = 1e3 * sorted(times)[len(times) // 2]
+        byts = nela * (Ma * Ma + 3 * Ma) * sz
+        flo = 2.0 * nela * Ma * Ma
+        apply[name] = {"us_per_launch": us, "gbs": byts / (us * 1e-6) / 1e9,
+                       "hbm_frac": byts / (us * 1e-6) / 1e9 / hbm_peak, "tflops": flo / (us * 1e-6) / 1e12,
+                       "bytes_per_launch": byts}
+    ga.close()
+    schur_apply = {"workload": "y = S v, 32x32 elements, n=24 (kp = 98304), L2 flushed before each launch",
+                   "median_of": 20, **apply,
+                   "note": "FP64 is bound by the FP64 ALU (1.26 TFLOP/s) before HBM; FP32 is HBM-bound"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle runs in a fresh single-threaded process after the GPU timing
@@ -287,6 +342,8 @@ def run_ours(args):
                        "gmres_iterations": iters[-1], "wall_s": round(wall, 3),
                        "device_ms": {"pre": round(pre_ms, 4), "gmres": round(tot_ms / len(reps_timed), 4),
                                      "post": round(post_ms, 4)}},
+            "mixed": mixed,
+            "schur_apply": schur_apply,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},

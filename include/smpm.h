@@ -141,6 +141,10 @@ smpm_status schur_solve_host(smpm_handle h, const double* f, const double* g, do
 
 /* y = S v, S = I + B A^-1 E (Eq. schur_complement_system); v, y: kp. */
 smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream);
+/* y = S v in FP32 with the FP32 copy of the T_e factors (the operator of the
+ * inner GMRES of the mixed-precision path); v, y: kp floats.  Needs
+ * schur_factor with precision = 1 (else ESTATE). */
+smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* stream);
 /* t = M^-1 v, block-Jacobi of Sec. 2 / Fig. 2; v, t: kp. */
 smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream);
 /* y = S M^-1 v computed in the fused checkerboard form; v, y: kp. */

@@ -24,7 +24,7 @@ EXPORTS = [
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
-    "smpm_apply_deflation_noalloc",
+    "smpm_apply_deflation_noalloc", "smpm_apply_schur32",
 ]
 
 
@@ -72,7 +72,8 @@ def lib():
         L.schur_solve.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
         L.schur_solve_host.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
         for name in ["smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond", "smpm_apply_deflation",
-                     "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_apply_deflation_noalloc"]:
+                     "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_apply_deflation_noalloc",
+                     "smpm_apply_schur32"]:
             getattr(L, name).argtypes = [P, P, P, P]
         L.smpm_recover.argtypes = [P, P, P, P, P]
         L.smpm_null_vectors.argtypes = [P, P, P, P, P]
@@ -114,8 +115,8 @@ def _ptr(x):
         if x.dtype != np.float64 or not x.flags.c_contiguous:
             raise TypeError("arrays must be contiguous float64")
         return x.ctypes.data
-    if x.dtype.__str__() != "torch.float64" or not x.is_contiguous():
-        raise TypeError("tensors must be contiguous float64")
+    if str(x.dtype) not in ("torch.float64", "torch.float32") or not x.is_contiguous():
+        raise TypeError("tensors must be contiguous float64 (float32 for the FP32 operator)")
     return x.data_ptr()
 
 
@@ -208,6 +209,10 @@ class Grid:
 
     def apply_schur(self, v, out, stream=None):
         return self._op("smpm_apply_schur", v, out, stream)
+
+    def apply_schur32(self, v, out, stream=None):
+        """y = S v in FP32 (float32 tensors; needs factor(precision=1))."""
+        return self._op("smpm_apply_schur32", v, out, stream)
 
     def apply_precond(self, v, out, stream=None):
         return self._op("smpm_apply_precond", v, out, stream)

@@ -68,6 +68,8 @@ struct GmresArgs {
   int buf_elems;       // elements of S per stream buffer (>= M*M + 4*n*n, multiple of 16 bytes)
   long long* trace;
   int trace_cap;
+  const int* skip;  // when non-null and set on entry, the kernel returns at once
+  int* its_out;     // when non-null: Arnoldi steps of this launch
 };
 
 #define GM_TRACE(tag)                                                                   \
@@ -379,14 +381,13 @@ __device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, const S* Tw,
     s.cs[i] = ci;
   }
   __syncthreads();
-  if (with_c && threadIdx.x < 4) {
-    int F = threadIdx.x;
-    int j = dev_iface(g, e, F);
-    if (j >= 0) {
-      double sum = 0;
-      for (int tt = 0; tt < n; ++tt) sum += s.cs[F * n + tt];
-      a.c[j] = sum;
-    }
+  if (with_c && threadIdx.x < 128) {  // face F summed by warp F
+    const int F = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double sum = 0;
+    for (int tt = lane; tt < n; tt += 32) sum += s.cs[F * n + tt];
+    sum = warp_sum(sum);
+    const int j = dev_iface(g, e, F);
+    if (lane == 0 && j >= 0) a.c[j] = sum;
   }
   __syncthreads();
 }
@@ -481,17 +482,48 @@ __device__ void owned_dots(const GmresArgs<S>& a, const Smem<S>& s, const S* vec
     double sum = 0;
     if (l < nl) {
       const S* vl = (l == nl - 1) ? vec : basis(a, s, l);
-      double s0 = 0, s1 = 0;
-      int i = lane;
-      for (; i + P < E; i += 2 * P) {
-        s0 += (double)vl[i] * (double)vec[i];
-        s1 += (double)vl[i + P] * (double)vec[i + P];
+      if constexpr (sizeof(S) == 4) {
+        // FP32 products summed in FP32 over chunks of 16, chunks added in FP64
+        int i = lane, cnt = 0;
+        float f0 = 0.f;
+        for (; i < E; i += P) {
+          f0 = fmaf((float)vl[i], (float)vec[i], f0);
+          if (++cnt == 16) {
+            sum += (double)f0;
+            f0 = 0.f;
+            cnt = 0;
+          }
+        }
+        sum += (double)f0;
+      } else {
+        double s0 = 0, s1 = 0;
+        int i = lane;
+        for (; i + P < E; i += 2 * P) {
+          s0 += (double)vl[i] * (double)vec[i];
+          s1 += (double)vl[i + P] * (double)vec[i + P];
+        }
+        if (i < E) s0 += (double)vl[i] * (double)vec[i];
+        sum = s0 + s1;
       }
-      if (i < E) s0 += (double)vl[i] * (double)vec[i];
-      sum = s0 + s1;
     }
     for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
     if (l < nl && lane == 0 && sum != 0.0) atomicAdd(out + l, sum);
+  }
+}
+
+// base[i] - sum_{l < nl} coef[l] * basis(l)[i] for one owned entry; FP32
+// arithmetic for FP32 bases (coefficients rounded once), FP64 otherwise.
+template <typename S>
+__device__ __forceinline__ double basis_combo(const GmresArgs<S>& a, const Smem<S>& s, double base, const double* coef,
+                                              int nl, int i) {
+  if constexpr (sizeof(S) == 4) {
+    float r = (float)base;
+    for (int l = 0; l < nl; ++l) r = fmaf(-(float)coef[l], (float)basis(a, s, l)[i], r);
+    return (double)r;
+  } else {
+    double r = base;
+    for (int l = 0; l < nl; ++l) r -= coef[l] * (double)basis(a, s, l)[i];
+    return r;
   }
 }
 
@@ -581,6 +613,7 @@ __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, 
 template <typename S>
 __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.skip && *((volatile const int*)a.skip)) return;
   const Smem<S> s = carve(a, smraw);
   const DevGeo& g = a.g;
   const int M = g.M, n = g.n, m = a.m;
@@ -688,9 +721,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       S* vj = basis(a, s, j);
       if (j > 0) {
         for (int i = threadIdx.x; i < ES; i += blockDim.x) {
-          double r = (double)s.w2[i];
-          for (int l = 0; l < j; ++l) r -= s.hs2[l] * (double)basis(a, s, l)[i];
-          S rv = (S)r;
+          S rv = (S)basis_combo(a, s, (double)s.w2[i], s.hs2, j, i);
           vj[i] = rv;
           long long sl = entry_slot(a, i);
           if (sl >= 0) a.vglob[sl] = rv;
@@ -727,11 +758,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       }
       __syncthreads();
       // ---- E: w2 = w - V h1; V^T w2, ||w2||^2
-      for (int i = threadIdx.x; i < ES; i += blockDim.x) {
-        double r = (double)s.w[i];
-        for (int l = 0; l <= j; ++l) r -= s.hs1[l] * (double)basis(a, s, l)[i];
-        s.w2[i] = (S)r;
-      }
+      for (int i = threadIdx.x; i < ES; i += blockDim.x) s.w2[i] = (S)basis_combo(a, s, (double)s.w[i], s.hs1, j + 1, i);
       __syncthreads();
       owned_dots(a, s, s.w2, j + 2, accE);
       GM_TRACE(8);
@@ -811,14 +838,12 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
          i += (size_t)G * blockDim.x)
       a.acc[i] = 0.0;
     if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
-    for (int l = threadIdx.x; l < j; l += blockDim.x) s.hs1[l] = __ldcg(a.gs->y + l) * s.invb[l];
+    for (int l = threadIdx.x; l < j; l += blockDim.x) s.hs1[l] = -__ldcg(a.gs->y + l) * s.invb[l];
     __syncthreads();
     for (int i = threadIdx.x; i < ES; i += blockDim.x) {
       long long sl = entry_slot(a, i);
       if (sl < 0) continue;
-      double r = (double)ldcg(a.x + sl);
-      for (int l = 0; l < j; ++l) r += s.hs1[l] * (double)basis(a, s, l)[i];
-      a.x[sl] = (S)r;
+      a.x[sl] = (S)basis_combo(a, s, (double)ldcg(a.x + sl), s.hs1, j, i);
     }
     if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
     ++cycle;
@@ -834,6 +859,8 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     a.gs->nan = nan ? 1 : 0;
     a.gs->scal[7] = cycle;
     a.gs->scal[6] = jlast;
+    a.gs->scal[5] += total;  // iterations over all launches of a solve
+    if (a.its_out) *a.its_out = total;
   }
   ms_drain(a, s, msd);
 #undef GM_FAIL

@@ -47,10 +47,14 @@ struct PrePostArgs {
   double* zero[7];  // kp-long buffers zeroed in P1 (x, t, y, vglob, b_S, rhs, x_S)
   double* gacc;     // GMRES accumulators, zeroed in P1
   long long gacc_n;
+  float* zero32[4];  // kp-long FP32 buffers zeroed in P1 (mixed precision), or null
+  double* cr;        // d, zeroed in P1 (mixed precision), or null
+  float* rg32;       // kp, FP32 copy of the GMRES right-hand side (mixed precision), or null
+  int assembled;     // k_post: x_S is given in xs (skip the assembly)
 };
 
 // accumulator slots
-enum { ACC_ULB = 0, ACC_USBS = 1, ACC_MEAN = 2, ACC_RES = 3, ACC_BSN = 4 };
+enum { ACC_ULB = 0, ACC_USBS = 1, ACC_MEAN = 2, ACC_RES = 3, ACC_BSN = 4, ACC_RGN = 5 };
 
 __device__ double* fd_scratch(const Smem<double>& s) { return s.mats; }
 
@@ -75,8 +79,14 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
     for (int v = 0; v < 7; ++v) P.zero[v][i] = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.gacc_n; i += (long long)G * blockDim.x)
     P.gacc[i] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x) {
     P.cb[i] = 0.0;
+    if (P.cr) P.cr[i] = 0.0;
+  }
+  if (P.zero32[0])
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
+      for (int v = 0; v < 4; ++v) P.zero32[v][i] = 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->scal[5] = 0.0;  // inner iterations of the solve
   double part = 0;
   for (long long e = blockIdx.x; e < g.nel; e += G) {
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
@@ -151,7 +161,7 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
       P.chatb[j] = __ldcg(a.chat + j);
   }
   // ---- P4: owner entries: project b_S, rhs = P b_S
-  double bsn = 0;
+  double bsn = 0, rgn = 0;
   for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
     const long long sl = entry_slot(a, i);
     if (sl < 0) continue;
@@ -177,9 +187,15 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
       r -= acc;
     }
     P.rg[sl] = r;
+    if (P.rg32) P.rg32[sl] = (float)r;
+    rgn += r * r;
   }
   bsn = warp_sum(bsn);
-  if ((threadIdx.x & 31) == 0 && bsn != 0.0) atomicAdd(P.acc + ACC_BSN, bsn);
+  rgn = warp_sum(rgn);
+  if ((threadIdx.x & 31) == 0) {
+    if (bsn != 0.0) atomicAdd(P.acc + ACC_BSN, bsn);
+    if (rgn != 0.0) atomicAdd(P.acc + ACC_RGN, rgn);
+  }
 }
 
 __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
@@ -194,7 +210,9 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
   unsigned epoch = 0;
   int trace_n = 0;
   // ---- Q1-Q4: x_S
-  if (a.precond == 0) {
+  if (P.assembled) {
+    // x_S given (iterative refinement)
+  } else if (a.precond == 0) {
     for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
       const long long sl = entry_slot(a, i);
       if (sl >= 0) P.xs[sl] = __ldcg(a.x + sl);

@@ -40,7 +40,11 @@ constexpr int kSlotsPerBlock = 256;   // slots per CTA in the vector kernels
 constexpr int kElemThreads = 256;     // threads per element CTA
 constexpr int kTraceCap = 1 << 16;    // entries of the optional phase trace
 constexpr int kGmresThreads = 256;    // threads per CTA of the persistent GMRES kernel
-constexpr size_t kCtlBytes = 32 + 8 * sizeof(double);  // barrier counters, error flag, accumulators
+// per-solve control block (zeroed by one memset): 64 barrier counters |
+// err, done, nref | 8 accumulators | 32 refinement residual norms
+constexpr size_t kCtlBytes = 720;  // + 32 inner iteration counts
+constexpr int kMaxRefine = 8;        // FP64 refinement steps of the mixed-precision path
+constexpr double kInnerTol = 1e-4;   // relative tolerance of each FP32 inner GMRES
 
 struct GState {
   double tolabs, beta0, beta, wnorm0sq, resid;
@@ -421,6 +425,7 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
 
 #include "smpm_gmres.cuh"
 #include "smpm_prepost.cuh"
+#include "smpm_refine.cuh"
 
 // ------------------------------------------------------------- host side
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -454,6 +459,15 @@ struct smpm_handle_s {
   } gm;  // launch shape of the persistent GMRES kernel
   double* wvown = nullptr;
   double* wacc = nullptr;
+  // mixed precision: FP32 operator copies and work vectors, FP64 residual
+  float *dT32 = nullptr, *dG32 = nullptr, *dX32 = nullptr, *dRs32 = nullptr;
+  float *wx32 = nullptr, *wt32 = nullptr, *wy32 = nullptr, *wV32 = nullptr, *wrg32 = nullptr, *wvown32 = nullptr;
+  double *wr = nullptr, *wcr = nullptr, *wrn = nullptr;
+  int *wdone = nullptr, *wnref = nullptr;
+  struct {
+    int basis_smem = 0, mats_smem = 0, stream_mats = 0, buf_elems = 0;
+    size_t smem = 0, smem_ref = 0;
+  } gm32;
   double *wacc8 = nullptr, *wxs = nullptr, *dZtuS = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the GMRES kernel of each solve
   cudaEvent_t evp = nullptr, evq = nullptr;  // start of k_pre, end of k_post
@@ -597,9 +611,41 @@ smpm_status print_trace(smpm_handle h, cudaStream_t st) {
   return SMPM_OK;
 }
 
+// Shared-memory layout of the owned data of the GMRES kernel, in order of
+// preference: resident matrices + basis; streamed matrices (two bulk-copy
+// buffers) + basis; streamed matrices with the basis in global memory; all
+// global.
+struct Layout {
+  int basis_smem, mats_smem, stream_mats, buf_elems;
+  size_t smem;
+};
+
+template <typename S>
+Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, int precond, bool no_smem,
+                     bool force_stream, int smem_optin) {
+  Layout L;
+  L.buf_elems = g.M * g.M + 4 * g.n * g.n;
+  L.basis_smem = no_smem ? 0 : 1;
+  L.mats_smem = (no_smem || force_stream) ? 0 : 1;
+  L.stream_mats = 0;
+  auto need = [&]() {
+    return gmres_smem_bytes<S>(m, g.M, g.n, ES, nown_b, nown_w, L.basis_smem, L.mats_smem, g.d,
+                               L.stream_mats ? L.buf_elems : 0);
+  };
+  if (need() > (size_t)smem_optin) L.mats_smem = 0;
+  if (!L.mats_smem && !no_smem && precond > 0) {
+    L.stream_mats = 1;
+    if (need() > (size_t)smem_optin) L.basis_smem = 0;
+    if (need() > (size_t)smem_optin) L.stream_mats = 0;
+  }
+  if (need() > (size_t)smem_optin) L.basis_smem = 0;
+  L.smem = need();
+  return L;
+}
+
 // Kernel arguments shared by the three cooperative kernels of a solve.
 GmresArgs<double> gmres_args(smpm_handle h, double tol) {
-  GmresArgs<double> a;
+  GmresArgs<double> a{};
   a.g = h->dg;
   a.black = h->dblack;
   a.white = h->dwhite;
@@ -615,20 +661,171 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol) {
   a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems;
   a.trace = h->wtrace;
   a.trace_cap = h->wtrace ? kTraceCap : 0;
+  a.skip = nullptr;
   return a;
+}
+
+GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
+  GmresArgs<float> a{};
+  a.g = h->dg;
+  a.black = h->dblack;
+  a.white = h->dwhite;
+  a.nblack = (int)h->f.black.size();
+  a.nwhite = (int)h->f.white.size();
+  a.Tc = h->dT32; a.Gc = h->dG32; a.Xc = h->dX32; a.Rs = h->dRs32; a.H = h->dH;
+  a.vglob = h->wV32; a.vown = h->wvown32; a.t = h->wt32; a.y = h->wy32;
+  a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg32; a.x = h->wx32;
+  a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
+  a.precond = h->opts.precond; a.m = h->opts.restart; a.maxit = h->opts.restart; a.tol = tol;
+  a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
+  a.mats_smem = h->gm32.mats_smem; a.basis_smem = h->gm32.basis_smem;
+  a.stream_mats = h->gm32.stream_mats; a.buf_elems = h->gm32.buf_elems;
+  a.trace = nullptr;
+  a.trace_cap = 0;
+  a.skip = h->wdone;
+  return a;
+}
+
+// One right-hand side, FP32 inner GMRES inside FP64 iterative refinement
+// (GMRES-IR): k_pre, then kMaxRefine pairs (k_gmres<float>, k_refine) that
+// return at once after convergence, then k_post on the assembled x_S.
+smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, double* u, double tol,
+                            smpm_report* rep, cudaStream_t st) {
+  const int m = h->opts.restart;
+  smpm_report R{};
+  const long long launches0 = h->launches;
+  CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
+  PrePostArgs P{};
+  P.ga = gmres_args(h, tol);
+  P.ga.mats_smem = 0;
+  P.ga.basis_smem = 0;
+  P.ga.stream_mats = 0;
+  P.ga.trace = nullptr;
+  P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
+  P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
+  P.chatb = h->wchatb; P.xs = h->wxs; P.u = u; P.acc = h->wacc8;
+  double* zs[7] = {h->wx, h->wt, h->wy, h->wV, h->wbS, h->wrg, h->wxs};
+  for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+  P.gacc = h->wacc;
+  P.gacc_n = (long long)(2 * m + 1) * (m + 3);
+  float* z32[4] = {h->wx32, h->wt32, h->wy32, h->wV32};
+  for (int i = 0; i < 4; ++i) P.zero32[i] = z32[i];
+  P.cr = h->wcr;
+  P.rg32 = h->wrg32;
+  P.assembled = 0;
+  CU(cudaEventRecord(h->evp, st));
+  {
+    P.ga.bar = h->wbar + 0;
+    void* args[] = {&P};
+    CU(cudaLaunchCooperativeKernel((const void*)k_pre, dim3(h->gm.grid), dim3(kGmresThreads), args, h->gm.smem_pp,
+                                   st));
+    CHECK_LAUNCH();
+  }
+  CU(cudaEventRecord(h->ev0, st));
+  for (int ref = 0; ref < kMaxRefine; ++ref) {
+    GmresArgs<float> a = gmres_args32(h, kInnerTol);
+    a.bar = h->wbar + 2 + 2 * ref;
+    a.its_out = reinterpret_cast<int*>(h->wctl + 592) + ref;
+    if (ref == 0 && h->wtrace) {
+      a.trace = h->wtrace;
+      a.trace_cap = kTraceCap;
+    }
+    {
+      void* args[] = {&a};
+      CU(cudaLaunchCooperativeKernel((const void*)k_gmres<float>, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                     h->gm32.smem, st));
+      CHECK_LAUNCH();
+    }
+    RefineArgs RA{};
+    RA.ga = a;
+    RA.ga.mats_smem = 0;
+    RA.ga.basis_smem = 0;
+    RA.ga.stream_mats = 0;
+    RA.ga.bar = h->wbar + 3 + 2 * ref;
+    RA.ga.rhs = h->wrg32;
+    RA.Tc64 = h->dT;
+    RA.Rs64 = h->dRs;
+    RA.xS = h->wxs;
+    RA.bS = h->wbS;
+    RA.r = h->wr;
+    RA.cr = h->wcr;
+    RA.chat_r = h->wchatb;
+    RA.rgn = h->wacc8 + ACC_RGN;
+    RA.rn = h->wrn + ref;
+    RA.done = h->wdone;
+    RA.nref = h->wnref;
+    RA.rhs32 = h->wrg32;
+    RA.tol = tol;
+    void* args[] = {&RA};
+    CU(cudaLaunchCooperativeKernel((const void*)k_refine, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                   h->gm32.smem_ref, st));
+    CHECK_LAUNCH();
+  }
+  CU(cudaEventRecord(h->ev1, st));
+  {
+    P.ga.bar = h->wbar + 1;
+    P.assembled = 1;
+    void* args[] = {&P};
+    CU(cudaLaunchCooperativeKernel((const void*)k_post, dim3(h->gm.grid), dim3(kGmresThreads), args, h->gm.smem_pp,
+                                   st));
+    CHECK_LAUNCH();
+    CU(cudaEventRecord(h->evq, st));
+  }
+  int herr = 0, done = 0, nref = 0;
+  double acc8[8], rn[32], scal[8];
+  CU(cudaMemcpyAsync(&herr, h->werr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&done, h->wdone, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&nref, h->wnref, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(acc8, h->wacc8, sizeof(acc8), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(rn, h->wrn, sizeof(rn), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(scal, reinterpret_cast<char*>(h->wgs) + offsetof(GState, scal), sizeof(scal),
+                     cudaMemcpyDeviceToHost, st));
+  int its[32];
+  CU(cudaMemcpyAsync(its, h->wctl + 592, sizeof(its), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (herr) return fail(SMPM_ETIMEOUT, "a grid barrier or copy wait of the solve kernels timed out");
+  if (h->wtrace) {
+    std::fprintf(stderr, "[smpm trace] refinement rounds:");
+    for (int i = 0; i < nref && i < 32; ++i)
+      std::fprintf(stderr, " (%d inner, |r|^2 %.3e)", its[i], rn[i]);
+    std::fprintf(stderr, "  |P b_S|^2 %.3e\n", acc8[ACC_RGN]);
+    print_trace(h, st);
+  }
+  R.iterations = (int)scal[5];
+  R.refinements = nref;
+  R.converged = done ? 1 : 0;
+  const double rho = nref > 0 ? std::sqrt(rn[nref - 1]) : 0.0;
+  R.gmres_relres = acc8[ACC_RGN] > 0 ? rho / std::sqrt(acc8[ACC_RGN]) : 0.0;
+  R.schur_relres = acc8[ACC_BSN] > 0 ? std::sqrt(acc8[ACC_RES] / acc8[ACC_BSN]) : 0.0;
+  if (!std::isfinite(R.gmres_relres) || !std::isfinite(R.schur_relres))
+    return fail(SMPM_ENAN, "non-finite value in the right-hand side or the refinement");
+  {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    R.gmres_ms = ms;
+    CU(cudaEventElapsedTime(&ms, h->evp, h->ev0));
+    R.pre_ms = ms;
+    CU(cudaEventElapsedTime(&ms, h->ev1, h->evq));
+    R.post_ms = ms;
+  }
+  R.launches = (int)(h->launches - launches0);
+  if (rep) *rep = R;
+  if (!done && acc8[ACC_RGN] > 0) return fail(SMPM_ENOTCONV, "iterative refinement did not reach tol");
+  return SMPM_OK;
 }
 
 // One right-hand side, FP64, Algorithms 1-3: three cooperative launches
 // (k_pre, k_gmres, k_post) and one host synchronisation for the report.
 smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* u, double tol, smpm_report* rep,
                       cudaStream_t st) {
+  if (h->opts.precision == 1) return solve_one_mixed(h, f, gn, u, tol, rep, st);
   const int m = h->opts.restart;
   smpm_report R{};
   const long long launches0 = h->launches;
   // one memset per solve: barrier counters of the three kernels, error flag,
   // pre/post accumulators (contiguous); everything else is zeroed in k_pre
   CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
-  PrePostArgs P;
+  PrePostArgs P{};
   P.ga = gmres_args(h, tol);
   P.ga.mats_smem = 0;
   P.ga.basis_smem = 0;
@@ -859,32 +1056,50 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
     gm.ES = 2 * g.M * gm.nown_b;
     if (gm.ES % 2 == 0) gm.ES += 1;
     const int m = opts.restart;
-    // shared-memory layout of the owned data, in order of preference:
-    // resident matrices + basis; streamed matrices (two bulk-copy buffers) +
-    // basis; streamed matrices, basis in global memory; all global.
     const bool no_smem = (opts.flags & SMPM_FLAG_NO_SMEM_RESIDENCY) != 0;
     const bool force_stream = (opts.flags & SMPM_FLAG_STREAM_MATRICES) != 0;
-    const int buf = g.M * g.M + 4 * g.n * g.n;
-    auto need = [&]() {
-      return gmres_smem_bytes<double>(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, gm.basis_smem, gm.mats_smem, g.d,
-                                      gm.stream_mats ? gm.buf_elems : 0);
-    };
-    gm.basis_smem = no_smem ? 0 : 1;
-    gm.mats_smem = (no_smem || force_stream) ? 0 : 1;
-    gm.stream_mats = 0;
-    gm.buf_elems = buf;
-    if (need() > (size_t)smem_optin) gm.mats_smem = 0;
-    if (!gm.mats_smem && !no_smem && opts.precond > 0) {
-      gm.stream_mats = 1;
-      if (need() > (size_t)smem_optin) gm.basis_smem = 0;
-      if (need() > (size_t)smem_optin) gm.stream_mats = 0;
+    {
+      Layout L = choose_layout<double>(g, m, gm.ES, gm.nown_b, gm.nown_w, opts.precond, no_smem, force_stream,
+                                       smem_optin);
+      gm.basis_smem = L.basis_smem;
+      gm.mats_smem = L.mats_smem;
+      gm.stream_mats = L.stream_mats;
+      gm.buf_elems = L.buf_elems;
+      gm.smem = L.smem;
     }
-    if (need() > (size_t)smem_optin) gm.basis_smem = 0;
-    gm.smem = need();
     CU(cudaFuncSetAttribute(k_gmres<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem));
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<double>, kGmresThreads, gm.smem));
     if (per_sm < 1) return fail(SMPM_ECUDA, "the GMRES kernel does not fit on an SM");
+    if (opts.precision == 1) {
+      // FP32 inner GMRES: FP32 copies of the operator, its own layout, the
+      // refinement kernel, FP32 work vectors and the FP64 residual
+      Layout L = choose_layout<float>(g, m, gm.ES, gm.nown_b, gm.nown_w, opts.precond, no_smem, force_stream,
+                                      smem_optin);
+      auto& g32 = h->gm32;
+      g32.basis_smem = L.basis_smem;
+      g32.mats_smem = L.mats_smem;
+      g32.stream_mats = L.stream_mats;
+      g32.buf_elems = L.buf_elems;
+      g32.smem = L.smem;
+      CU(cudaFuncSetAttribute(k_gmres<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g32.smem));
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<float>, kGmresThreads, g32.smem));
+      if (per_sm < 1) return fail(SMPM_ECUDA, "the FP32 GMRES kernel does not fit on an SM");
+      g32.smem_ref = refine_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
+      if (g32.smem_ref > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the refinement kernel");
+      CU(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g32.smem_ref));
+      CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, kGmresThreads, g32.smem_ref));
+      if (per_sm < 1) return fail(SMPM_ECUDA, "the refinement kernel does not fit on an SM");
+      auto to32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+      if ((s = upload(h, &h->dT32, to32(Tc), st)) || (s = upload(h, &h->dG32, to32(Gc), st)) ||
+          (s = upload(h, &h->dX32, to32(Xc), st)) || (s = upload(h, &h->dRs32, to32(h->f.Rs), st)))
+        return s;
+      if ((s = dalloc(h, &h->wx32, g.kp)) || (s = dalloc(h, &h->wt32, g.kp)) || (s = dalloc(h, &h->wy32, g.kp)) ||
+          (s = dalloc(h, &h->wV32, g.kp)) || (s = dalloc(h, &h->wrg32, g.kp)) || (s = dalloc(h, &h->wr, g.kp)) ||
+          (s = dalloc(h, &h->wcr, g.d)))
+        return s;
+      if (!g32.basis_smem && (s = dalloc(h, &h->wvown32, (size_t)gm.grid * (m + 1) * gm.ES))) return s;
+    }
     gm.smem_pp = prepost_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
     if (gm.smem_pp > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the solve kernels");
     CU(cudaFuncSetAttribute(k_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem_pp));
@@ -904,8 +1119,11 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
     if ((s = upload(h, &h->dZtuS, ztus, st))) return s;
     if ((s = dalloc(h, &h->wctl, kCtlBytes)) || (s = dalloc(h, &h->wxs, g.kp))) return s;
     h->wbar = reinterpret_cast<unsigned*>(h->wctl);
-    h->werr = reinterpret_cast<int*>(h->wctl + 16);
-    h->wacc8 = reinterpret_cast<double*>(h->wctl + 32);
+    h->werr = reinterpret_cast<int*>(h->wctl + 256);
+    h->wdone = reinterpret_cast<int*>(h->wctl + 260);
+    h->wnref = reinterpret_cast<int*>(h->wctl + 264);
+    h->wacc8 = reinterpret_cast<double*>(h->wctl + 272);
+    h->wrn = reinterpret_cast<double*>(h->wctl + 336);
     if ((s = dalloc(h, &h->wacc, (size_t)(2 * m + 1) * (m + 3)))) return s;
     if (!gm.basis_smem && (s = dalloc(h, &h->wvown, (size_t)gm.grid * (m + 1) * gm.ES))) return s;
   }
@@ -918,7 +1136,6 @@ smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double
                         smpm_report* rep, void* stream) {
   if (!h || !f || !u || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
   if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
-  if (h->opts.precision != 0) return fail(SMPM_EINVAL, "precision mode not available in this build");
   double t = tol > 0 ? tol : h->opts.tol;
   cudaStream_t st = as_stream(stream);
   smpm_status worst = SMPM_OK;
@@ -961,6 +1178,16 @@ smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* st
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   return launch_schur(h, v, y, as_stream(stream));
+}
+
+smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* stream) {
+  NEED_FACTOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
+  const DevGeo& g = h->dg;
+  k_schur<float><<<(unsigned)g.nel, kElemThreads, 2 * g.M * sizeof(float), as_stream(stream)>>>(g, h->dT32, v, y);
+  CHECK_LAUNCH();
+  return SMPM_OK;
 }
 
 smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream) {

@@ -206,3 +206,37 @@ def test_config2_full_size(built):
     assert rel(host(u), uo) < 1e-9
     ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, f)
     assert rel(host(u), ud) < 1e-8
+
+
+@pytest.mark.parametrize("flags", [0, 2], ids=["smem", "stream"])
+def test_mixed_precision_matches_oracle(pair, flags):
+    """FP32 inner GMRES inside FP64 iterative refinement: the solution
+    matches the exact discrete solution to a relative L2 error of 1e-9."""
+    og, osys, lg = pair
+    if og.d < 2:
+        pytest.skip("single interface")
+    f = inputs.white_noise(og.r, 23)
+    gslots = np.random.default_rng(24).standard_normal(og.kp)
+    b = og.rhs(f, gslots)
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, b)
+    lg.factor(precision=1, tol=1e-11, flags=flags)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(dev(f), u, g=dev(gslots))[0]
+    assert rep["converged"] == 1 and rep["refinements"] >= 1, rep
+    assert rel(host(u), ud) < 1e-9, (rep, rel(host(u), ud))
+    lg.factor()
+
+
+def test_fp32_schur_apply(built):
+    """The FP32 operator of the inner GMRES agrees with the FP64 S to FP32
+    round-off (relative 1e-5)."""
+    og = SMPMGrid(5, 4, 7)
+    osys = SchurSystem(og)
+    lg = Grid(5, 4, 7)
+    lg.factor(precision=1)
+    v = np.random.default_rng(41).standard_normal(og.k)
+    vp = torch.as_tensor(og.to_padded(v), dtype=torch.float32, device="cuda")
+    out = torch.zeros(og.kp, dtype=torch.float32, device="cuda")
+    lg.apply_schur32(vp, out)
+    got = og.from_padded(out.double().cpu().numpy())
+    assert rel(got, osys.apply_S(v)) < 1e-5
