@@ -23,9 +23,13 @@ schur    S = I + B A^-1 E (Eq. schur_complement_system), null vectors u_L, u_S
 gmres    Restarted GMRES with modified Gram-Schmidt and Givens rotations.
 methods  Algorithms 1, 2, 3, the direct bordered solve of L u = f~ and the
          zero-mean normalisation.
+adjoint  Reverse-mode derivative of u(f, g): the transposed bordered direct
+         solve and Algorithm 3 on S^T (transposed blocks, C^T, swapped null
+         vectors), with dl/df and dl/dg.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (closed forms, the Fig. 1 node list, polynomial exactness, spectral
 convergence, operator identities, agreement of Algorithms 1-3 with the direct
-solve).  No function is "parity unpinned".
+solve; for the adjoint, brute-force transposition of the forward map, the
+inner-product identity and central differences).  No function is "parity unpinned".
 """
