@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile", choices=["gmres", "apply"], default=None,
+                   help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
 
 
@@ -371,9 +373,44 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ ncu cases
+def run_profile(which):
+    """Small fixed cases for ncu captures: `gmres` runs three solves of the
+    bench workload (FP64), `apply` three y = S v launches each in FP32 and
+    FP64 on 32x32 elements, n = 24.  Prints "ok" and no bench line."""
+    import torch
+    from paper_1601_03432_gb300 import Grid, inputs
+    from paper_1601_03432_gb300.build import build
+    build()
+    W = WORKLOAD
+    if which == "gmres":
+        g = Grid(W["mx"], W["my"], W["n"])
+        g.factor(tol=W["tol"], restart=W["restart"])
+        x, y = g.node_coords()
+        f, _ = inputs.fourier_rhs(x, y, seed=W["seed"])
+        fd = torch.as_tensor(f, dtype=torch.float64, device="cuda")
+        ud = torch.zeros_like(fd)
+        for _ in range(3):
+            g.solve(fd, ud)
+    else:
+        g = Grid(32, 32, 24)
+        g.factor(tol=W["tol"], restart=W["restart"], precision=1)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        for dt, fn in ((torch.float32, g.apply_schur32), (torch.float64, g.apply_schur)):
+            v = torch.randn(g.kp, dtype=dt, device="cuda", generator=gen)
+            yv = torch.empty_like(v)
+            for _ in range(3):
+                fn(v, yv)
+    torch.cuda.synchronize()
+    g.close()
+    print("ok")
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a.profile)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
