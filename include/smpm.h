@@ -71,6 +71,7 @@ typedef struct {
  * large-grid layouts, selectable for testing). */
 #define SMPM_FLAG_NO_SMEM_RESIDENCY 1
 #define SMPM_FLAG_STREAM_MATRICES 2
+#define SMPM_FLAG_ADJOINT 4        /* also build the transposed system for schur_solve_adjoint */
 
 /* Per-solve report, written by schur_solve when the pointer is non-null. */
 typedef struct {
@@ -129,6 +130,26 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream);
  * ENAN, ECUDA. */
 smpm_status schur_solve(smpm_handle h, const double* f, const double* g, double tol,
                         int nrhs, double* u, smpm_report* rep, void* stream);
+
+/* Reverse-mode derivative of schur_solve: for a loss l(u) with
+ * gbar_u = dl/du, returns gbar_f = dl/df and gbar_g = dl/dg.  The solve is
+ * linear in (f, g): b = f + tau g (Eq. smpm_poisson), b~ = b - u_L u_L^T b
+ * (Eq. regularize_poisson), L z = b~, u = z - (w^T z / 1^T w) 1, so
+ *   dl/db = Pi lam,  L^T lam = N^T gbar_u,  N^T y = y - w (1^T y) / 1^T w,
+ * with Pi = I - u_L u_L^T.  L^T lam = N^T gbar_u is solved by Algorithm 3 on
+ * the transposed Schur system S^T = I + E^T A^-T B^T (Sec. 1.3 transposed):
+ * transposed block-Jacobi blocks, the same interface indicators Z, coarse
+ * matrix C^T (left null vector c0, right null vector u_C), left null vector
+ * B 1 of S^T; then lam = A^-T (y - B^T mu) for the interface solution mu.
+ *   gbar_u : device, r * nrhs
+ *   gbar_f : device, r * nrhs, output (dl/df = dl/db)
+ *   gbar_g : device, kp * nrhs, output or null; tau_F dl/db at the face node
+ *            on physical-boundary slots, 0 on interface slots
+ * Always FP64 (also on a handle factored with precision 1).  Needs
+ * schur_factor with SMPM_FLAG_ADJOINT in opts.flags (else ESTATE).  rep and
+ * errors as schur_solve. */
+smpm_status schur_solve_adjoint(smpm_handle h, const double* gbar_u, double tol, int nrhs,
+                                double* gbar_f, double* gbar_g, smpm_report* rep, void* stream);
 
 /* As schur_solve, with f, g and u in HOST memory: the library copies the
  * inputs to its device staging buffers, solves, and copies u back before

@@ -13,6 +13,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmpm.so")
 
+FLAG_NO_SMEM_RESIDENCY, FLAG_STREAM_MATRICES, FLAG_ADJOINT = 1, 2, 4
+
 SMPM_OK, SMPM_EINVAL, SMPM_ENOINTERFACE, SMPM_ENOMEM, SMPM_ECUDA, SMPM_ENOTCONV, SMPM_EBREAKDOWN, SMPM_ENAN, \
     SMPM_ESTATE, SMPM_ETIMEOUT = range(10)
 STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "EBREAKDOWN", "ENAN", "ESTATE",
@@ -24,7 +26,7 @@ EXPORTS = [
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
-    "smpm_apply_deflation_noalloc", "smpm_apply_schur32",
+    "smpm_apply_deflation_noalloc", "smpm_apply_schur32", "schur_solve_adjoint",
 ]
 
 
@@ -71,6 +73,7 @@ def lib():
         L.schur_factor.argtypes = [P, ctypes.POINTER(SmpmOpts), P]
         L.schur_solve.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
         L.schur_solve_host.argtypes = [P, P, P, D, I, P, ctypes.POINTER(SmpmReport), P]
+        L.schur_solve_adjoint.argtypes = [P, P, D, I, P, P, ctypes.POINTER(SmpmReport), P]
         for name in ["smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond", "smpm_apply_deflation",
                      "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_apply_deflation_noalloc",
                      "smpm_apply_schur32"]:
@@ -193,6 +196,15 @@ class Grid:
         """schur_solve on device tensors (float64, contiguous); returns the reports."""
         reps = (SmpmReport * nrhs)()
         st = lib().schur_solve(self.h, _ptr(f), _ptr(g), float(tol), nrhs, _ptr(u), reps, _stream(stream))
+        check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
+        return [r.as_dict() for r in reps]
+
+    def solve_adjoint(self, gbar_u, gbar_f, gbar_g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
+        """schur_solve_adjoint on device tensors: dl/df (and dl/dg) from dl/du;
+        needs factor(flags=FLAG_ADJOINT)."""
+        reps = (SmpmReport * nrhs)()
+        st = lib().schur_solve_adjoint(self.h, _ptr(gbar_u), float(tol), nrhs, _ptr(gbar_f), _ptr(gbar_g), reps,
+                                       _stream(stream))
         check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
         return [r.as_dict() for r in reps]
 

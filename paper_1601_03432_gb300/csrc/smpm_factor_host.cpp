@@ -494,6 +494,93 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   return SMPM_OK;
 }
 
+// Row sums of T_e over each input face: Rs[row * 4 + G] = sum_q T_e[row, G n + q]
+// (the pushed part of S Z, one column per face of e).
+void row_sums(const Geometry& g, const std::vector<double>& T, std::vector<double>* Rs) {
+  const int n = g.n, M = g.M;
+  Rs->assign(static_cast<size_t>(g.nel) * M * 4, 0.0);
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e) {
+    const double* Te = T.data() + static_cast<size_t>(e) * M * M;
+    double* R = Rs->data() + static_cast<size_t>(e) * M * 4;
+    for (int row = 0; row < M; ++row)
+      for (int G = 0; G < 4; ++G) {
+        double acc = 0;
+        for (int q = 0; q < n; ++q) acc += Te[row * M + G * n + q];
+        R[row * 4 + G] = acc;
+      }
+  }
+}
+
+// Block-Jacobi factors of the checkerboard blocks of I + (push form of T)
+// (Sec. 2, Fig. 2): per black element the X_F blocks (the neighbours' T rows
+// facing e, restricted to their slots facing e) and G = (I - X Y)^-1 with
+// Y = T_e; identical blocks (same face-type masks) share one inversion.
+int block_factors(const Geometry& g, const std::vector<int>& black, const std::vector<double>& T,
+                  std::vector<double>* Gout, std::vector<double>* Xout, std::string* err) {
+  const int n = g.n, M = g.M;
+  const size_t nb = black.size();
+  Gout->assign(nb * M * M, 0.0);
+  Xout->assign(nb * 4 * n * n, 0.0);
+  std::map<long long, std::vector<double>> gcache;
+  for (size_t ib = 0; ib < nb; ++ib) {
+    int e = black[ib];
+    double* X = Xout->data() + ib * 4 * n * n;
+    long long key = g.mask(e);
+    for (int F = 0; F < 4; ++F) {
+      int e2 = g.neighbour(e, F);
+      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
+      if (e2 < 0) continue;
+      const double* T2 = T.data() + static_cast<size_t>(e2) * M * M;
+      int Fo = opposite(F);
+      for (int t = 0; t < n; ++t)
+        for (int q = 0; q < n; ++q) X[(F * n + t) * n + q] = T2[(Fo * n + t) * M + Fo * n + q];
+    }
+    if (!gcache.count(key)) {
+      const double* Y = T.data() + static_cast<size_t>(e) * M * M;
+      std::vector<double> A(static_cast<size_t>(M) * M, 0.0);
+      for (int F = 0; F < 4; ++F)
+        for (int t = 0; t < n; ++t)
+          for (int col = 0; col < M; ++col) {
+            double acc = 0;
+            for (int q = 0; q < n; ++q) acc += X[(F * n + t) * n + q] * Y[(F * n + q) * M + col];
+            A[(F * n + t) * M + col] = (F * n + t == col ? 1.0 : 0.0) - acc;
+          }
+      DenseLU lu = lu_factor(A.data(), M);
+      if (!lu.ok) { *err = "singular block-Jacobi block"; return SMPM_EINVAL; }
+      std::vector<double> Gi(static_cast<size_t>(M) * M), col(M);
+      for (int j = 0; j < M; ++j) {
+        std::fill(col.begin(), col.end(), 0.0);
+        col[j] = 1.0;
+        lu_solve(lu, col.data());
+        for (int i = 0; i < M; ++i) Gi[i * M + j] = col[i];
+      }
+      gcache[key] = Gi;
+    }
+    const std::vector<double>& Gi = gcache.at(key);
+    std::memcpy(Gout->data() + ib * M * M, Gi.data(), sizeof(double) * M * M);
+  }
+  return SMPM_OK;
+}
+
+// Transposed fast diagonalisation: K = V diag(lam) Vinv gives
+// K^T = Vinv^T diag(lam) V^T, stored in the same (V, Vinv, lam) layout.
+void transpose_fd(int n, const std::vector<double>& fd, std::vector<double>* out) {
+  const size_t fds = 2 * (size_t)n * n + n;
+  out->assign(fd.size(), 0.0);
+  for (size_t cls = 0; cls * fds < fd.size(); ++cls) {
+    const double* V = fd.data() + cls * fds;
+    const double* Vi = V + n * n;
+    double* W = out->data() + cls * fds;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        W[i * n + j] = Vi[j * n + i];
+        W[n * n + i * n + j] = V[j * n + i];
+      }
+    for (int i = 0; i < n; ++i) W[2 * n * n + i] = V[2 * n * n + i];
+  }
+}
+
 }  // namespace
 
 // -------------------------------------------------------------- public
@@ -601,63 +688,15 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
     const std::vector<double>& T = tcache.at(g.mask(static_cast<int>(e)));
     std::memcpy(f->T.data() + static_cast<size_t>(e) * M * M, T.data(), sizeof(double) * M * M);
   }
-  f->Rs.assign(static_cast<size_t>(g.nel) * M * 4, 0.0);
-#pragma omp parallel for schedule(static)
-  for (long long e = 0; e < g.nel; ++e) {
-    const double* T = f->T.data() + static_cast<size_t>(e) * M * M;
-    double* R = f->Rs.data() + static_cast<size_t>(e) * M * 4;
-    for (int row = 0; row < M; ++row)
-      for (int G = 0; G < 4; ++G) {
-        double s = 0;
-        for (int q = 0; q < n; ++q) s += T[row * M + G * n + q];
-        R[row * 4 + G] = s;
-      }
-  }
+  row_sums(g, f->T, &f->Rs);
 
   // checkerboard blocks
   f->black.clear();
   f->white.clear();
   for (long long e = 0; e < g.nel; ++e) (g.black(static_cast<int>(e)) ? f->black : f->white).push_back(static_cast<int>(e));
-  const size_t nb = f->black.size();
-  f->G.assign(nb * M * M, 0.0);
-  f->X.assign(nb * 4 * n * n, 0.0);
-  std::map<long long, std::vector<double>> gcache;
-  for (size_t ib = 0; ib < nb; ++ib) {
-    int e = f->black[ib];
-    double* X = f->X.data() + ib * 4 * n * n;
-    long long key = g.mask(e);
-    for (int F = 0; F < 4; ++F) {
-      int e2 = g.neighbour(e, F);
-      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
-      if (e2 < 0) continue;
-      const double* T2 = f->T.data() + static_cast<size_t>(e2) * M * M;
-      int Fo = opposite(F);
-      for (int t = 0; t < n; ++t)
-        for (int s = 0; s < n; ++s) X[(F * n + t) * n + s] = T2[(Fo * n + t) * M + Fo * n + s];
-    }
-    if (!gcache.count(key)) {
-      const double* Y = f->T.data() + static_cast<size_t>(e) * M * M;
-      std::vector<double> A(static_cast<size_t>(M) * M, 0.0);
-      for (int F = 0; F < 4; ++F)
-        for (int t = 0; t < n; ++t)
-          for (int col = 0; col < M; ++col) {
-            double s = 0;
-            for (int q = 0; q < n; ++q) s += X[(F * n + t) * n + q] * Y[(F * n + q) * M + col];
-            A[(F * n + t) * M + col] = (F * n + t == col ? 1.0 : 0.0) - s;
-          }
-      DenseLU lu = lu_factor(A.data(), M);
-      if (!lu.ok) { *err = "singular block-Jacobi block"; return SMPM_EINVAL; }
-      std::vector<double> Gi(static_cast<size_t>(M) * M), col(M);
-      for (int j = 0; j < M; ++j) {
-        std::fill(col.begin(), col.end(), 0.0);
-        col[j] = 1.0;
-        lu_solve(lu, col.data());
-        for (int i = 0; i < M; ++i) Gi[i * M + j] = col[i];
-      }
-      gcache[key] = Gi;
-    }
-    const std::vector<double>& Gi = gcache.at(key);
-    std::memcpy(f->G.data() + ib * M * M, Gi.data(), sizeof(double) * M * M);
+  {
+    int st = block_factors(g, f->black, f->T, &f->G, &f->X, err);
+    if (st != SMPM_OK) return st;
   }
 
   // B 1 and the coarse matrix C = Z^T S Z
@@ -686,6 +725,7 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
     }
   }
   // bordered K = [[C, c0], [c0^T, 0]]: u_C from K^T [y; eta] = [0; 1], H from K^-1
+  std::vector<double> Kinv;  // leading d x d block of K^-1 (kept for the adjoint)
   {
     const int d1 = d + 1;
     std::vector<double> K1(static_cast<size_t>(d1) * d1, 0.0);
@@ -708,7 +748,7 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
     nrm = std::sqrt(nrm) * (y[imax] >= 0 ? 1.0 : -1.0);
     f->uC.resize(d);
     for (int i = 0; i < d; ++i) f->uC[i] = y[i] / nrm;
-    std::vector<double> Kinv(static_cast<size_t>(d) * d);
+    Kinv.assign(static_cast<size_t>(d) * d, 0.0);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int j = 0; j < d; ++j) {
       std::vector<double> col(d1, 0.0);
@@ -778,6 +818,63 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
         tot += w;
       }
   for (auto& v : f->what) v /= tot;
+
+  if (o.flags & SMPM_FLAG_ADJOINT) {
+    // transposed system: T~_e = T_e^T in the same push form (the slot swap
+    // Phi maps S^T to I + push(T^T)); blocks, row sums and fast
+    // diagonalisation follow from it, the coarse matrix is C^T
+    f->Ta.resize(f->T.size());
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < g.nel; ++e) {
+      const double* Te = f->T.data() + static_cast<size_t>(e) * M * M;
+      double* Ae = f->Ta.data() + static_cast<size_t>(e) * M * M;
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) Ae[i * M + j] = Te[j * M + i];
+    }
+    row_sums(g, f->Ta, &f->Rsa);
+    int sta = block_factors(g, f->black, f->Ta, &f->Ga, &f->Xa, err);
+    if (sta != SMPM_OK) return sta;
+    transpose_fd(n, f->fdx, &f->fdxT);
+    transpose_fd(n, f->fdy, &f->fdyT);
+    // C^T is singular with left null vector c0 and right null vector u_C;
+    // (K^T)^-1 = (K^-1)^T solves the bordered [[C^T, c0], [c0^T, 0]], so
+    //   Ha = (I - u_C u_C^T) Kinv^T (I - c0^ c0^T)
+    // maps r to the y with C^T y = r - c0^ (c0^T r) and u_C^T y = 0
+    // (the reading with the null vectors' roles swapped)
+    std::vector<double> ch(d), v(d, 0.0), w(d, 0.0);
+    double cn = 0;
+    for (int i = 0; i < d; ++i) cn += f->c0[i] * f->c0[i];
+    cn = std::sqrt(cn);
+    for (int i = 0; i < d; ++i) ch[i] = f->c0[i] / cn;
+    // v_i = sum_k Kinv[k][i] ch_k ; w_j = sum_k u_k Kinv[j][k] - (u . v) ch_j
+    for (int k = 0; k < d; ++k) {
+      const double* row = Kinv.data() + static_cast<size_t>(k) * d;
+      for (int i = 0; i < d; ++i) v[i] += row[i] * ch[k];
+    }
+    double uv = 0;
+    for (int k = 0; k < d; ++k) uv += f->uC[k] * v[k];
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < d; ++j) {
+      const double* row = Kinv.data() + static_cast<size_t>(j) * d;
+      double acc = 0;
+      for (int k = 0; k < d; ++k) acc += f->uC[k] * row[k];
+      w[j] = acc - uv * ch[j];
+    }
+    f->Ha.assign(static_cast<size_t>(d) * d, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        f->Ha[static_cast<size_t>(i) * d + j] =
+            Kinv[static_cast<size_t>(j) * d + i] - v[i] * ch[j] - f->uC[i] * w[j];
+    // left null vector of the permuted S^T: Phi B1 = B1 (B1 is constant on
+    // each interface), normalised
+    double bn = 0;
+    for (double b : f->B1) bn += b * b;
+    bn = std::sqrt(bn);
+    f->uSa.resize(g.kp);
+    for (long long i = 0; i < g.kp; ++i) f->uSa[i] = f->B1[i] / bn;
+    f->has_adjoint = true;
+  }
   return SMPM_OK;
 }
 

@@ -79,6 +79,17 @@ struct Factors {
   std::vector<double> B1;    // kp : B 1 (right null vector of S)
   int null_iterations = 0;   // GMRES steps of the u_S bordered solve
   double null_relres = 0;
+  // Transposed system for the adjoint solve (built with SMPM_FLAG_ADJOINT).
+  // With Phi the involution that swaps the two slots facing each other across
+  // an interface, Phi S^T Phi is again "I + push form" with T~_e = T_e^T, the
+  // same checkerboard blocks and the same Z, coarse matrix C^T, left null
+  // vector Phi B1 = B1 and coarse null vectors swapped (left c0, right u_C).
+  bool has_adjoint = false;
+  std::vector<double> Ta;          // nel * M*M : T_e^T, row-major
+  std::vector<double> Rsa, Ga, Xa; // as Rs, G, X for T~
+  std::vector<double> Ha;          // d*d : (I - u_C u_C^T) K^-T (I - c0^ c0^T)
+  std::vector<double> uSa;         // kp : B1 / |B1|
+  std::vector<double> fdxT, fdyT;  // fast diagonalisation of K^T: (Vinv^T, V^T, lam)
 };
 
 // Host factor step (smpm_factor_host.cpp).

@@ -22,6 +22,18 @@
 //       T_e x_S also give the true residual ||b_S - S x_S||^2; GLL-weighted
 //       mean of u accumulated
 //   Q6  u <- u - mean
+//
+// With `adjoint` set the same kernels run the transposed solve (reverse-mode
+// derivative of u(f, g)), on the factors of the slot-swapped S^T (T~ = T^T,
+// see the factor step) and with the transposed element operators:
+//   P1  y = gbar (= dl/du); 1^T y accumulated
+//   P2  y <- y - w^ (1^T y)  (N^T, N the zero-mean map); w = A_e^-T y_e; the
+//       face values of w (E^T A^-T y) are pushed into the facing slots
+//   P3, P4, Q1-Q4 unchanged (the transposed factors are passed in)
+//   Q5  lam_e = A_e^-T (y_e - B_e^T mu_e) with mu_e the element's own slots of
+//       the solution; u_L^T lam accumulated
+//   Q6  dl/db = lam - u_L (u_L^T lam) written to u; dl/dg on boundary-face
+//       slots = tau_F dl/db at the face node (gg, if given)
 #pragma once
 // Included inside the anonymous namespace of smpm_solver.cu.
 
@@ -51,6 +63,8 @@ struct PrePostArgs {
   double* cr;        // d, zeroed in P1 (mixed precision), or null
   float* rg32;       // kp, FP32 copy of the GMRES right-hand side (mixed precision), or null
   int assembled;     // k_post: x_S is given in xs (skip the assembly)
+  int adjoint;       // transposed solve (see above)
+  double* gg;        // adjoint: kp, dl/dg per padded slot, or null
 };
 
 // accumulator slots
@@ -101,7 +115,7 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
         if (bb == n - 1 && dev_neighbour(g, (int)e, 3) < 0) v += g.tau_y * P.gn[s0 + 3 * n + aa];
       }
       P.b[gq] = v;
-      part += P.uL[gq] * v;
+      part += P.adjoint ? v : P.uL[gq] * v;
     }
   }
   part = warp_sum(part);
@@ -113,7 +127,7 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
   for (long long e = blockIdx.x; e < g.nel; e += G) {
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
       const long long gq = e * nn + q;
-      double v = P.b[gq] - alpha * P.uL[gq];
+      double v = P.b[gq] - alpha * (P.adjoint ? P.what[gq] : P.uL[gq]);
       P.b[gq] = v;
       B[q] = v;
     }
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
         int aa, bb;
         face_node(n, F, t, &aa, &bb);
         const double tau = F < 2 ? g.tau_x : g.tau_y, pw = F < 2 ? g.p_x : g.p_y;
-        val = -tau * (pw * U[bb * n + aa] - normal_deriv(g, P.D, U, F, t));
+        val = P.adjoint ? U[bb * n + aa] : -tau * (pw * U[bb * n + aa] - normal_deriv(g, P.D, U, F, t));
         const size_t sl = (size_t)e2 * M + (F ^ 1) * n + t;
         P.bS[sl] = val;
         pus += P.uS[sl] * val;
@@ -169,6 +183,7 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
     if (dev_neighbour(g, e, F) < 0) {
       P.bS[sl] = 0.0;
       P.rg[sl] = 0.0;
+      if (P.rg32) P.rg32[sl] = 0.f;
       continue;
     }
     double v = __ldcg(P.bS + sl) - beta * P.uS[sl];
@@ -254,18 +269,37 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = __ldcg(P.xs + e * M + i);
     __syncthreads();
     for (int F = 0; F < 4; ++F) {  // faces in turn: a corner node takes both slots
-      if (dev_neighbour(g, (int)e, F) >= 0)
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-          int aa, bb;
-          face_node(n, F, t, &aa, &bb);
-          B[bb * n + aa] -= s.p[F * n + t];
+      if (dev_neighbour(g, (int)e, F) >= 0) {
+        if (!P.adjoint) {
+          for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            int aa, bb;
+            face_node(n, F, t, &aa, &bb);
+            B[bb * n + aa] -= s.p[F * n + t];
+          }
+        } else {
+          // - B_e^T mu: the slot (F, t) feeds, through B, the flux
+          // -tau_F (p_F u(q) - n_F.grad u(q)) at face node q = (F, t); its
+          // transpose touches the n nodes on the normal line through q
+          const double tau = F < 2 ? g.tau_x : g.tau_y, pw = F < 2 ? g.p_x : g.p_y;
+          const double sc = F < 2 ? g.sx : g.sy;
+          const int drow = (F & 1) ? n - 1 : 0;   // D row of the face end
+          const double sgn = (F & 1) ? 1.0 : -1.0;  // outward normal along the axis
+          for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+            const int t = idx / n, k = idx % n;
+            const double v = s.p[F * n + t];
+            const double dn = sgn * sc * __ldg(P.D + drow * n + k);
+            const double coef = -tau * ((k == drow ? pw : 0.0) - dn);
+            const int q = F < 2 ? t * n + k : k * n + t;
+            B[q] -= coef * v;
+          }
         }
+      }
       __syncthreads();
     }
     elem_fd(P, (int)e, B, U, t1);
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
       P.u[e * nn + q] = U[q];
-      pm += P.what[e * nn + q] * U[q];
+      pm += (P.adjoint ? P.uL[e * nn + q] : P.what[e * nn + q]) * U[q];
     }
     // (S x_S) on the slots facing e: x_S + T_e x_S,e
     gemv_split(a.Tc + (size_t)e * M * M, M, s.p, s.z, M, M, s.red);
@@ -285,10 +319,29 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
     if (pr != 0.0) atomicAdd(P.acc + ACC_RES, pr);
   }
   if (!grid_sync(a.bar, a.err, epoch)) return;
-  // ---- Q6: zero GLL-weighted mean
+  // ---- Q6: zero GLL-weighted mean (adjoint: projection out of u_L, dl/dg)
   const double mean = __ldcg(P.acc + ACC_MEAN);
-  for (long long e = blockIdx.x; e < g.nel; e += G)
-    for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean;
+  if (!P.adjoint) {
+    for (long long e = blockIdx.x; e < g.nel; e += G)
+      for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean;
+    return;
+  }
+  for (long long e = blockIdx.x; e < g.nel; e += G) {
+    if (P.gg)
+      for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const int F = i / n, t = i % n;
+        double v = 0;
+        if (dev_neighbour(g, (int)e, F) < 0) {
+          int aa, bb;
+          face_node(n, F, t, &aa, &bb);
+          const long long q = e * nn + bb * n + aa;
+          v = (F < 2 ? g.tau_x : g.tau_y) * (__ldcg(P.u + q) - mean * P.uL[q]);
+        }
+        P.gg[e * M + i] = v;
+      }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean * P.uL[e * nn + q];
+  }
 }
 
 inline size_t prepost_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d) {

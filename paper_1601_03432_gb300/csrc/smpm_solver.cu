@@ -427,6 +427,92 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
 #include "smpm_prepost.cuh"
 #include "smpm_refine.cuh"
 
+// y = S v streamed from HBM: a persistent CTA per SM walks its elements
+// e = c, c+G, ... and keeps STAGES of them in flight with bulk copies of the
+// (contiguous, column-major) T_e into shared-memory buffers, so the factor
+// streams at HBM rate while the GEMV of an earlier element runs.  Outputs as
+// k_schur (push form).  A copy that never completes (bounded wait) leaves NaN
+// in that element's outputs.
+template <typename S>
+__global__ void __launch_bounds__(256, 2) k_schur_stream(DevGeo g, const S* __restrict__ Tc, const S* v, S* y,
+                                                         int stages) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int M = g.M, n = g.n, G = gridDim.x;
+  const unsigned mbytes = (unsigned)(M * M * sizeof(S));
+  S* buf = reinterpret_cast<S*>(raw);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(buf + (size_t)stages * M * M);
+  S* ve = reinterpret_cast<S*>(mbar + stages);
+  S* z = ve + M;
+  S* red = z + M;
+  const long long nk = (g.nel - blockIdx.x + G - 1) / G;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < stages; ++b) mbar_init(mbar + b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](long long k) {
+    if (threadIdx.x != 0 || k >= nk) return;
+    const int b = (int)(k % stages);
+    const long long e = blockIdx.x + k * G;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar + b)), "r"(mbytes)
+                 : "memory");
+    bulk_g2s(buf + (size_t)b * M * M, Tc + (size_t)e * M * M, mbytes, mbar + b);
+  };
+  for (int k = 0; k < stages; ++k) issue(k);
+  __shared__ int ok;
+  bool failed = false;
+  long long waited = 0;  // copies completed or given up
+  // register prefetch of the next element's vector entries (thread i < M):
+  // own slot i and the neighbour slot its output row feeds
+  auto nb_slot = [&](long long e, int i) -> long long {
+    const int F = i / n, t = i % n, e2 = dev_neighbour(g, (int)e, F);
+    return e2 >= 0 ? (long long)e2 * M + (F ^ 1) * n + t : -1;
+  };
+  S pv_own = 0, pv_nb = 0;
+  if (nk > 0 && threadIdx.x < M) {
+    pv_own = v[(long long)blockIdx.x * M + threadIdx.x];
+    const long long sl = nb_slot(blockIdx.x, threadIdx.x);
+    pv_nb = sl >= 0 ? v[sl] : S(0);
+  }
+  for (long long k = 0; k < nk; ++k) {
+    const long long e = blockIdx.x + k * G;
+    const int b = (int)(k % stages);
+    S cur_nb = pv_nb;
+    if (threadIdx.x < M) ve[threadIdx.x] = pv_own;
+    if (k + 1 < nk && threadIdx.x < M) {
+      const long long e1 = e + G;
+      pv_own = v[e1 * M + threadIdx.x];
+      const long long sl = nb_slot(e1, threadIdx.x);
+      pv_nb = sl >= 0 ? v[sl] : S(0);
+    }
+    if (threadIdx.x == 0) ok = (!failed && mbar_wait(mbar + b, (unsigned)((k / stages) & 1))) ? 1 : 0;
+    __syncthreads();
+    if (ok) {
+      waited = k + 1;
+      gemv_split(buf + (size_t)b * M * M, M, ve, z, M, M, red);
+      issue(k + stages);  // buffer b is free again (gemv_split ends with a barrier)
+    } else {
+      failed = true;  // stop issuing; the outputs of this CTA become NaN
+    }
+    if (threadIdx.x < M) {
+      const int i = threadIdx.x;
+      const long long sl = nb_slot(e, i);
+      if (sl >= 0) y[sl] = ok ? cur_nb + z[i] : (S)nan("");
+      else y[e * M + i] = ve[i];
+    }
+    __syncthreads();
+  }
+  if (failed && threadIdx.x == 0) {  // bounded wait for the copies still in flight
+    const long long issued = (waited + stages < nk) ? waited + stages : nk;
+    for (long long k = waited; k < issued; ++k) mbar_wait(mbar + (k % stages), (unsigned)((k / stages) & 1));
+  }
+}
+
+inline size_t schur_stream_smem(int M, int stages, size_t elem) {
+  return (size_t)stages * M * M * elem + stages * 8 + (2 * (size_t)M + 256) * elem + 64;
+}
+
 // ------------------------------------------------------------- host side
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -469,6 +555,9 @@ struct smpm_handle_s {
     size_t smem = 0, smem_ref = 0;
   } gm32;
   double *wacc8 = nullptr, *wxs = nullptr, *dZtuS = nullptr;
+  // transposed system for the adjoint solve (SMPM_FLAG_ADJOINT)
+  double *dTa = nullptr, *dRsa = nullptr, *dGa = nullptr, *dXa = nullptr, *dHa = nullptr;
+  double *dfdxT = nullptr, *dfdyT = nullptr, *duSa = nullptr, *dZtuSa = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the GMRES kernel of each solve
   cudaEvent_t evp = nullptr, evq = nullptr;  // start of k_pre, end of k_post
   unsigned char* wctl = nullptr;              // [bar x4 | err | pad | acc8] zeroed per solve
@@ -542,11 +631,39 @@ std::vector<double> transpose_blocks(const std::vector<double>& src, int b, size
 size_t elem_smem(int n) { return 3 * (size_t)n * n * sizeof(double); }
 
 // ---- operator launches (FP64) ----------------------------------------
-smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
+template <typename S>
+smpm_status launch_schur_stream(smpm_handle h, const S* T, const S* v, S* y, cudaStream_t st) {
   const DevGeo& g = h->dg;
-  k_schur<double><<<(unsigned)g.nel, kElemThreads, 2 * g.M * sizeof(double), st>>>(g, h->dT, v, y);
+  int dev = 0, sms = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // two CTAs per SM when at least two stages fit in half the SM's shared
+  // memory, else one CTA with as many stages as fit (at most 8)
+  int per_sm_smem = 0;
+  CU(cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  int cps = 2, stages = 8;
+  while (stages > 1 && 2 * (schur_stream_smem(g.M, stages, sizeof(S)) + 1024) > (size_t)per_sm_smem) --stages;
+  if (stages < 2) {
+    cps = 1;
+    stages = 8;
+    while (stages > 1 && schur_stream_smem(g.M, stages, sizeof(S)) > (size_t)optin) --stages;
+  }
+  const size_t smem = schur_stream_smem(g.M, stages, sizeof(S));
+  if (smem > (size_t)optin) {  // one matrix does not fit: per-element kernel from global memory
+    k_schur<S><<<(unsigned)g.nel, kElemThreads, 2 * g.M * sizeof(S), st>>>(g, T, v, y);
+    CHECK_LAUNCH();
+    return SMPM_OK;
+  }
+  CU(cudaFuncSetAttribute(k_schur_stream<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)std::min<long long>((long long)sms * cps, g.nel);
+  k_schur_stream<S><<<grid, kElemThreads, smem, st>>>(g, T, v, y, stages);
   CHECK_LAUNCH();
   return SMPM_OK;
+}
+
+smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
+  return launch_schur_stream<double>(h, h->dT, v, y, st);
 }
 
 // t = M^-1 v (t fully written), then optionally y = S t and c = Z^T y.
@@ -643,8 +760,9 @@ Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, i
   return L;
 }
 
-// Kernel arguments shared by the three cooperative kernels of a solve.
-GmresArgs<double> gmres_args(smpm_handle h, double tol) {
+// Kernel arguments shared by the three cooperative kernels of a solve
+// (adj: the operator of the slot-swapped transposed system).
+GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   GmresArgs<double> a{};
   a.g = h->dg;
   a.black = h->dblack;
@@ -652,6 +770,7 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol) {
   a.nblack = (int)h->f.black.size();
   a.nwhite = (int)h->f.white.size();
   a.Tc = h->dT; a.Gc = h->dG; a.Xc = h->dX; a.Rs = h->dRs; a.H = h->dH;
+  if (adj) { a.Tc = h->dTa; a.Gc = h->dGa; a.Xc = h->dXa; a.Rs = h->dRsa; a.H = h->dHa; }
   a.vglob = h->wV; a.vown = h->wvown; a.t = h->wt; a.y = h->wy;
   a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg; a.x = h->wx;
   a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
@@ -816,9 +935,11 @@ smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, do
 
 // One right-hand side, FP64, Algorithms 1-3: three cooperative launches
 // (k_pre, k_gmres, k_post) and one host synchronisation for the report.
+// adj: the transposed solve on the adjoint factors (f = dl/du, u = dl/db,
+// gg = dl/dg or null), always FP64.
 smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* u, double tol, smpm_report* rep,
-                      cudaStream_t st) {
-  if (h->opts.precision == 1) return solve_one_mixed(h, f, gn, u, tol, rep, st);
+                      cudaStream_t st, bool adj = false, double* gg = nullptr) {
+  if (h->opts.precision == 1 && !adj) return solve_one_mixed(h, f, gn, u, tol, rep, st);
   const int m = h->opts.restart;
   smpm_report R{};
   const long long launches0 = h->launches;
@@ -826,13 +947,19 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   // pre/post accumulators (contiguous); everything else is zeroed in k_pre
   CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
   PrePostArgs P{};
-  P.ga = gmres_args(h, tol);
+  P.ga = gmres_args(h, tol, adj);
   P.ga.mats_smem = 0;
   P.ga.basis_smem = 0;
   P.ga.stream_mats = 0;
   P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
   P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
   P.chatb = h->wchatb; P.xs = h->wxs; P.u = u; P.acc = h->wacc8;
+  if (adj) {
+    P.adjoint = 1;
+    P.gg = gg;
+    P.gn = nullptr;
+    P.fdx = h->dfdxT; P.fdy = h->dfdyT; P.uS = h->duSa; P.ZtuS = h->dZtuSa;
+  }
   P.ga.trace = nullptr;
   P.ga.bar = h->wbar + 0;
   double* zs[7] = {h->wx, h->wt, h->wy, h->wV, h->wbS, h->wrg, h->wxs};
@@ -848,7 +975,7 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   }
   CU(cudaEventRecord(h->ev0, st));
   {
-    GmresArgs<double> a = gmres_args(h, tol);
+    GmresArgs<double> a = gmres_args(h, tol, adj);
     a.bar = h->wbar + 1;
     void* args[] = {&a};
     CU(cudaLaunchCooperativeKernel((const void*)k_gmres<double>, dim3(h->gm.grid), dim3(kGmresThreads), args,
@@ -1117,6 +1244,24 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
         for (int t = 0; t < g.n; ++t) ztus[j] += h->f.uS[e * g.M + F * g.n + t];
       }
     if ((s = upload(h, &h->dZtuS, ztus, st))) return s;
+    if (h->f.has_adjoint) {
+      // T~_e = T_e^T: its column-major device copy is T_e row-major
+      std::vector<double> Gca = transpose_blocks(h->f.Ga, g.M, h->f.black.size()),
+                          Xca = transpose_blocks(h->f.Xa, g.n, 4 * h->f.black.size());
+      std::vector<double> ztusa(g.d, 0.0);
+      for (long long e = 0; e < g.nel; ++e)
+        for (int F = 0; F < 4; ++F) {
+          int j = h->g.iface((int)e, F);
+          if (j < 0) continue;
+          for (int t = 0; t < g.n; ++t) ztusa[j] += h->f.uSa[e * g.M + F * g.n + t];
+        }
+      if ((s = upload(h, &h->dTa, h->f.T, st)) || (s = upload(h, &h->dRsa, h->f.Rsa, st)) ||
+          (s = upload(h, &h->dGa, Gca, st)) || (s = upload(h, &h->dXa, Xca, st)) ||
+          (s = upload(h, &h->dHa, h->f.Ha, st)) || (s = upload(h, &h->dfdxT, h->f.fdxT, st)) ||
+          (s = upload(h, &h->dfdyT, h->f.fdyT, st)) || (s = upload(h, &h->duSa, h->f.uSa, st)) ||
+          (s = upload(h, &h->dZtuSa, ztusa, st)))
+        return s;
+    }
     if ((s = dalloc(h, &h->wctl, kCtlBytes)) || (s = dalloc(h, &h->wxs, g.kp))) return s;
     h->wbar = reinterpret_cast<unsigned*>(h->wctl);
     h->werr = reinterpret_cast<int*>(h->wctl + 256);
@@ -1142,6 +1287,23 @@ smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double
   for (int k = 0; k < nrhs; ++k) {
     smpm_status s = solve_one(h, f + (size_t)k * h->g.r, gn ? gn + (size_t)k * h->g.kp : nullptr,
                               u + (size_t)k * h->g.r, t, rep ? rep + k : nullptr, st);
+    if (s == SMPM_ENOTCONV) worst = s;
+    else if (s != SMPM_OK) return s;
+  }
+  return worst;
+}
+
+smpm_status schur_solve_adjoint(smpm_handle h, const double* gbar_u, double tol, int nrhs, double* gbar_f,
+                                double* gbar_g, smpm_report* rep, void* stream) {
+  if (!h || !gbar_u || !gbar_f || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
+  if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
+  if (!h->f.has_adjoint) return fail(SMPM_ESTATE, "schur_factor was called without SMPM_FLAG_ADJOINT");
+  double t = tol > 0 ? tol : h->opts.tol;
+  cudaStream_t st = as_stream(stream);
+  smpm_status worst = SMPM_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    smpm_status s = solve_one(h, gbar_u + (size_t)k * h->g.r, nullptr, gbar_f + (size_t)k * h->g.r, t,
+                              rep ? rep + k : nullptr, st, true, gbar_g ? gbar_g + (size_t)k * h->g.kp : nullptr);
     if (s == SMPM_ENOTCONV) worst = s;
     else if (s != SMPM_OK) return s;
   }
@@ -1184,10 +1346,7 @@ smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* st
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
-  const DevGeo& g = h->dg;
-  k_schur<float><<<(unsigned)g.nel, kElemThreads, 2 * g.M * sizeof(float), as_stream(stream)>>>(g, h->dT32, v, y);
-  CHECK_LAUNCH();
-  return SMPM_OK;
+  return launch_schur_stream<float>(h, h->dT32, v, y, as_stream(stream));
 }
 
 smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream) {
@@ -1296,6 +1455,15 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
   else if (nm == "B1") src = &f.B1;
   else if (nm == "uL") src = &f.uL;
   else if (nm == "what") src = &f.what;
+  else if (nm == "Ta") src = &f.Ta;
+  else if (nm == "Ga") src = &f.Ga;
+  else if (nm == "Xa") src = &f.Xa;
+  else if (nm == "Ha") src = &f.Ha;
+  else if (nm == "Rsa") src = &f.Rsa;
+  else if (nm == "Rs") src = &f.Rs;
+  else if (nm == "uSa") src = &f.uSa;
+  else if (nm == "fdx") src = &f.fdx;
+  else if (nm == "fdxT") src = &f.fdxT;
   else if (nm == "black") { tmp.assign(f.black.begin(), f.black.end()); src = &tmp; }
   else if (nm == "null_iterations") { tmp.assign(1, (double)f.null_iterations); src = &tmp; }
   else return fail(SMPM_EINVAL, "unknown factor name " + nm);

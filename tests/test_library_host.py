@@ -159,3 +159,104 @@ def test_null_vectors(pair):
     uL *= np.sign(uL @ osys.u_L)
     assert np.linalg.norm(uL - osys.u_L) < 1e-12
     np.testing.assert_allclose(lg.host_factor("what").sum(), 1.0, rtol=1e-14)
+
+
+# ---------------------------------------------------- transposed system
+@pytest.fixture(scope="module", params=GRIDS[1:3], ids=lambda p: "x".join(map(str, p[:3])))
+def apair(request):
+    mx, my, n, Lx, Ly = request.param
+    og = SMPMGrid(mx, my, n, Lx, Ly)
+    osys = SchurSystem(og)
+    lg = B.Grid(mx, my, n, Lx, Ly)
+    lg.factor_host_only(flags=B.FLAG_ADJOINT)
+    return og, osys, lg
+
+
+def _phi(og):
+    """The slot swap Phi on compact slots: (e, F, t) <-> (nbr(e, F), opp F, t)."""
+    p = np.empty(og.k, dtype=np.int64)
+    for i, (e, F, t) in enumerate(og.slots):
+        p[i] = og.slot_of[(og.neighbour(e, F), OPPOSITE[F], t)]
+    return p
+
+
+def test_adjoint_T_is_transpose(apair):
+    og, osys, lg = apair
+    M = 4 * og.n
+    T = lg.host_factor("T").reshape(og.nel, M, M)
+    Ta = lg.host_factor("Ta").reshape(og.nel, M, M)
+    assert np.array_equal(Ta, T.transpose(0, 2, 1))
+    # I + push(T~) is Phi S^T Phi
+    phi = _phi(og)
+    v = np.random.default_rng(8).standard_normal(og.k)
+    vp = og.to_padded(v)
+    yp = vp.copy()
+    n = og.n
+    for e in range(og.nel):
+        z = Ta[e] @ vp[e * M:(e + 1) * M]
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            if e2 >= 0:
+                yp[e2 * M + OPPOSITE[F] * n: e2 * M + OPPOSITE[F] * n + n] += z[F * n:(F + 1) * n]
+    ref = (osys.S.T @ v[phi])[phi]
+    np.testing.assert_allclose(og.from_padded(yp), ref, atol=1e-11 * np.abs(ref).max())
+
+
+def test_adjoint_block_jacobi_is_transposed(apair):
+    """The reduced form with (T~, G~, X~) applies Phi M^-T Phi."""
+    og, osys, lg = apair
+    n, M = og.n, 4 * og.n
+    T = lg.host_factor("Ta").reshape(og.nel, M, M)
+    G = lg.host_factor("Ga").reshape(-1, M, M)
+    X = lg.host_factor("Xa").reshape(-1, 4, n, n)
+    black = lg.host_factor("black").astype(int)
+    phi = _phi(og)
+    v = np.random.default_rng(4).standard_normal(og.k)
+    ref = osys.apply_MinvT(v[phi])[phi]
+    vp = og.to_padded(v)
+    out = np.zeros(og.kp)
+    for ib, e in enumerate(black):
+        p = vp[e * M:(e + 1) * M].copy()
+        q = np.zeros(M)
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            if e2 >= 0:
+                q[F * n:(F + 1) * n] = vp[e2 * M + OPPOSITE[F] * n: e2 * M + OPPOSITE[F] * n + n]
+        Xq = np.concatenate([X[ib, F] @ q[F * n:(F + 1) * n] for F in range(4)])
+        a = G[ib] @ (p - Xq)
+        b = q - T[e] @ a
+        out[e * M:(e + 1) * M] = a
+        for F in range(4):
+            e2 = og.neighbour(e, F)
+            if e2 >= 0:
+                out[e2 * M + OPPOSITE[F] * n: e2 * M + OPPOSITE[F] * n + n] = b[F * n:(F + 1) * n]
+    np.testing.assert_allclose(og.from_padded(out), ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_adjoint_coarse_and_null_vectors(apair):
+    from oracle.adjoint import AdjointDeflation
+    og, osys, lg = apair
+    d = og.d
+    Ha = lg.host_factor("Ha").reshape(d, d)
+    r = np.random.default_rng(6).standard_normal(d)
+    ref = AdjointDeflation(osys).coarse_solve(r)
+    np.testing.assert_allclose(Ha @ r, ref, atol=1e-9 * np.abs(ref).max())
+    uSa = og.from_padded(lg.host_factor("uSa"))
+    ref = osys.B1 / np.linalg.norm(osys.B1)
+    assert np.linalg.norm(uSa * np.sign(uSa @ ref) - ref) < 1e-14
+    assert np.linalg.norm(osys.S @ uSa) < 1e-12 * abs(osys.S).max()
+
+
+def test_transposed_fast_diagonalisation(apair):
+    og, osys, lg = apair
+    n = og.n
+    fd, fdT = lg.host_factor("fdx"), lg.host_factor("fdxT")
+    fds = 2 * n * n + n
+    for cls in range(4):
+        V, Vi, lam = (fd[cls * fds:cls * fds + n * n].reshape(n, n),
+                      fd[cls * fds + n * n:cls * fds + 2 * n * n].reshape(n, n), fd[cls * fds + 2 * n * n:(cls + 1) * fds])
+        W, Wi, lamT = (fdT[cls * fds:cls * fds + n * n].reshape(n, n),
+                       fdT[cls * fds + n * n:cls * fds + 2 * n * n].reshape(n, n),
+                       fdT[cls * fds + 2 * n * n:(cls + 1) * fds])
+        K = V @ np.diag(lam) @ Vi
+        np.testing.assert_allclose(W @ np.diag(lamT) @ Wi, K.T, atol=1e-10 * np.abs(K).max())
