@@ -139,6 +139,40 @@ void lu_solve(const DenseLU& f, double* b) {
   }
 }
 
+// Solve A X = B for nrhs right-hand sides at once: B row-major n x nrhs.
+// Row operations on whole rows of B (contiguous, vectorisable) stream the
+// factors once per call instead of once per right-hand side.
+void lu_solve_multi(const DenseLU& f, double* B, int nrhs) {
+  const int n = f.n;
+  const double* a = f.a.data();
+  for (int k = 0; k < n; ++k)
+    if (f.piv[k] != k)
+      for (int c = 0; c < nrhs; ++c)
+        std::swap(B[static_cast<size_t>(k) * nrhs + c], B[static_cast<size_t>(f.piv[k]) * nrhs + c]);
+  for (int i = 0; i < n; ++i) {
+    double* bi = B + static_cast<size_t>(i) * nrhs;
+    const double* ri = a + static_cast<size_t>(i) * n;
+    for (int j = 0; j < i; ++j) {
+      const double l = ri[j];
+      if (l == 0.0) continue;
+      const double* bj = B + static_cast<size_t>(j) * nrhs;
+      for (int c = 0; c < nrhs; ++c) bi[c] -= l * bj[c];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double* bi = B + static_cast<size_t>(i) * nrhs;
+    const double* ri = a + static_cast<size_t>(i) * n;
+    for (int j = i + 1; j < n; ++j) {
+      const double u = ri[j];
+      if (u == 0.0) continue;
+      const double* bj = B + static_cast<size_t>(j) * nrhs;
+      for (int c = 0; c < nrhs; ++c) bi[c] -= u * bj[c];
+    }
+    const double inv = 1.0 / ri[i];
+    for (int c = 0; c < nrhs; ++c) bi[c] *= inv;
+  }
+}
+
 // Solve A^T x = b with the factors of A.
 void lu_solve_T(const DenseLU& f, double* b) {
   const int n = f.n;
@@ -437,15 +471,26 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
     int j = 0;
     for (; j < m && total < maxit; ++j) {
       op(V[j], w);
-      for (int i = 0; i <= j; ++i) {
-        double h = dot(V[i], w);
-        H[i * m + j] = h;
-        for (size_t q = 0; q < N; ++q) w[q] -= h * V[i][q];
-      }
-      for (int i = 0; i <= j; ++i) {  // second Gram-Schmidt sweep
-        double h = dot(V[i], w);
-        H[i * m + j] += h;
-        for (size_t q = 0; q < N; ++q) w[q] -= h * V[i][q];
+      // classical Gram-Schmidt, twice: h = V^T w in one pass over the
+      // basis, then w -= V h in one pass (both split over entries)
+      for (int sweep = 0; sweep < 2; ++sweep) {
+        std::vector<double> h(j + 1, 0.0);
+#pragma omp parallel
+        {
+          std::vector<double> hp(j + 1, 0.0);
+#pragma omp for schedule(static) nowait
+          for (long long q = 0; q < (long long)N; ++q)
+            for (int i = 0; i <= j; ++i) hp[i] += V[i][q] * w[q];
+#pragma omp critical
+          for (int i = 0; i <= j; ++i) h[i] += hp[i];
+        }
+#pragma omp parallel for schedule(static)
+        for (long long q = 0; q < (long long)N; ++q) {
+          double acc = w[q];
+          for (int i = 0; i <= j; ++i) acc -= h[i] * V[i][q];
+          w[q] = acc;
+        }
+        for (int i = 0; i <= j; ++i) H[i * m + j] = (sweep ? H[i * m + j] : 0.0) + h[i];
       }
       double hn = std::sqrt(dot(w, w));
       H[(j + 1) * m + j] = hn;
@@ -749,12 +794,16 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
     f->uC.resize(d);
     for (int i = 0; i < d; ++i) f->uC[i] = y[i] / nrm;
     Kinv.assign(static_cast<size_t>(d) * d, 0.0);
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int j = 0; j < d; ++j) {
-      std::vector<double> col(d1, 0.0);
-      col[j] = 1.0;
-      lu_solve(lu, col.data());
-      for (int i = 0; i < d; ++i) Kinv[static_cast<size_t>(i) * d + j] = col[i];
+    constexpr int kCols = 64;  // right-hand sides per block solve
+    const int nblk = (d + kCols - 1) / kCols;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int bk = 0; bk < nblk; ++bk) {
+      const int j0 = bk * kCols, nc = std::min(kCols, d - j0);
+      std::vector<double> Bm(static_cast<size_t>(d1) * nc, 0.0);
+      for (int c = 0; c < nc; ++c) Bm[static_cast<size_t>(j0 + c) * nc + c] = 1.0;
+      lu_solve_multi(lu, Bm.data(), nc);
+      for (int i = 0; i < d; ++i)
+        for (int c = 0; c < nc; ++c) Kinv[static_cast<size_t>(i) * d + j0 + c] = Bm[static_cast<size_t>(i) * nc + c];
     }
     f->H.assign(static_cast<size_t>(d) * d, 0.0);
 #pragma omp parallel for schedule(static)
