@@ -34,6 +34,7 @@ extern "C" {
 #endif
 
 typedef struct smpm_handle_s* smpm_handle;
+typedef struct smpm_batch_s* smpm_batch;   /* opaque; a set of factored handles solved together */
 
 typedef enum {
   SMPM_OK = 0,
@@ -117,6 +118,13 @@ smpm_status smpm_node_mass(smpm_handle h, double* w);
  * precond > 0 on a grid with a single interface, whose only block-Jacobi
  * block is the whole singular S), ENOINTERFACE, ENOMEM, ECUDA. */
 smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream);
+
+/* schur_factor with the same options for count distinct handles: the host
+ * factor steps run in parallel (one handle per host thread, largest grids
+ * first), then each handle's device part runs in turn on stream.  Stops at
+ * the first failing handle (its status and message are returned; handles
+ * after it are left unfactored). */
+smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* o, void* stream);
 
 /* Algorithm 3 (or 1/2 per opts.precond) for nrhs right-hand sides.
  *   f : device, r * nrhs, right-hand side of Eq. poisson at the nodes
@@ -214,6 +222,56 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
  * stream; a failed internal grid barrier (not expected) leaves y = NaN.
  * Errors: EINVAL, ESTATE, ECUDA. */
 smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream);
+
+/* ---- batched solves: many right-hand sides of many independent grids ----
+ * One persistent cooperative launch runs every right-hand side of every
+ * problem of the batch (Algorithm 3 per right-hand side, each problem with
+ * the precision, preconditioner and tol of its own schur_factor).  The
+ * launch's CTAs form teams of team_size CTAs; whole problems are assigned to
+ * teams (longest estimated work first, onto the least-loaded team) and a
+ * team solves its problems' right-hand sides one after another with team
+ * barriers in place of grid barriers.  The paper solves one system at a
+ * time; batching is a property of this library.
+ *
+ * smpm_batch_create: hs[count] factored handles (distinct; their device
+ * workspaces are used by the batch, so do not solve on them concurrently),
+ * nrhs[count] >= 1 right-hand sides each.  team_size <= 0 picks the smallest
+ * of 8, 16, 19, 38, 76 that fits (each problem's solve state must fit the
+ * shared memory of one CTA at that team size), else all SMs as one team.
+ * use_graph != 0 captures the batch's device work (argument copy, barrier
+ * resets, the launch, the report copy) in a CUDA graph on the first solve
+ * and replays it afterwards.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs, int team_size, int use_graph,
+                              smpm_batch* out);
+
+/* Sizes of the packed arrays (problem-major, right-hand-side-major within a
+ * problem: problem p's k-th right-hand side starts at the sum over q < p of
+ * nrhs_q r_q, plus k r_p, for f and u, and likewise with kp for g), the
+ * number of tasks (right-hand sides), the current team size and team count,
+ * and the device time of the last batched solve (ms).  Any pointer may be
+ * null. */
+smpm_status smpm_batch_info(smpm_batch b, long long* f_len, long long* g_len, long long* ntasks, int* team_size,
+                            int* nteams, double* last_ms);
+
+/* Solve the whole batch.  f, u: device, f_len doubles (packed as above; u is
+ * written, zero-mean per right-hand side); g: device, g_len doubles, or null
+ * for g = 0.  rep: host, ntasks entries in the packed order, or null.
+ * Ordered after prior work on stream; returns after the batch has finished.
+ * Errors: EINVAL, ENOTCONV (some right-hand side did not converge; u holds
+ * its last iterate), ENAN, ETIMEOUT, ECUDA. */
+smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, double* u, smpm_report* rep,
+                             void* stream);
+
+/* Autotuner: lays the batch out for each of candidates[ncand] team sizes
+ * that fits, times one solve of (f, g) after a warm-up solve (u is
+ * overwritten), keeps the fastest.  ms_out (host, ncand, may be null)
+ * receives each candidate's time (-1 when it does not fit); chosen (may be
+ * null) the team size kept. */
+smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, double* u, void* stream,
+                                const int* candidates, int ncand, double* ms_out, int* chosen);
+
+/* Release the batch (not its handles; null is ignored). */
+void smpm_batch_destroy(smpm_batch b);
 
 /* Release every resource of h (null is ignored). */
 void smpm_destroy(smpm_handle h);

@@ -6,6 +6,6 @@ The computation lives in the CUDA library ``libsmpm.so`` behind the C ABI of
 ``include/smpm.h``; ``Grid`` is its Python binding.  ``inputs`` holds the
 seeded synthetic workloads.
 """
-from ._binding import Grid, SmpmError, default_opts, lib  # noqa: F401
+from ._binding import Batch, Grid, SmpmError, default_opts, factor_many, lib  # noqa: F401
 
-__all__ = ["Grid", "SmpmError", "default_opts", "lib"]
+__all__ = ["Batch", "Grid", "SmpmError", "default_opts", "factor_many", "lib"]

@@ -27,6 +27,7 @@ EXPORTS = [
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
     "smpm_apply_deflation_noalloc", "smpm_apply_schur32", "schur_solve_adjoint",
+    "smpm_factor_many", "smpm_batch_create", "smpm_batch_info", "smpm_batch_solve", "smpm_batch_autotune", "smpm_batch_destroy",
 ]
 
 
@@ -85,10 +86,18 @@ def lib():
         L.smpm_host_factor.argtypes = [P, ctypes.c_char_p, P, LL, ctypes.POINTER(LL)]
         L.smpm_destroy.argtypes = [P]
         L.smpm_destroy.restype = None
+        L.smpm_factor_many.argtypes = [P, I, ctypes.POINTER(SmpmOpts), P]
+        L.smpm_batch_create.argtypes = [P, I, P, I, I, ctypes.POINTER(P)]
+        L.smpm_batch_info.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL),
+                                      ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]
+        L.smpm_batch_solve.argtypes = [P, P, P, P, ctypes.POINTER(SmpmReport), P]
+        L.smpm_batch_autotune.argtypes = [P, P, P, P, P, P, I, P, ctypes.POINTER(I)]
+        L.smpm_batch_destroy.argtypes = [P]
+        L.smpm_batch_destroy.restype = None
         L.smpm_last_error.argtypes = []
         L.smpm_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("smpm_default_opts", "smpm_destroy", "smpm_last_error"):
+            if name not in ("smpm_default_opts", "smpm_destroy", "smpm_last_error", "smpm_batch_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -252,3 +261,73 @@ class Grid:
 
     def null_vectors(self, uL, uS, uC, stream=None):
         check(lib().smpm_null_vectors(self.h, _ptr(uL), _ptr(uS), _ptr(uC), _stream(stream)))
+
+
+def factor_many(grids, stream=None, **opts):
+    """schur_factor for many grids with the same options; the host factor
+    steps run in parallel."""
+    o = default_opts(**opts)
+    hs = (ctypes.c_void_p * len(grids))(*[g.h for g in grids])
+    check(lib().smpm_factor_many(hs, len(grids), ctypes.byref(o), _stream(stream)))
+    for g in grids:
+        g.opts = o
+        g.factored = True
+
+
+class Batch:
+    """Many factored grids (and right-hand sides) solved in one persistent
+    launch (smpm_batch_*).  f, g, u are packed problem-major: problem p's
+    k-th right-hand side starts at offsets()[p] + k * r_p (g: with kp)."""
+
+    def __init__(self, grids, nrhs, team_size=0, use_graph=True):
+        self.grids = list(grids)
+        self.nrhs = [int(k) for k in nrhs]
+        hs = (ctypes.c_void_p * len(self.grids))(*[g.h for g in self.grids])
+        ks = (ctypes.c_int * len(self.grids))(*self.nrhs)
+        b = ctypes.c_void_p()
+        check(lib().smpm_batch_create(hs, len(self.grids), ks, int(team_size), 1 if use_graph else 0,
+                                      ctypes.byref(b)))
+        self.b = b
+        info = self.info()
+        self.f_len, self.g_len, self.ntasks = info["f_len"], info["g_len"], info["ntasks"]
+
+    def info(self):
+        fl, gl, nt = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        ts, nteams, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(lib().smpm_batch_info(self.b, ctypes.byref(fl), ctypes.byref(gl), ctypes.byref(nt), ctypes.byref(ts),
+                                    ctypes.byref(nteams), ctypes.byref(ms)))
+        return {"f_len": fl.value, "g_len": gl.value, "ntasks": nt.value, "team_size": ts.value,
+                "nteams": nteams.value, "last_ms": ms.value}
+
+    def offsets(self, kind="f"):
+        """Start of each problem's block in the packed f/u ("f") or g ("g")."""
+        out, o = [], 0
+        for g, k in zip(self.grids, self.nrhs):
+            out.append(o)
+            o += k * (g.r if kind == "f" else g.kp)
+        return out
+
+    def solve(self, f, u, g=None, stream=None, allow_notconv=False):
+        reps = (SmpmReport * self.ntasks)()
+        st = lib().smpm_batch_solve(self.b, _ptr(f), _ptr(g), _ptr(u), reps, _stream(stream))
+        check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
+        return [r.as_dict() for r in reps]
+
+    def autotune(self, f, u, g=None, candidates=(8, 16, 19, 38, 76, 152), stream=None):
+        cands = (ctypes.c_int * len(candidates))(*candidates)
+        ms = (ctypes.c_double * len(candidates))()
+        chosen = ctypes.c_int()
+        check(lib().smpm_batch_autotune(self.b, _ptr(f), _ptr(g), _ptr(u), _stream(stream), cands, len(candidates),
+                                        ms, ctypes.byref(chosen)))
+        return chosen.value, {c: ms[i] for i, c in enumerate(candidates)}
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().smpm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -70,11 +70,20 @@ struct GmresArgs {
   int trace_cap;
   const int* skip;  // when non-null and set on entry, the kernel returns at once
   int* its_out;     // when non-null: Arnoldi steps of this launch
+  int G;            // CTAs working on this solve (a team; the whole grid for one solve)
+  int base;         // first CTA of the team: the CTA's rank is blockIdx.x - base
+  S* wscr;          // when non-null: per-CTA global scratch for w, w2 (2 (ES+1) per rank)
 };
+
+// rank of this CTA within the team that works on a solve
+template <typename S>
+__device__ __forceinline__ int team_rank(const GmresArgs<S>& a) {
+  return (int)blockIdx.x - a.base;
+}
 
 #define GM_TRACE(tag)                                                                   \
   do {                                                                                  \
-    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && trace_n + 2 <= a.trace_cap) { \
+    if (a.trace && team_rank(a) == 0 && threadIdx.x == 0 && trace_n + 2 <= a.trace_cap) { \
       a.trace[trace_n++] = (tag);                                                       \
       a.trace[trace_n++] = clock64();                                                   \
     }                                                                                   \
@@ -85,22 +94,23 @@ __device__ __forceinline__ S ldcg(const S* p) {
   return __ldcg(p);
 }
 
-// Grid barrier on a monotonic counter: thread 0 of each CTA adds one with
+// Team barrier on a monotonic counter: thread 0 of each CTA adds one with
 // release semantics and polls with acquire loads until the counter reaches
-// the CTA's next epoch (a multiple of the grid size).  Bounded spin; err is
-// set on timeout and the caller unwinds.
+// the CTA's next epoch (a multiple of the team size G; the team is the whole
+// grid for a single solve).  Bounded spin; err is set on timeout and the
+// caller unwinds.
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch) {
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    epoch += gridDim.x;
+    epoch += (unsigned)G;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     long long spins = 0;
     while ((int)(ld_acquire(bar) - epoch) < 0) {
@@ -161,8 +171,13 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
   s.av = q; q += M;
   s.z = q; q += M;
   s.red = q; q += 256;
-  s.w = q; q += a.ES + 1;
-  s.w2 = q; q += a.ES + 1;
+  if (a.wscr) {
+    s.w = a.wscr + (size_t)team_rank(a) * 2 * (a.ES + 1);
+    s.w2 = s.w + a.ES + 1;
+  } else {
+    s.w = q; q += a.ES + 1;
+    s.w2 = q; q += a.ES + 1;
+  }
   s.V = q;
   if (a.basis_smem) q += (size_t)(m + 1) * a.ES;
   q = reinterpret_cast<S*>((reinterpret_cast<size_t>(q) + 15) & ~size_t(15));
@@ -172,9 +187,9 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
 
 template <typename S>
 inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
-                               long long d, int stream_elems = 0) {
+                               long long d, int stream_elems = 0, bool w_global = false) {
   size_t dbl = 2 + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
-  size_t sel = 4 * (size_t)M + 256 + 2 * (size_t)(ES + 1);
+  size_t sel = 4 * (size_t)M + 256 + (w_global ? 0 : 2 * (size_t)(ES + 1));
   if (basis_smem) sel += (size_t)(m + 1) * ES;
   if (mats_smem) sel += (size_t)nown_b * (2 * (size_t)M * M + 4 * (size_t)n * n) + (size_t)nown_w * M * M;
   sel += 2 * (size_t)stream_elems;
@@ -206,7 +221,7 @@ __device__ __forceinline__ const S* mat_Tw(const GmresArgs<S>& a, const Smem<S>&
 
 template <typename S>
 __device__ __forceinline__ S* basis(const GmresArgs<S>& a, const Smem<S>& s, int l) {
-  return a.basis_smem ? s.V + (size_t)l * a.ES : a.vown + ((size_t)blockIdx.x * (a.m + 1) + l) * a.ES;
+  return a.basis_smem ? s.V + (size_t)l * a.ES : a.vown + ((size_t)team_rank(a) * (a.m + 1) + l) * a.ES;
 }
 
 // ---- matrix stream: bulk copies into two shared-memory buffers ------------
@@ -251,14 +266,14 @@ __device__ void ms_issue(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& 
   if (ms.nitems == 0) return;
   const long long i = ms.issued++;
   if (threadIdx.x != 0) return;
-  const int M = a.g.M, n = a.g.n, G = gridDim.x;
+  const int M = a.g.M, n = a.g.n, G = a.G, rank = team_rank(a);
   const int it = (int)(i % ms.nitems), b = (int)(i & 1);
   S* dst = s.mats + (size_t)b * a.buf_elems;
   unsigned long long* bar = s.mbar + b;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const unsigned mm = (unsigned)(M * M * sizeof(S)), xx = (unsigned)(4 * n * n * sizeof(S));
   if (it < 2 * ms.nb) {
-    const int k = it >> 1, ib = blockIdx.x + k * G;
+    const int k = it >> 1, ib = rank + k * G;
     if ((it & 1) == 0) {
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(mm + xx)
                    : "memory");
@@ -269,7 +284,7 @@ __device__ void ms_issue(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& 
       bulk_g2s(dst, a.Tc + (size_t)a.black[ib] * M * M, mm, bar);
     }
   } else {
-    const int k = it - 2 * ms.nb, iw = blockIdx.x + k * G;
+    const int k = it - 2 * ms.nb, iw = rank + k * G;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(mm) : "memory");
     bulk_g2s(dst, a.Tc + (size_t)a.white[iw] * M * M, mm, bar);
   }
@@ -419,8 +434,8 @@ __device__ void push_step(const GmresArgs<S>& a, const Smem<S>& s, int e, const 
 template <typename S>
 __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
   const int d = (int)a.g.d;
-  const int per = (d + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * per, r1 = min(d, r0 + per);
+  const int per = (d + a.G - 1) / a.G;
+  const int r0 = team_rank(a) * per, r1 = min(d, r0 + per);
   if (r0 >= r1) return;
   for (int j = threadIdx.x; j < d; j += blockDim.x) s.cst[j] = __ldcg(a.c + j);
   __syncthreads();
@@ -531,7 +546,7 @@ template <typename S>
 __device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
   const int M2 = 2 * a.g.M;
   int k = i / M2, ii = i % M2;
-  int ib = blockIdx.x + k * gridDim.x;
+  int ib = team_rank(a) + k * a.G;
   if (k >= a.nown_b || ib >= a.nblack) return -1;
   return block_slot(a.g, a.black[ib], ii);
 }
@@ -541,9 +556,9 @@ template <typename S>
 __device__ bool black_phase(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>* ms, const S* src, double sc,
                             const S* own) {
   const DevGeo& g = a.g;
-  const int M = g.M, G = gridDim.x;
+  const int M = g.M, G = a.G;
   for (int k = 0; k < a.nown_b; ++k) {
-    int ib = blockIdx.x + k * G;
+    int ib = team_rank(a) + k * G;
     if (ib >= a.nblack) break;
     int e = a.black[ib];
     for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
@@ -577,17 +592,17 @@ template <typename S>
 __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, double sc, bool t_done,
                          int& trace_n, unsigned& epoch, MatStream<S>* ms = nullptr) {
   const DevGeo& g = a.g;
-  const int G = gridDim.x;
+  const int G = a.G;
   if (a.precond == 0) {
-    for (long long e = blockIdx.x; e < g.nel; e += G) push_step(a, s, (int)e, src, sc);
-    return grid_sync(a.bar, a.err, epoch);
+    for (long long e = team_rank(a); e < g.nel; e += G) push_step(a, s, (int)e, src, sc);
+    return grid_sync(a.bar, a.err, epoch, a.G);
   }
   if (!t_done && !black_phase(a, s, ms, src, sc, (const S*)nullptr)) return false;
   GM_TRACE(20);
-  if (!grid_sync(a.bar, a.err, epoch)) return false;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(21);
   for (int k = 0; k < a.nown_w; ++k) {
-    int iw = blockIdx.x + k * G;
+    int iw = team_rank(a) + k * G;
     if (iw >= a.nwhite) break;
     if (ms) {
       const S* T = ms_acquire(a, s, *ms);
@@ -599,35 +614,35 @@ __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, 
     }
   }
   GM_TRACE(22);
-  if (!grid_sync(a.bar, a.err, epoch)) return false;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(23);
   if (a.precond == 2) {
     coarse_rows(a, s);
     GM_TRACE(24);
-    if (!grid_sync(a.bar, a.err, epoch)) return false;
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
     GM_TRACE(25);
   }
   return true;
 }
 
+// One GMRES solve by the CTAs of a team (the whole grid for k_gmres).
+// epoch: the team barrier's epoch, carried across consecutive bodies.
+// Returns false when a barrier or copy wait timed out (err set).
 template <typename S>
-__global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  if (a.skip && *((volatile const int*)a.skip)) return;
+__device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned& epoch) {
   const Smem<S> s = carve(a, smraw);
   const DevGeo& g = a.g;
   const int M = g.M, n = g.n, m = a.m;
-  const int ES = a.ES, G = gridDim.x;
+  const int ES = a.ES, G = a.G, rank = team_rank(a);
   const int m3 = m + 3;
   int trace_n = 0;
-  unsigned epoch = 0;
 
   // ---- matrix stream (owned matrices too large for shared memory)
   MatStream<S> msd;
   msd.nb = 0;
   msd.nw = 0;
-  for (int k = 0; k < a.nown_b; ++k) msd.nb += (blockIdx.x + k * G < a.nblack) ? 1 : 0;
-  for (int k = 0; k < a.nown_w; ++k) msd.nw += (blockIdx.x + k * G < a.nwhite) ? 1 : 0;
+  for (int k = 0; k < a.nown_b; ++k) msd.nb += (rank + k * G < a.nblack) ? 1 : 0;
+  for (int k = 0; k < a.nown_w; ++k) msd.nw += (rank + k * G < a.nwhite) ? 1 : 0;
   msd.nitems = 2 * msd.nb + msd.nw;
   msd.issued = msd.consumed = 0;
   MatStream<S>* ms = a.stream_mats ? &msd : nullptr;
@@ -644,13 +659,13 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
 #define GM_FAIL()           \
   do {                      \
     ms_drain(a, s, msd);    \
-    return;                 \
+    return false;           \
   } while (0)
 
   // ---- resident copies of the owned matrices
   if (a.mats_smem) {
     for (int k = 0; k < a.nown_b; ++k) {
-      int ib = blockIdx.x + k * G;
+      int ib = rank + k * G;
       if (ib >= a.nblack) break;
       int e = a.black[ib];
       S* dst = s.mats + (size_t)k * (2 * M * M + 4 * n * n);
@@ -661,7 +676,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       for (int i = threadIdx.x; i < 4 * n * n; i += blockDim.x) dst[2 * M * M + i] = a.Xc[(size_t)ib * 4 * n * n + i];
     }
     for (int k = 0; k < a.nown_w; ++k) {
-      int iw = blockIdx.x + k * G;
+      int iw = rank + k * G;
       if (iw >= a.nwhite) break;
       int e = a.white[iw];
       S* dst = s.mats + (size_t)a.nown_b * (2 * M * M + 4 * n * n) + (size_t)k * M * M;
@@ -697,7 +712,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       nn = warp_sum(nn);
       if ((threadIdx.x & 31) == 0 && nn != 0.0) atomicAdd(accN, nn);
     }
-    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
     const double beta = sqrt(__ldcg(accN));
     if (cycle == 0) {
       beta0 = beta;
@@ -729,7 +744,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
         __syncthreads();
       }
       if (a.precond == 0) {
-        if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();  // neighbours read v_j
+        if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();  // neighbours read v_j
         if (!apply_op(a, s, a.vglob, ivj, false, trace_n, epoch, ms)) GM_FAIL();
       } else {
         if (!black_phase(a, s, ms, (const S*)nullptr, ivj, vj)) GM_FAIL();
@@ -744,7 +759,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       __syncthreads();
       owned_dots(a, s, s.w, j + 2, accD);
       GM_TRACE(5);
-      if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
+      if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
       GM_TRACE(6);
       for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
         double v = __ldcg(accD + l);
@@ -762,7 +777,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       __syncthreads();
       owned_dots(a, s, s.w2, j + 2, accE);
       GM_TRACE(8);
-      if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
+      if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
       GM_TRACE(9);
       for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
         double v = __ldcg(accE + l);
@@ -807,7 +822,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
         s.misc[2] = fabs(s.gg[j + 1]);
         s.misc[3] = (bsq <= 1e-28 * s.misc[0]) ? 1.0 : 0.0;
         s.misc[4] = bnext;
-        if (blockIdx.x == 0) {
+        if (rank == 0) {
           double* Rc = a.gs->R + (size_t)j * (kMaxRestart + 1);
           for (int l = 0; l <= j; ++l) Rc[l] = s.col[l];
           a.gs->g[j] = s.gg[j];
@@ -825,7 +840,7 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     jlast = j;
     if (nan) break;
     // ---- end of cycle: y = R^-1 g (CTA 0), x += V diag(invb) y on owned entries
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
       const int m1 = kMaxRestart + 1;
       for (int i = j - 1; i >= 0; --i) {
         double sum = a.gs->g[i];
@@ -834,10 +849,10 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       }
     }
     // the accumulators are consumed: zero them for the next cycle
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)(2 * m + 1) * m3;
+    for (size_t i = (size_t)rank * blockDim.x + threadIdx.x; i < (size_t)(2 * m + 1) * m3;
          i += (size_t)G * blockDim.x)
       a.acc[i] = 0.0;
-    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
     for (int l = threadIdx.x; l < j; l += blockDim.x) s.hs1[l] = -__ldcg(a.gs->y + l) * s.invb[l];
     __syncthreads();
     for (int i = threadIdx.x; i < ES; i += blockDim.x) {
@@ -845,11 +860,11 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
       if (sl < 0) continue;
       a.x[sl] = (S)basis_combo(a, s, (double)ldcg(a.x + sl), s.hs1, j, i);
     }
-    if (!grid_sync(a.bar, a.err, epoch)) GM_FAIL();
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
     ++cycle;
     if (converged || breakdown || total >= a.maxit) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (rank == 0 && threadIdx.x == 0) {
     a.gs->beta0 = beta0;
     a.gs->tolabs = tolabs;
     a.gs->resid = resid;
@@ -863,5 +878,14 @@ __global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
     if (a.its_out) *a.its_out = total;
   }
   ms_drain(a, s, msd);
+  return true;
 #undef GM_FAIL
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256, 1) k_gmres(GmresArgs<S> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (a.skip && *((volatile const int*)a.skip)) return;
+  unsigned epoch = 0;
+  gmres_body(a, smraw, epoch);
 }

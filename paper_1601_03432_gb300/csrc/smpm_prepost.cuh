@@ -78,31 +78,29 @@ __device__ void elem_fd(const PrePostArgs& P, int e, double* B, double* U, doubl
   elem_solve_dev(g.n, fd_x(g, P.fdx, e), fd_y(g, P.fdy, e), B, U, t1);
 }
 
-__global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+__device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& epoch) {
   const GmresArgs<double>& a = P.ga;
   const Smem<double> s = carve(a, smraw);
   const DevGeo& g = a.g;
-  const int n = g.n, nn = n * n, M = g.M, G = gridDim.x;
+  const int n = g.n, nn = n * n, M = g.M, G = a.G, rank = team_rank(a);
   double* B = fd_scratch(s);
   double* U = B + nn;
   double* t1 = U + nn;
-  unsigned epoch = 0;
   // ---- P1: zero the work vectors; b = f + tau g; u_L^T b
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
+  for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
     for (int v = 0; v < 7; ++v) P.zero[v][i] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.gacc_n; i += (long long)G * blockDim.x)
+  for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < P.gacc_n; i += (long long)G * blockDim.x)
     P.gacc[i] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x) {
+  for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x) {
     P.cb[i] = 0.0;
     if (P.cr) P.cr[i] = 0.0;
   }
   if (P.zero32[0])
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
+    for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
       for (int v = 0; v < 4; ++v) P.zero32[v][i] = 0.f;
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.gs->scal[5] = 0.0;  // inner iterations of the solve
+  if (rank == 0 && threadIdx.x == 0) a.gs->scal[5] = 0.0;  // inner iterations of the solve
   double part = 0;
-  for (long long e = blockIdx.x; e < g.nel; e += G) {
+  for (long long e = rank; e < g.nel; e += G) {
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
       const int aa = q % n, bb = q / n;
       const long long gq = e * nn + q;
@@ -120,11 +118,11 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
   }
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(P.acc + ACC_ULB, part);
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   // ---- P2: project b; w = A_e^-1 b_e; push fluxes into b_S; u_S^T b_S; Z^T b_S
   const double alpha = __ldcg(P.acc + ACC_ULB);
   double pus = 0;
-  for (long long e = blockIdx.x; e < g.nel; e += G) {
+  for (long long e = rank; e < g.nel; e += G) {
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
       const long long gq = e * nn + q;
       double v = P.b[gq] - alpha * (P.adjoint ? P.what[gq] : P.uL[gq]);
@@ -162,16 +160,16 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
   }
   pus = warp_sum(pus);
   if ((threadIdx.x & 31) == 0 && pus != 0.0) atomicAdd(P.acc + ACC_USBS, pus);
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   // ---- P3: c_hat_b = C^+ Z^T (b_S - beta u_S)
   const double beta = __ldcg(P.acc + ACC_USBS);
   if (a.precond == 2) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
+    for (int j = rank * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
       a.c[j] = __ldcg(P.cb + j) - beta * P.ZtuS[j];
-    if (!grid_sync(a.bar, a.err, epoch)) return;
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
     coarse_rows(a, s);  // a.c -> a.chat
-    if (!grid_sync(a.bar, a.err, epoch)) return;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
+    if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+    for (int j = rank * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
       P.chatb[j] = __ldcg(a.chat + j);
   }
   // ---- P4: owner entries: project b_S, rhs = P b_S
@@ -211,18 +209,23 @@ __global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
     if (bsn != 0.0) atomicAdd(P.acc + ACC_BSN, bsn);
     if (rgn != 0.0) atomicAdd(P.acc + ACC_RGN, rgn);
   }
+  return true;
 }
 
-__global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
+__global__ void __launch_bounds__(256, 1) k_pre(PrePostArgs P) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned epoch = 0;
+  pre_body(P, smraw, epoch);
+}
+
+__device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& epoch) {
   const GmresArgs<double>& a = P.ga;
   const Smem<double> s = carve(a, smraw);
   const DevGeo& g = a.g;
-  const int n = g.n, nn = n * n, M = g.M, G = gridDim.x;
+  const int n = g.n, nn = n * n, M = g.M, G = a.G, rank = team_rank(a);
   double* B = fd_scratch(s);
   double* U = B + nn;
   double* t1 = U + nn;
-  unsigned epoch = 0;
   int trace_n = 0;
   // ---- Q1-Q4: x_S
   if (P.assembled) {
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
     }
   } else {
     for (int k = 0; k < a.nown_b; ++k) {
-      const int ib = blockIdx.x + k * G;
+      const int ib = rank + k * G;
       if (ib >= a.nblack) break;
       const int e = a.black[ib];
       for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) {
@@ -245,14 +248,14 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
       block_solve(a, s, k, ib, e, s.w);
     }
     if (a.precond == 1) {
-      if (!grid_sync(a.bar, a.err, epoch)) return;
+      if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
       for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
         const long long sl = entry_slot(a, i);
         if (sl >= 0) P.xs[sl] = __ldcg(a.t + sl);
       }
     } else {
       // white step and coarse solve of y = S t, then x_S = t - Z (c_hat - c_hat_b)
-      if (!apply_op(a, s, a.x, 1.0, true, trace_n, epoch)) return;
+      if (!apply_op(a, s, a.x, 1.0, true, trace_n, epoch)) return false;
       for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
         const long long sl = entry_slot(a, i);
         if (sl < 0) continue;
@@ -261,10 +264,10 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
       }
     }
   }
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   // ---- Q5: recovery u_e = A_e^-1 (b_e - E_e x_S), residual b_S - S x_S, mean
   double pm = 0, pr = 0;
-  for (long long e = blockIdx.x; e < g.nel; e += G) {
+  for (long long e = rank; e < g.nel; e += G) {
     for (int q = threadIdx.x; q < nn; q += blockDim.x) B[q] = P.b[e * nn + q];
     for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = __ldcg(P.xs + e * M + i);
     __syncthreads();
@@ -318,15 +321,15 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
     if (pm != 0.0) atomicAdd(P.acc + ACC_MEAN, pm);
     if (pr != 0.0) atomicAdd(P.acc + ACC_RES, pr);
   }
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   // ---- Q6: zero GLL-weighted mean (adjoint: projection out of u_L, dl/dg)
   const double mean = __ldcg(P.acc + ACC_MEAN);
   if (!P.adjoint) {
-    for (long long e = blockIdx.x; e < g.nel; e += G)
+    for (long long e = rank; e < g.nel; e += G)
       for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean;
-    return;
+    return true;
   }
-  for (long long e = blockIdx.x; e < g.nel; e += G) {
+  for (long long e = rank; e < g.nel; e += G) {
     if (P.gg)
       for (int i = threadIdx.x; i < M; i += blockDim.x) {
         const int F = i / n, t = i % n;
@@ -342,8 +345,17 @@ __global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
     __syncthreads();
     for (int q = threadIdx.x; q < nn; q += blockDim.x) P.u[e * nn + q] -= mean * P.uL[e * nn + q];
   }
+  return true;
 }
 
-inline size_t prepost_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d) {
-  return gmres_smem_bytes<double>(m, M, n, ES, nown_b, nown_w, 0, 0, d) + (3 * (size_t)n * n + 64) * sizeof(double);
+__global__ void __launch_bounds__(256, 1) k_post(PrePostArgs P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned epoch = 0;
+  post_body(P, smraw, epoch);
+}
+
+inline size_t prepost_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d,
+                                 bool w_global = false) {
+  return gmres_smem_bytes<double>(m, M, n, ES, nown_b, nown_w, 0, 0, d, 0, w_global) +
+         (3 * (size_t)n * n + 64) * sizeof(double);
 }

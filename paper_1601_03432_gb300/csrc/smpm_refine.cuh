@@ -32,25 +32,26 @@ struct RefineArgs {
   double tol;
 };
 
-inline size_t refine_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d) {
-  return gmres_smem_bytes<float>(m, M, n, ES, nown_b, nown_w, 0, 0, d) + (2 * (size_t)M + 256 + 16) * sizeof(double);
+inline size_t refine_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d,
+                                bool w_global = false) {
+  return gmres_smem_bytes<float>(m, M, n, ES, nown_b, nown_w, 0, 0, d, 0, w_global) +
+         (2 * (size_t)M + 256 + 16) * sizeof(double);
 }
 
-__global__ void __launch_bounds__(256, 1) k_refine(RefineArgs R) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  if (*((volatile const int*)R.done)) return;
+// One refinement step by the CTAs of a team; returns 1 when converged (done
+// set), 0 when another inner solve follows, -1 when a barrier timed out.
+__device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& epoch) {
   const GmresArgs<float>& a = R.ga;
   const Smem<float> s = carve(a, smraw);
   double* p64 = reinterpret_cast<double*>(s.mats);
   double* z64 = p64 + a.g.M;
   double* red64 = z64 + a.g.M;
   const DevGeo& g = a.g;
-  const int n = g.n, M = g.M, G = gridDim.x;
-  unsigned epoch = 0;
+  const int n = g.n, M = g.M, G = a.G, rank = team_rank(a);
   int trace_n = 0;
   // ---- R1-R3: t = M^-1 y, S t, c_hat
-  if (!black_phase(a, s, (MatStream<float>*)nullptr, a.x, 1.0, (const float*)nullptr)) return;
-  if (!apply_op(a, s, a.x, 1.0, true, trace_n, epoch)) return;
+  if (!black_phase(a, s, (MatStream<float>*)nullptr, a.x, 1.0, (const float*)nullptr)) return -1;
+  if (!apply_op(a, s, a.x, 1.0, true, trace_n, epoch)) return -1;
   // ---- R4: x_S += t - Z (c_hat - c_hat_r); y <- 0 for the next inner solve
   for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
     const long long sl = entry_slot(a, i);
@@ -59,10 +60,10 @@ __global__ void __launch_bounds__(256, 1) k_refine(RefineArgs R) {
     if (j >= 0) R.xS[sl] += (double)__ldcg(a.t + sl) - (__ldcg(a.chat + j) - R.chat_r[j]);
     a.x[sl] = 0.f;
   }
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
   // ---- R5: r = b_S - S x_S (FP64), ||r||^2, Z^T r
   double pr = 0;
-  for (long long e = blockIdx.x; e < g.nel; e += G) {
+  for (long long e = rank; e < g.nel; e += G) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) p64[i] = __ldcg(R.xS + e * M + i);
     __syncthreads();
     gemv_split(R.Tc64 + (size_t)e * M * M, M, p64, z64, M, M, red64);
@@ -90,13 +91,13 @@ __global__ void __launch_bounds__(256, 1) k_refine(RefineArgs R) {
   }
   pr = warp_sum(pr);
   if ((threadIdx.x & 31) == 0 && pr != 0.0) atomicAdd(R.rn, pr);
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
   // ---- R6: convergence test (uniform), else c_hat_r = C^+ Z^T r
   const double rho = sqrt(__ldcg(R.rn)), target = R.tol * sqrt(*R.rgn);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *R.nref += 1;
+  if (rank == 0 && threadIdx.x == 0) *R.nref += 1;
   if (rho <= target) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *R.done = 1;
-    return;
+    if (rank == 0 && threadIdx.x == 0) *R.done = 1;
+    return 1;
   }
   {
     GmresArgs<float> b = a;
@@ -104,13 +105,21 @@ __global__ void __launch_bounds__(256, 1) k_refine(RefineArgs R) {
     b.chat = R.chat_r;
     coarse_rows(b, s);
   }
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
   // ---- R7: next inner right-hand side P r (FP32); Z^T r back to zero
   for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
     const long long sl = entry_slot(a, i);
     if (sl < 0) continue;
     R.rhs32[sl] = (float)deflate_slot_cg(g, (const double*)R.r, R.chat_r, R.Rs64, sl);
   }
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < g.d; j += (long long)G * blockDim.x)
+  for (long long j = (long long)rank * blockDim.x + threadIdx.x; j < g.d; j += (long long)G * blockDim.x)
     R.cr[j] = 0.0;
+  return 0;
+}
+
+__global__ void __launch_bounds__(256, 1) k_refine(RefineArgs R) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (*((volatile const int*)R.done)) return;
+  unsigned epoch = 0;
+  refine_body(R, smraw, epoch);
 }

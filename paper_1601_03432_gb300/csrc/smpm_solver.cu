@@ -426,6 +426,7 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
 #include "smpm_gmres.cuh"
 #include "smpm_prepost.cuh"
 #include "smpm_refine.cuh"
+#include "smpm_batch.cuh"
 
 // y = S v streamed from HBM: a persistent CTA per SM walks its elements
 // e = c, c+G, ... and keeps STAGES of them in flight with bulk copies of the
@@ -619,6 +620,18 @@ void free_all(smpm_handle h) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum minus
+// its static shared memory.  The limit belongs to the kernel, shared by every
+// handle of the process, so it is never lowered to one handle's size.
+template <typename K>
+cudaError_t set_smem_limit(K* fn, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 // count square blocks of size b x b, each transposed (row-major -> column-major)
 std::vector<double> transpose_blocks(const std::vector<double>& src, int b, size_t count) {
   std::vector<double> out(src.size());
@@ -655,7 +668,7 @@ smpm_status launch_schur_stream(smpm_handle h, const S* T, const S* v, S* y, cud
     CHECK_LAUNCH();
     return SMPM_OK;
   }
-  CU(cudaFuncSetAttribute(k_schur_stream<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CU(set_smem_limit(k_schur_stream<S>, optin));
   const unsigned grid = (unsigned)std::min<long long>((long long)sms * cps, g.nel);
   k_schur_stream<S><<<grid, kElemThreads, smem, st>>>(g, T, v, y, stages);
   CHECK_LAUNCH();
@@ -781,6 +794,8 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   a.trace = h->wtrace;
   a.trace_cap = h->wtrace ? kTraceCap : 0;
   a.skip = nullptr;
+  a.G = h->gm.grid;
+  a.base = 0;
   return a;
 }
 
@@ -802,20 +817,18 @@ GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
   a.trace = nullptr;
   a.trace_cap = 0;
   a.skip = h->wdone;
+  a.G = h->gm.grid;
+  a.base = 0;
   return a;
 }
 
-// One right-hand side, FP32 inner GMRES inside FP64 iterative refinement
-// (GMRES-IR): k_pre, then kMaxRefine pairs (k_gmres<float>, k_refine) that
-// return at once after convergence, then k_post on the assembled x_S.
-smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, double* u, double tol,
-                            smpm_report* rep, cudaStream_t st) {
+// Arguments of k_pre / k_post for one solve (mixed: also the FP32 buffers
+// that k_pre clears; adj: the transposed system).  The all-global layout.
+PrePostArgs prepost_args(smpm_handle h, double tol, const double* f, const double* gn, double* u, bool mixed,
+                         bool adj = false, double* gg = nullptr) {
   const int m = h->opts.restart;
-  smpm_report R{};
-  const long long launches0 = h->launches;
-  CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
   PrePostArgs P{};
-  P.ga = gmres_args(h, tol);
+  P.ga = gmres_args(h, tol, adj);
   P.ga.mats_smem = 0;
   P.ga.basis_smem = 0;
   P.ga.stream_mats = 0;
@@ -827,11 +840,55 @@ smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, do
   for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
   P.gacc = h->wacc;
   P.gacc_n = (long long)(2 * m + 1) * (m + 3);
-  float* z32[4] = {h->wx32, h->wt32, h->wy32, h->wV32};
-  for (int i = 0; i < 4; ++i) P.zero32[i] = z32[i];
-  P.cr = h->wcr;
-  P.rg32 = h->wrg32;
-  P.assembled = 0;
+  if (mixed) {
+    float* z32[4] = {h->wx32, h->wt32, h->wy32, h->wV32};
+    for (int i = 0; i < 4; ++i) P.zero32[i] = z32[i];
+    P.cr = h->wcr;
+    P.rg32 = h->wrg32;
+  }
+  if (adj) {
+    P.adjoint = 1;
+    P.gg = gg;
+    P.gn = nullptr;
+    P.fdx = h->dfdxT; P.fdy = h->dfdyT; P.uS = h->duSa; P.ZtuS = h->dZtuSa;
+  }
+  return P;
+}
+
+// Arguments of one refinement step after the inner solve with arguments a.
+RefineArgs refine_args(smpm_handle h, const GmresArgs<float>& a, double tol) {
+  RefineArgs RA{};
+  RA.ga = a;
+  RA.ga.mats_smem = 0;
+  RA.ga.basis_smem = 0;
+  RA.ga.stream_mats = 0;
+  RA.ga.rhs = h->wrg32;
+  RA.Tc64 = h->dT;
+  RA.Rs64 = h->dRs;
+  RA.xS = h->wxs;
+  RA.bS = h->wbS;
+  RA.r = h->wr;
+  RA.cr = h->wcr;
+  RA.chat_r = h->wchatb;
+  RA.rgn = h->wacc8 + ACC_RGN;
+  RA.rn = h->wrn;
+  RA.done = h->wdone;
+  RA.nref = h->wnref;
+  RA.rhs32 = h->wrg32;
+  RA.tol = tol;
+  return RA;
+}
+
+// One right-hand side, FP32 inner GMRES inside FP64 iterative refinement
+// (GMRES-IR): k_pre, then kMaxRefine pairs (k_gmres<float>, k_refine) that
+// return at once after convergence, then k_post on the assembled x_S.
+smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, double* u, double tol,
+                            smpm_report* rep, cudaStream_t st) {
+  const int m = h->opts.restart;
+  smpm_report R{};
+  const long long launches0 = h->launches;
+  CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
+  PrePostArgs P = prepost_args(h, tol, f, gn, u, true);
   CU(cudaEventRecord(h->evp, st));
   {
     P.ga.bar = h->wbar + 0;
@@ -855,26 +912,9 @@ smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, do
                                      h->gm32.smem, st));
       CHECK_LAUNCH();
     }
-    RefineArgs RA{};
-    RA.ga = a;
-    RA.ga.mats_smem = 0;
-    RA.ga.basis_smem = 0;
-    RA.ga.stream_mats = 0;
+    RefineArgs RA = refine_args(h, a, tol);
     RA.ga.bar = h->wbar + 3 + 2 * ref;
-    RA.ga.rhs = h->wrg32;
-    RA.Tc64 = h->dT;
-    RA.Rs64 = h->dRs;
-    RA.xS = h->wxs;
-    RA.bS = h->wbS;
-    RA.r = h->wr;
-    RA.cr = h->wcr;
-    RA.chat_r = h->wchatb;
-    RA.rgn = h->wacc8 + ACC_RGN;
     RA.rn = h->wrn + ref;
-    RA.done = h->wdone;
-    RA.nref = h->wnref;
-    RA.rhs32 = h->wrg32;
-    RA.tol = tol;
     void* args[] = {&RA};
     CU(cudaLaunchCooperativeKernel((const void*)k_refine, dim3(h->gm.grid), dim3(kGmresThreads), args,
                                    h->gm32.smem_ref, st));
@@ -946,26 +986,8 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   // one memset per solve: barrier counters of the three kernels, error flag,
   // pre/post accumulators (contiguous); everything else is zeroed in k_pre
   CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
-  PrePostArgs P{};
-  P.ga = gmres_args(h, tol, adj);
-  P.ga.mats_smem = 0;
-  P.ga.basis_smem = 0;
-  P.ga.stream_mats = 0;
-  P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
-  P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
-  P.chatb = h->wchatb; P.xs = h->wxs; P.u = u; P.acc = h->wacc8;
-  if (adj) {
-    P.adjoint = 1;
-    P.gg = gg;
-    P.gn = nullptr;
-    P.fdx = h->dfdxT; P.fdy = h->dfdyT; P.uS = h->duSa; P.ZtuS = h->dZtuSa;
-  }
-  P.ga.trace = nullptr;
+  PrePostArgs P = prepost_args(h, tol, f, gn, u, false, adj, gg);
   P.ga.bar = h->wbar + 0;
-  double* zs[7] = {h->wx, h->wt, h->wy, h->wV, h->wbS, h->wrg, h->wxs};
-  for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
-  P.gacc = h->wacc;
-  P.gacc_n = (long long)(2 * m + 1) * (m + 3);
   {
     void* args[] = {&P};
     CU(cudaEventRecord(h->evp, st));
@@ -1028,6 +1050,229 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
 }  // namespace
 
 // ================================================================ C ABI
+
+// ===================================================================== batch
+struct smpm_batch_s {
+  std::vector<smpm_handle> hs;
+  std::vector<int> nrhs;
+  std::vector<long long> foff, goff;  // start of problem p's block in the packed f (u) and g
+  long long f_len = 0, g_len = 0, ntasks = 0;
+  int grid = 0, team_size = 0, nteams = 0, use_graph = 1;
+  size_t smem = 0;
+  BatchTask* dtasks = nullptr;
+  int *dbegin = nullptr, *dteam = nullptr, *derr = nullptr;
+  unsigned* dbars = nullptr;
+  BatchIO* dio = nullptr;
+  TaskReport* drep = nullptr;
+  BatchIO* hio = nullptr;        // pinned
+  TaskReport* hrep = nullptr;    // pinned
+  int* herr = nullptr;           // pinned
+  std::vector<void*> allocs;     // device memory of the current team layout
+  std::vector<long long> task_of;  // report index of (problem p, rhs k): task_of[foff-like prefix]
+  std::vector<long long> rhs_base;
+  cudaStream_t bs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ein = nullptr, eout = nullptr;
+  float last_ms = 0;
+};
+
+namespace {
+
+void batch_free_layout(smpm_batch b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+  b->dtasks = nullptr;
+  b->dbegin = b->dteam = nullptr;
+}
+
+template <typename P>
+smpm_status balloc(smpm_batch b, P** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+  if (e != cudaSuccess) return fail(SMPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  b->allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return SMPM_OK;
+}
+
+// Lay the batch out for teams of T CTAs: longest-processing-time assignment
+// of whole problems to teams, per-problem scratch for that team size, the
+// task table (one task per right-hand side) and the launch's shared memory.
+smpm_status batch_layout(smpm_batch b, int T) {
+  batch_free_layout(b);
+  int dev = 0, sms = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (T < 1 || T > sms) return fail(SMPM_EINVAL, "team size must be in [1, number of SMs]");
+  const int np = (int)b->hs.size();
+  b->grid = sms;
+  b->team_size = T;
+  b->nteams = sms / T;
+  // cost estimate of a problem: right-hand sides x operator entries
+  std::vector<double> cost(np);
+  std::vector<int> order(np);
+  for (int p = 0; p < np; ++p) {
+    const Geometry& g = b->hs[p]->g;
+    cost[p] = (double)b->nrhs[p] * ((double)g.nel * g.M * g.M + 2e4 * T);
+    order[p] = p;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<double> load(b->nteams, 0.0);
+  std::vector<std::vector<int>> plist(b->nteams);
+  for (int p : order) {
+    int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[t] += cost[p];
+    plist[t].push_back(p);
+  }
+  // per-problem layout for G = T (all-global operator and basis)
+  struct PL {
+    int nown_b, nown_w, ES;
+    bool wg;
+    double* vown64;
+    float* vown32;
+    double* wscr64;
+    float* wscr32;
+  };
+  std::vector<PL> pl(np);
+  size_t smem = 0;
+  smpm_status st;
+  for (int p = 0; p < np; ++p) {
+    smpm_handle h = b->hs[p];
+    const Geometry& g = h->g;
+    const int nb = (int)h->f.black.size(), nw = (int)h->f.white.size(), m = h->opts.restart;
+    PL& L = pl[p];
+    L.nown_b = (nb + T - 1) / T;
+    L.nown_w = (nw + T - 1) / T;
+    L.ES = 2 * g.M * L.nown_b;
+    if (L.ES % 2 == 0) L.ES += 1;
+    const bool mixed = h->opts.precision == 1;
+    auto need = [&](bool wg) {
+      size_t a = prepost_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg);
+      if (mixed) {
+        a = std::max(a, gmres_smem_bytes<float>(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, 0, 0, g.d, 0, wg));
+        a = std::max(a, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg));
+      } else {
+        a = std::max(a, gmres_smem_bytes<double>(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, 0, 0, g.d, 0, wg));
+      }
+      return a + kBatchHdr;
+    };
+    L.wg = need(false) > (size_t)optin;
+    const size_t nd = need(L.wg);
+    if (nd > (size_t)optin) return fail(SMPM_EINVAL, "a problem of the batch is too large for teams of this size");
+    smem = std::max(smem, nd);
+    L.vown64 = nullptr;
+    L.vown32 = nullptr;
+    L.wscr64 = nullptr;
+    L.wscr32 = nullptr;
+    const size_t vn = (size_t)T * (m + 1) * L.ES;
+    if (!mixed && (st = balloc(b, &L.vown64, vn))) return st;
+    if (mixed && (st = balloc(b, &L.vown32, vn))) return st;
+    if (L.wg) {
+      if ((st = balloc(b, &L.wscr64, (size_t)T * 2 * (L.ES + 1)))) return st;
+      if (mixed && (st = balloc(b, &L.wscr32, (size_t)T * 2 * (L.ES + 1)))) return st;
+    }
+  }
+  // task table
+  std::vector<BatchTask> tasks;
+  std::vector<int> begin(b->nteams + 1, 0);
+  b->task_of.assign(b->ntasks, -1);
+  for (int t = 0; t < b->nteams; ++t) {
+    begin[t] = (int)tasks.size();
+    for (int p : plist[t]) {
+      smpm_handle h = b->hs[p];
+      const PL& L = pl[p];
+      const bool mixed = h->opts.precision == 1;
+      const double tol = h->opts.tol;
+      for (int k = 0; k < b->nrhs[p]; ++k) {
+        BatchTask bt{};
+        bt.P = prepost_args(h, tol, nullptr, nullptr, nullptr, mixed);
+        auto team_fields = [&](auto& a) {
+          a.G = T;
+          a.base = t * T;
+          a.nown_b = L.nown_b;
+          a.nown_w = L.nown_w;
+          a.ES = L.ES;
+          a.mats_smem = 0;
+          a.basis_smem = 0;
+          a.stream_mats = 0;
+          a.bar = b->dbars + t;
+          a.err = b->derr;
+          a.trace = nullptr;
+          a.trace_cap = 0;
+          a.skip = nullptr;
+          a.its_out = nullptr;
+        };
+        team_fields(bt.P.ga);
+        bt.P.ga.vown = L.vown64;
+        bt.P.ga.wscr = L.wscr64;
+        if (mixed) {
+          bt.a32 = gmres_args32(h, kInnerTol);
+          team_fields(bt.a32);
+          bt.a32.vown = L.vown32;
+          bt.a32.wscr = L.wscr32;
+          bt.R = refine_args(h, bt.a32, tol);
+        }
+        bt.precision = mixed ? 1 : 0;
+        bt.has_g = 1;
+        bt.f_off = b->foff[p] + (long long)k * h->g.r;
+        bt.u_off = bt.f_off;
+        bt.g_off = b->goff[p] + (long long)k * h->g.kp;
+        bt.ctl = h->wctl;
+        bt.its = reinterpret_cast<int*>(h->wctl + 592);
+        bt.rn = h->wrn;
+        b->task_of[b->rhs_base[p] + k] = (long long)tasks.size();
+        tasks.push_back(bt);
+      }
+    }
+  }
+  begin[b->nteams] = (int)tasks.size();
+  std::vector<int> team_of(sms, -1);
+  for (int c = 0; c < b->nteams * T; ++c) team_of[c] = c / T;
+  if ((st = balloc(b, &b->dtasks, tasks.size())) || (st = balloc(b, &b->dbegin, begin.size())) ||
+      (st = balloc(b, &b->dteam, team_of.size())))
+    return st;
+  CU(cudaMemcpy(b->dtasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(b->dbegin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(b->dteam, team_of.data(), team_of.size() * sizeof(int), cudaMemcpyHostToDevice));
+  b->smem = smem;
+  CU(set_smem_limit(k_batch, optin));
+  int per = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kGmresThreads, smem));
+  if (per < 1) return fail(SMPM_ECUDA, "the batch kernel does not fit on an SM");
+  return SMPM_OK;
+}
+
+// The device work of one batched solve, in stream order.
+smpm_status batch_enqueue(smpm_batch b, cudaStream_t st) {
+  CU(cudaMemcpyAsync(b->dio, b->hio, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(b->dbars, 0, sizeof(unsigned) * b->grid, st));
+  CU(cudaMemsetAsync(b->derr, 0, sizeof(int), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(kGmresThreads);
+  cfg.dynamicSmemBytes = b->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int ctl = (int)kCtlBytes;
+  CU(cudaLaunchKernelEx(&cfg, k_batch, (const BatchTask*)b->dtasks, (const int*)b->dbegin, (const int*)b->dteam,
+                        (const BatchIO*)b->dio, b->drep, ctl));
+  CU(cudaMemcpyAsync(b->hrep, b->drep, sizeof(TaskReport) * b->ntasks, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(b->herr, b->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return SMPM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void smpm_default_opts(smpm_opts* o) {
@@ -1109,7 +1354,12 @@ smpm_status smpm_node_mass(smpm_handle h, double* wq) {
   return SMPM_OK;
 }
 
-smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Options check shared by the factor entry points.
+smpm_status check_factor_opts(smpm_handle h, const smpm_opts* o, smpm_opts* out) {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   smpm_opts opts;
   smpm_default_opts(&opts);
@@ -1122,7 +1372,22 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   if (h->g.d < 2 && opts.precond > 0)
     return fail(SMPM_EINVAL, "with a single interface the only block-Jacobi block is all of the singular S; "
                              "use precond = 0");
-  cudaStream_t st = as_stream(stream);
+  *out = opts;
+  return SMPM_OK;
+}
+
+// Device half of the factor step: uploads of the host factors in h->f,
+// workspaces and launch shapes.
+smpm_status factor_device(smpm_handle h, cudaStream_t st);
+
+}  // namespace
+
+extern "C" {
+
+smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
+  smpm_opts opts;
+  smpm_status cs = check_factor_opts(h, o, &opts);
+  if (cs != SMPM_OK) return cs;
   free_all(h);
   h->factored = false;
   h->opts = opts;
@@ -1130,6 +1395,50 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   std::string err;
   int rc = factor_host(h->g, opts, &h->f, &err);
   if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
+  return factor_device(h, as_stream(stream));
+}
+
+smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* o, void* stream) {
+  if (!hs || count < 1) return fail(SMPM_EINVAL, "bad arguments");
+  smpm_opts opts;
+  for (int i = 0; i < count; ++i) {
+    smpm_status cs = check_factor_opts(hs[i], o, &opts);
+    if (cs != SMPM_OK) return cs;
+  }
+  std::vector<Factors> fs(count);
+  std::vector<std::string> errs(count);
+  std::vector<int> rc(count, SMPM_OK), order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return hs[a]->g.d * (long long)hs[a]->g.M > hs[b]->g.d * (long long)hs[b]->g.M;
+  });
+  // one problem per thread, largest first (the factor step's own parallel
+  // loops run single-threaded inside this region)
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int k = 0; k < count; ++k) {
+    const int i = order[k];
+    rc[i] = factor_host(hs[i]->g, opts, &fs[i], &errs[i]);
+  }
+  cudaStream_t st = as_stream(stream);
+  for (int i = 0; i < count; ++i) {
+    if (rc[i] != SMPM_OK) return fail(static_cast<smpm_status>(rc[i]), errs[i]);
+    smpm_handle h = hs[i];
+    free_all(h);
+    h->factored = false;
+    h->opts = opts;
+    h->f = std::move(fs[i]);
+    smpm_status s = factor_device(h, st);
+    if (s != SMPM_OK) return s;
+  }
+  return SMPM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+smpm_status factor_device(smpm_handle h, cudaStream_t st) {
+  const smpm_opts opts = h->opts;
   const Geometry& g = h->g;
   DevGeo& dg = h->dg;
   dg.mx = g.mx; dg.my = g.my; dg.n = g.n; dg.M = g.M;
@@ -1194,7 +1503,7 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
       gm.buf_elems = L.buf_elems;
       gm.smem = L.smem;
     }
-    CU(cudaFuncSetAttribute(k_gmres<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem));
+    CU(set_smem_limit(k_gmres<double>, smem_optin));
     int per_sm = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<double>, kGmresThreads, gm.smem));
     if (per_sm < 1) return fail(SMPM_ECUDA, "the GMRES kernel does not fit on an SM");
@@ -1209,12 +1518,12 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
       g32.stream_mats = L.stream_mats;
       g32.buf_elems = L.buf_elems;
       g32.smem = L.smem;
-      CU(cudaFuncSetAttribute(k_gmres<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g32.smem));
+      CU(set_smem_limit(k_gmres<float>, smem_optin));
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<float>, kGmresThreads, g32.smem));
       if (per_sm < 1) return fail(SMPM_ECUDA, "the FP32 GMRES kernel does not fit on an SM");
       g32.smem_ref = refine_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
       if (g32.smem_ref > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the refinement kernel");
-      CU(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g32.smem_ref));
+      CU(set_smem_limit(k_refine, smem_optin));
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, kGmresThreads, g32.smem_ref));
       if (per_sm < 1) return fail(SMPM_ECUDA, "the refinement kernel does not fit on an SM");
       auto to32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
@@ -1229,8 +1538,8 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
     }
     gm.smem_pp = prepost_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
     if (gm.smem_pp > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the solve kernels");
-    CU(cudaFuncSetAttribute(k_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem_pp));
-    CU(cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gm.smem_pp));
+    CU(set_smem_limit(k_pre, smem_optin));
+    CU(set_smem_limit(k_post, smem_optin));
     for (const void* fn : {(const void*)k_pre, (const void*)k_post}) {
       int per = 0;
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kGmresThreads, gm.smem_pp));
@@ -1276,6 +1585,10 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   h->factored = true;
   return SMPM_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double tol, int nrhs, double* u,
                         smpm_report* rep, void* stream) {
@@ -1480,6 +1793,176 @@ void smpm_destroy(smpm_handle h) {
   delete h;
 }
 
+
+smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs, int team_size, int use_graph,
+                              smpm_batch* out) {
+  if (!hs || count < 1 || !nrhs || !out) return fail(SMPM_EINVAL, "bad arguments");
+  *out = nullptr;
+  for (int p = 0; p < count; ++p) {
+    if (!hs[p] || nrhs[p] < 1) return fail(SMPM_EINVAL, "null handle or nrhs < 1 in the batch");
+    if (!hs[p]->factored) return fail(SMPM_ESTATE, "a handle of the batch has not been factored");
+    for (int q = 0; q < p; ++q)
+      if (hs[q] == hs[p]) return fail(SMPM_EINVAL, "a handle appears twice in the batch");
+  }
+  smpm_batch b = new smpm_batch_s();
+  b->hs.assign(hs, hs + count);
+  b->nrhs.assign(nrhs, nrhs + count);
+  b->use_graph = use_graph ? 1 : 0;
+  long long fo = 0, go = 0, rb = 0;
+  for (int p = 0; p < count; ++p) {
+    b->foff.push_back(fo);
+    b->goff.push_back(go);
+    b->rhs_base.push_back(rb);
+    fo += (long long)nrhs[p] * hs[p]->g.r;
+    go += (long long)nrhs[p] * hs[p]->g.kp;
+    rb += nrhs[p];
+  }
+  b->f_len = fo;
+  b->g_len = go;
+  b->ntasks = rb;
+  auto bad = [&](smpm_status st) {
+    smpm_batch_destroy(b);
+    return st;
+  };
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    return bad(fail(SMPM_ECUDA, "no CUDA device"));
+  if (cudaMalloc(&b->dbars, sizeof(unsigned) * sms) || cudaMalloc(&b->derr, sizeof(int)) ||
+      cudaMalloc(&b->dio, sizeof(BatchIO)) || cudaMalloc(&b->drep, sizeof(TaskReport) * b->ntasks) ||
+      cudaMallocHost(&b->hio, sizeof(BatchIO)) || cudaMallocHost(&b->hrep, sizeof(TaskReport) * b->ntasks) ||
+      cudaMallocHost(&b->herr, sizeof(int)) || cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) ||
+      cudaEventCreate(&b->ein) || cudaEventCreate(&b->eout))
+    return bad(fail(SMPM_ENOMEM, "batch allocation failed"));
+  int T = team_size;
+  if (T <= 0) {  // default: the smallest team size of the candidate list that fits
+    T = sms;
+    for (int c : {8, 16, 19, 38, 76})
+      if (c <= sms) {
+        smpm_status st = batch_layout(b, c);
+        if (st == SMPM_OK) {
+          T = c;
+          break;
+        }
+      }
+  }
+  smpm_status st = batch_layout(b, T);
+  if (st != SMPM_OK) return bad(st);
+  *out = b;
+  return SMPM_OK;
+}
+
+smpm_status smpm_batch_info(smpm_batch b, long long* f_len, long long* g_len, long long* ntasks, int* team_size,
+                            int* nteams, double* last_ms) {
+  if (!b) return fail(SMPM_EINVAL, "null batch");
+  if (f_len) *f_len = b->f_len;
+  if (g_len) *g_len = b->g_len;
+  if (ntasks) *ntasks = b->ntasks;
+  if (team_size) *team_size = b->team_size;
+  if (nteams) *nteams = b->nteams;
+  if (last_ms) *last_ms = b->last_ms;
+  return SMPM_OK;
+}
+
+smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, double* u, smpm_report* rep,
+                             void* stream) {
+  if (!b || !f || !u) return fail(SMPM_EINVAL, "bad arguments");
+  cudaStream_t us = as_stream(stream);
+  b->hio->f = f;
+  b->hio->g = g;
+  b->hio->u = u;
+  CU(cudaEventRecord(b->ein, us));
+  CU(cudaStreamWaitEvent(b->bs, b->ein, 0));
+  if (b->use_graph) {
+    if (!b->gexec) {
+      CU(cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
+      smpm_status st = batch_enqueue(b, b->bs);
+      cudaGraph_t gr = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->bs, &gr);
+      if (st != SMPM_OK) {
+        if (gr) cudaGraphDestroy(gr);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(SMPM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      b->graph = gr;
+      CU(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+    }
+    CU(cudaEventRecord(b->ein, b->bs));
+    CU(cudaGraphLaunch(b->gexec, b->bs));
+  } else {
+    CU(cudaEventRecord(b->ein, b->bs));
+    smpm_status st = batch_enqueue(b, b->bs);
+    if (st != SMPM_OK) return st;
+  }
+  CU(cudaEventRecord(b->eout, b->bs));
+  CU(cudaStreamWaitEvent(us, b->eout, 0));
+  CU(cudaStreamSynchronize(b->bs));
+  CU(cudaEventElapsedTime(&b->last_ms, b->ein, b->eout));
+  if (*b->herr) return fail(SMPM_ETIMEOUT, "a team barrier of the batch kernel timed out");
+  smpm_status worst = SMPM_OK;
+  for (size_t p = 0; p < b->hs.size(); ++p)
+    for (int k = 0; k < b->nrhs[p]; ++k) {
+      const long long i = b->rhs_base[p] + k;
+      const TaskReport& t = b->hrep[b->task_of[i]];
+      smpm_report R{};
+      R.iterations = t.iterations;
+      R.restarts = t.restarts;
+      R.refinements = t.refinements;
+      R.converged = t.converged;
+      R.gmres_relres = t.gmres_den > 0 ? t.gmres_num / t.gmres_den : 0.0;
+      R.schur_relres = t.bsn2 > 0 ? std::sqrt(t.res2 / t.bsn2) : 0.0;
+      R.launches = 1;
+      R.gmres_ms = b->last_ms;
+      if (!std::isfinite(R.gmres_relres) || !std::isfinite(R.schur_relres))
+        return fail(SMPM_ENAN, "non-finite residual in a batched solve");
+      if (!t.converged) worst = SMPM_ENOTCONV;
+      if (rep) rep[i] = R;
+    }
+  if (worst != SMPM_OK) return fail(worst, "a batched solve did not converge");
+  return SMPM_OK;
+}
+
+smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, double* u, void* stream,
+                                const int* candidates, int ncand, double* ms_out, int* chosen) {
+  if (!b || !f || !u || !candidates || ncand < 1) return fail(SMPM_EINVAL, "bad arguments");
+  int best = -1;
+  double best_ms = 1e300;
+  for (int i = 0; i < ncand; ++i) {
+    if (ms_out) ms_out[i] = -1.0;
+    if (batch_layout(b, candidates[i]) != SMPM_OK) continue;
+    smpm_status st = smpm_batch_solve(b, f, g, u, nullptr, stream);  // warm-up (and graph capture)
+    if (st != SMPM_OK && st != SMPM_ENOTCONV) return st;
+    st = smpm_batch_solve(b, f, g, u, nullptr, stream);
+    if (st != SMPM_OK && st != SMPM_ENOTCONV) return st;
+    if (ms_out) ms_out[i] = b->last_ms;
+    if (b->last_ms < best_ms) {
+      best_ms = b->last_ms;
+      best = candidates[i];
+    }
+  }
+  if (best < 0) return fail(SMPM_EINVAL, "no candidate team size fits the batch");
+  smpm_status st = batch_layout(b, best);
+  if (st != SMPM_OK) return st;
+  if (chosen) *chosen = best;
+  return SMPM_OK;
+}
+
+void smpm_batch_destroy(smpm_batch b) {
+  if (!b) return;
+  if (b->bs) cudaStreamSynchronize(b->bs);
+  batch_free_layout(b);
+  cudaFree(b->dbars);
+  cudaFree(b->derr);
+  cudaFree(b->dio);
+  cudaFree(b->drep);
+  cudaFreeHost(b->hio);
+  cudaFreeHost(b->hrep);
+  cudaFreeHost(b->herr);
+  if (b->ein) cudaEventDestroy(b->ein);
+  if (b->eout) cudaEventDestroy(b->eout);
+  if (b->bs) cudaStreamDestroy(b->bs);
+  delete b;
+}
+
 }  // extern "C"
 
 // ============================================ allocation-free deflation
@@ -1520,7 +2003,7 @@ __global__ void __launch_bounds__(256) k_deflate_noalloc(DevGeo g, const double*
     for (int t = 0; t < n; ++t) s += v[(size_t)e1 * M + F1 * n + t] + v[(size_t)e2 * M + (F1 ^ 1) * n + t];
     c[j] = s;
   }
-  bool ok = grid_sync(bar, err, epoch);
+  bool ok = grid_sync(bar, err, epoch, (int)gridDim.x);
   if (ok) {
     const int lane = threadIdx.x & 31;
     const long long nw = nthr >> 5;
@@ -1531,7 +2014,7 @@ __global__ void __launch_bounds__(256) k_deflate_noalloc(DevGeo g, const double*
       acc = warp_sum(acc);
       if (lane == 0) chat[r] = acc;
     }
-    ok = grid_sync(bar, err, epoch);
+    ok = grid_sync(bar, err, epoch, (int)gridDim.x);
   }
   for (long long s = tid; s < g.kp; s += nthr) y[s] = ok ? deflate_slot_cg(g, v, chat, Rs, s) : nan("");
 }

@@ -1,0 +1,135 @@
+"""GPU parity of batched solves (smpm_batch_*): many right-hand sides of
+uneven grids in one persistent launch, against the oracle's direct solve and
+against the single-grid solves of the same handles.
+
+Tolerances as for single solves: relative L2 error 1e-10 (FP64) and 1e-9
+(mixed precision) against the exact discrete solution; iteration counts
+within one of the single solves (team sizes change the order of the FP64
+atomic sums, nothing else)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1601_03432_gb300 import Batch, Grid, factor_many, inputs
+from oracle.smpm import SMPMGrid
+from oracle.schur import SchurSystem
+from oracle import methods
+
+PROBLEMS = [(3, 2, 5, 2), (4, 4, 6, 1), (2, 3, 8, 3), (5, 4, 7, 2), (6, 3, 4, 1)]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1601_03432_gb300.build import build
+    build()
+    assert torch.cuda.is_available()
+
+
+def make_inputs(problems, seed, with_g=True):
+    rng = np.random.default_rng(seed)
+    fs, gs, refs = [], [], []
+    for (mx, my, n, k) in problems:
+        og = SMPMGrid(mx, my, n)
+        osys = SchurSystem(og)
+        Lm = og.assemble_L()
+        for _ in range(k):
+            f = rng.standard_normal(og.r)
+            g = rng.standard_normal(og.kp) if with_g else np.zeros(og.kp)
+            fs.append(f)
+            gs.append(g)
+            refs.append(methods.direct_solve(og, Lm, osys.u_L, og.rhs(f, g)))
+    return fs, gs, refs
+
+
+def packed(arrs):
+    return torch.as_tensor(np.concatenate(arrs), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("team", [1, 2, 4, 19, 152])
+@pytest.mark.parametrize("graph", [True, False], ids=["graph", "nograph"])
+def test_batch_matches_direct_solve(built, precision, team, graph):
+    grids = [Grid(mx, my, n) for (mx, my, n, _) in PROBLEMS]
+    for g in grids:
+        g.factor(tol=1e-12 if precision == 0 else 1e-11, precision=precision)
+    fs, gs, refs = make_inputs(PROBLEMS, 5)
+    b = Batch(grids, [k for *_, k in PROBLEMS], team_size=team, use_graph=graph)
+    assert b.info()["team_size"] == team
+    f, g = packed(fs), packed(gs)
+    u = torch.zeros_like(f)
+    for rep_round in range(2):  # the second call replays the graph
+        u.zero_()
+        reps = b.solve(f, u, g=g)
+        uh = u.cpu().numpy()
+        o = 0
+        for i, ref in enumerate(refs):
+            got = uh[o:o + ref.size]
+            o += ref.size
+            assert reps[i]["converged"] == 1
+            assert rel(got, ref) < (1e-10 if precision == 0 else 1e-9), (i, reps[i], rel(got, ref))
+    # same iteration counts as the single-grid solves (within one)
+    i = 0
+    for gr, (_, _, _, k) in zip(grids, PROBLEMS):
+        for _ in range(k):
+            fi = torch.as_tensor(fs[i], dtype=torch.float64, device="cuda")
+            gi = torch.as_tensor(gs[i], dtype=torch.float64, device="cuda")
+            ui = torch.zeros_like(fi)
+            r1 = gr.solve(fi, ui, g=gi)[0]
+            assert abs(r1["iterations"] - reps[i]["iterations"]) <= 1, (i, r1, reps[i])
+            i += 1
+    b.close()
+
+
+def test_batch_without_g_and_autotune(built):
+    probs = [(4, 5, 6, 2), (3, 3, 9, 1), (7, 2, 5, 3)]
+    grids = [Grid(mx, my, n) for (mx, my, n, _) in probs]
+    for gr in grids:
+        gr.factor(tol=1e-11, precision=1)
+    fs, _, refs = make_inputs(probs, 8, with_g=False)
+    b = Batch(grids, [k for *_, k in probs])
+    f = packed(fs)
+    u = torch.zeros_like(f)
+    chosen, ms = b.autotune(f, u, candidates=(2, 8, 38))
+    assert chosen in (2, 8, 38) and ms[chosen] > 0
+    u.zero_()
+    b.solve(f, u)
+    uh = u.cpu().numpy()
+    o = 0
+    for ref in refs:
+        assert rel(uh[o:o + ref.size], ref) < 1e-9
+        o += ref.size
+
+
+def test_batch_config4_sample(built):
+    """The first 12 problems of the seeded uneven config-4 batch (mixed
+    precision, 1e-10): each right-hand side against the single-grid solve of
+    the same handle."""
+    probs = inputs.uneven_batch(512, seed=7)[:12]
+    grids = [Grid(mx, my, n) for (mx, my, n, k) in probs]
+    factor_many(grids, tol=1e-10, precision=1)
+    fs = []
+    for gr, (mx, my, n, k) in zip(grids, probs):
+        x, y = gr.node_coords()
+        for j in range(k):
+            fs.append(inputs.fourier_rhs(x, y, seed=1000 + j)[0])
+    b = Batch(grids, [p[3] for p in probs])
+    f = packed(fs)
+    u = torch.zeros_like(f)
+    reps = b.solve(f, u)
+    assert all(r["converged"] == 1 for r in reps)
+    uh = u.cpu().numpy()
+    o, i = 0, 0
+    for gr, p in zip(grids, probs):
+        for j in range(p[3]):
+            fi = torch.as_tensor(fs[i], dtype=torch.float64, device="cuda")
+            ui = torch.zeros_like(fi)
+            gr.solve(fi, ui)
+            assert rel(uh[o:o + gr.r], ui.cpu().numpy()) < 1e-8
+            o += gr.r
+            i += 1

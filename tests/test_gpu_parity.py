@@ -240,3 +240,20 @@ def test_fp32_schur_apply(built):
     lg.apply_schur32(vp, out)
     got = og.from_padded(out.double().cpu().numpy())
     assert rel(got, osys.apply_S(v)) < 1e-5
+
+
+def test_handles_of_different_sizes_interleaved(built):
+    """Solves on a large-grid handle after a small grid was factored (the
+    kernels' shared-memory limits are per process, not per handle)."""
+    big = Grid(12, 10, 9)
+    big.factor(tol=1e-12)
+    small = Grid(2, 2, 4)
+    small.factor(tol=1e-12)
+    for lg in (big, small, big):
+        og = SMPMGrid(lg.mx, lg.my, lg.n)
+        osys = SchurSystem(og)
+        f = inputs.white_noise(og.r, 3)
+        u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+        lg.solve(dev(f), u)
+        ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, f)
+        assert rel(host(u), ud) < 1e-10
