@@ -28,6 +28,8 @@ EXPORTS = [
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
     "smpm_apply_deflation_noalloc", "smpm_apply_schur32", "schur_solve_adjoint",
     "smpm_factor_many", "smpm_batch_create", "smpm_batch_info", "smpm_batch_solve", "smpm_batch_autotune", "smpm_batch_destroy",
+    "smpm_batch_task_times", "smpm_batch_apply_schur", "smpm_batch_apply_schur32",
+    "smpm_batch_set_apply_kernel",
 ]
 
 
@@ -92,6 +94,10 @@ def lib():
                                       ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]
         L.smpm_batch_solve.argtypes = [P, P, P, P, ctypes.POINTER(SmpmReport), P]
         L.smpm_batch_autotune.argtypes = [P, P, P, P, P, P, I, P, ctypes.POINTER(I)]
+        L.smpm_batch_task_times.argtypes = [P, P, P, P]
+        L.smpm_batch_apply_schur.argtypes = [P, P, P, P]
+        L.smpm_batch_apply_schur32.argtypes = [P, P, P, P]
+        L.smpm_batch_set_apply_kernel.argtypes = [P, I]
         L.smpm_batch_destroy.argtypes = [P]
         L.smpm_batch_destroy.restype = None
         L.smpm_last_error.argtypes = []
@@ -320,6 +326,32 @@ class Batch:
         check(lib().smpm_batch_autotune(self.b, _ptr(f), _ptr(g), _ptr(u), _stream(stream), cands, len(candidates),
                                         ms, ctypes.byref(chosen)))
         return chosen.value, {c: ms[i] for i, c in enumerate(candidates)}
+
+    def v_len(self):
+        """Length of the packed slot vectors of apply_schur (sum of kp)."""
+        return sum(g.kp for g in self.grids)
+
+    def set_apply_kernel(self, kind):
+        """1: warp per element from global memory (default); 0: bulk-copy ring."""
+        check(lib().smpm_batch_set_apply_kernel(self.b, int(kind)))
+
+    def apply_schur(self, v, y, stream=None):
+        """y_p = S_p v_p for every problem (packed slot vectors, float64)."""
+        check(lib().smpm_batch_apply_schur(self.b, _ptr(v), _ptr(y), _stream(stream)))
+        return y
+
+    def apply_schur32(self, v, y, stream=None):
+        """As apply_schur with the FP32 factors (float32 vectors)."""
+        check(lib().smpm_batch_apply_schur32(self.b, _ptr(v), _ptr(y), _stream(stream)))
+        return y
+
+    def task_times(self):
+        """(team, start ms, end ms) of every right-hand side of the last solve."""
+        team = np.empty(self.ntasks, dtype=np.int32)
+        t0 = np.empty(self.ntasks)
+        t1 = np.empty(self.ntasks)
+        check(lib().smpm_batch_task_times(self.b, team.ctypes.data, t0.ctypes.data, t1.ctypes.data))
+        return team, t0, t1
 
     def close(self):
         if getattr(self, "b", None):

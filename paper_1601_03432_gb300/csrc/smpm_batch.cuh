@@ -35,7 +35,15 @@ struct TaskReport {
   int iterations, restarts, refinements, converged;
   double gmres_num, gmres_den;  // relres = num / den
   double res2, bsn2;            // ||b_S - S x_S||^2, ||b_S||^2
+  unsigned long long t_begin, t_end;  // global timer (ns) at the task's start and end on its team's first CTA
+  int team, pad;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 
 constexpr int kBatchHdr = (int)((sizeof(BatchTask) + 127) / 128 * 128);
 
@@ -64,6 +72,7 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
     }
     __syncthreads();
     const int rank = team_rank(T.P.ga);
+    const unsigned long long t_begin = global_ns();
     // per-solve control block of the problem (accumulators, flags, counts)
     if (rank == 0)
       for (int i = 256 / 4 + threadIdx.x; i < ctl_bytes / 4; i += blockDim.x) reinterpret_cast<int*>(T.ctl)[i] = 0;
@@ -110,6 +119,9 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
         r.gmres_num = nref > 0 ? sqrt(__ldcg(T.rn + nref - 1)) : 0.0;
         r.gmres_den = sqrt(__ldcg(acc8 + ACC_RGN));
       }
+      r.t_begin = t_begin;
+      r.t_end = global_ns();
+      r.team = team;
       rep[t] = r;
     }
   }

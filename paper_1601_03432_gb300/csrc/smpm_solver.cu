@@ -510,6 +510,255 @@ __global__ void __launch_bounds__(256, 2) k_schur_stream(DevGeo g, const S* __re
   }
 }
 
+
+// y_p = S_p v_p for every problem p of a batch in one launch: the elements of
+// all problems form one list; CTA c walks entries c, c+G, ... and streams
+// their T_e (M_p^2 s bytes each, contiguous, column-major) with bulk copies
+// into a shared-memory ring of `ring` bytes, as many elements in flight as
+// fit (at most kRingSlots), so small elements keep as many bytes in flight
+// as large ones.  Warp 0 owns the ring: its lanes load the metadata of the
+// next candidate elements in parallel (one table entry each), lane 0 places
+// them at the ring head in order (wrapping to the start when the tail is
+// free), and each lane issues its own element's copy and stages its
+// metadata in the slot, so the other warps never wait on the element table:
+// one element ahead they prefetch into registers the element's own slots and
+// the neighbour slots its rows feed.
+constexpr int kRingSlots = 16;
+
+template <typename S>
+struct ElemMeta {
+  const S* T;      // this element's T_e
+  long long off;   // slot offset of the problem in the packed vectors
+  int e, M, n, mx, my;
+  unsigned boff;   // byte offset of the element's copy in the ring (staged copies only)
+};
+
+template <typename S>
+__global__ void __launch_bounds__(256, 2) k_schur_stream_batch(const ElemMeta<S>* __restrict__ tab, long long nelem,
+                                                               const S* v, S* y, unsigned ring, int Mmax) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int G = gridDim.x, lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
+  unsigned char* buf = raw;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(raw + ring);
+  ElemMeta<S>* meta = reinterpret_cast<ElemMeta<S>*>(mbar + kRingSlots);
+  S* ve = reinterpret_cast<S*>(meta + kRingSlots);
+  S* z = ve + Mmax;
+  S* red = z + Mmax;
+  const long long nk = (nelem - blockIdx.x + G - 1) / G;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kRingSlots; ++b) mbar_init(mbar + b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // ring state, kept identical in every lane of warp 0
+  long long issued = 0;
+  unsigned head = 0, tail = 0;  // [tail, head) in ring order holds unconsumed copies
+  bool empty = true;
+  auto refill = [&](long long consumed) {
+    if (!w0) return;
+    long long lim = consumed + kRingSlots;
+    if (lim > nk) lim = nk;
+    const int cnt = (int)(lim - issued);
+    if (cnt <= 0) return;
+    ElemMeta<S> em{};
+    if (lane < cnt) em = tab[blockIdx.x + (issued + lane) * G];
+    int placed = 0;  // candidates 0 .. placed-1 get a place, in order
+    unsigned pos_mine = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const int Mj = __shfl_sync(0xffffffffu, em.M, j);
+      const unsigned need = (unsigned)(Mj * Mj * sizeof(S));
+      unsigned pos;
+      bool fits = true;
+      if (empty) {
+        pos = 0;
+        head = tail = 0;
+      } else if (head == tail) {
+        fits = false;
+      } else if (head > tail) {
+        if (head + need <= ring) pos = head;
+        else if (need <= tail) pos = 0;
+        else fits = false;
+      } else {
+        if (head + need <= tail) pos = head;
+        else fits = false;
+      }
+      if (!fits) break;
+      if (lane == j) pos_mine = pos;
+      head = pos + need;
+      empty = false;
+      ++placed;
+    }
+    if (lane < placed) {
+      const long long k = issued + lane;
+      const int b = (int)(k % kRingSlots);
+      em.boff = pos_mine;
+      meta[b] = em;
+      const unsigned need = (unsigned)(em.M * em.M * sizeof(S));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar + b)), "r"(need)
+                   : "memory");
+      bulk_g2s(buf + pos_mine, em.T + (size_t)em.e * em.M * em.M, need, mbar + b);
+    }
+    issued += placed;
+  };
+  // neighbour slot fed by row i of element (e, M, n) on an mx x my grid, or -1
+  auto nb_slot = [](const ElemMeta<S>& md, int i) -> long long {
+    const int F = i / md.n, t = i % md.n, ix = md.e % md.mx, iy = md.e / md.mx;
+    int e2;
+    switch (F) {
+      case 0: e2 = ix > 0 ? md.e - 1 : -1; break;
+      case 1: e2 = ix < md.mx - 1 ? md.e + 1 : -1; break;
+      case 2: e2 = iy > 0 ? md.e - md.mx : -1; break;
+      default: e2 = iy < md.my - 1 ? md.e + md.mx : -1; break;
+    }
+    return e2 >= 0 ? (long long)e2 * md.M + (F ^ 1) * md.n + t : -1;
+  };
+  refill(0);
+  __syncthreads();  // metadata of the first copies visible
+  __shared__ int ok;
+  __shared__ long long nissued;
+  bool failed = false;
+  long long waited = 0;
+  S pv_own = 0, pv_nb = 0;
+  bool have_pf = false;  // pv_own / pv_nb hold the current element's entries
+  if (nk > 0) {
+    const ElemMeta<S> md = meta[0];
+    if (threadIdx.x < md.M) {
+      pv_own = v[md.off + (long long)md.e * md.M + threadIdx.x];
+      const long long sl = nb_slot(md, threadIdx.x);
+      pv_nb = sl >= 0 ? v[md.off + sl] : S(0);
+    }
+    have_pf = true;
+  }
+  for (long long k = 0; k < nk; ++k) {
+    const int b = (int)(k % kRingSlots);
+    ElemMeta<S> md = meta[b];  // staged before the previous barrier; read before the slot is reused
+    const S cur_nb = pv_nb;
+    const bool cur_pf = have_pf;
+    if (threadIdx.x < md.M) ve[threadIdx.x] = have_pf ? pv_own : v[md.off + (long long)md.e * md.M + threadIdx.x];
+    if (threadIdx.x == 0) {
+      ok = (!failed && k < issued && mbar_wait(mbar + b, (unsigned)((k / kRingSlots) & 1))) ? 1 : 0;
+      nissued = issued;
+    }
+    __syncthreads();
+    have_pf = k + 1 < nissued;
+    if (have_pf) {  // prefetch the next element's vector entries (its metadata is staged)
+      const ElemMeta<S> m1 = meta[(k + 1) % kRingSlots];
+      if (threadIdx.x < m1.M) {
+        pv_own = v[m1.off + (long long)m1.e * m1.M + threadIdx.x];
+        const long long sl = nb_slot(m1, threadIdx.x);
+        pv_nb = sl >= 0 ? v[m1.off + sl] : S(0);
+      }
+    }
+    if (ok) {
+      waited = k + 1;
+      gemv_split(reinterpret_cast<const S*>(buf + md.boff), md.M, ve, z, md.M, md.M, red);
+      if (w0) {  // element k's copy is consumed: the tail moves on
+        if (k + 1 < issued) tail = meta[(k + 1) % kRingSlots].boff;
+        else empty = true;
+      }
+      refill(k + 1);
+    } else {
+      failed = true;
+      md = tab[blockIdx.x + k * G];  // no staged copy: metadata from the table
+    }
+    if (threadIdx.x < md.M) {
+      const int i = threadIdx.x;
+      const long long sl = nb_slot(md, i);
+      if (!ok) {
+        y[md.off + (sl >= 0 ? sl : (long long)md.e * md.M + i)] = (S)nan("");
+      } else if (sl >= 0) {
+        y[md.off + sl] = (cur_pf ? cur_nb : v[md.off + sl]) + z[i];
+      } else {
+        y[md.off + (long long)md.e * md.M + i] = ve[i];
+      }
+    }
+    __syncthreads();  // also publishes the metadata staged by refill
+  }
+  if (failed && threadIdx.x == 0)  // bounded wait for the copies still in flight
+    for (long long k = waited; k < issued; ++k) mbar_wait(mbar + (k % kRingSlots), (unsigned)((k / kRingSlots) & 1));
+}
+
+// Warp-per-element variant of the batched apply: warp w of the grid takes
+// elements w, w + W, ... (W warps in all).  Lane l owns rows l, l+32, l+64
+// (M <= 96) and walks the columns of T_e straight from global memory (each
+// column is M contiguous entries, read by the warp as coalesced 128-byte
+// lines), eight columns per step so that 24 independent loads per lane are in
+// flight; the element's own slots sit in a per-warp shared-memory row and
+// are broadcast column by column.  No CTA barrier, no copy engine: every warp
+// is an independent stream of loads, and the SM keeps many of them resident.
+template <typename S>
+__global__ void __launch_bounds__(256) k_schur_warp_batch(const ElemMeta<S>* __restrict__ tab, long long nelem,
+                                                          const S* v, S* y) {
+  __shared__ S xs[8][96];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  S* x = xs[wib];
+  for (long long k = (long long)blockIdx.x * (blockDim.x >> 5) + wib; k < nelem; k += W) {
+    const ElemMeta<S> md = tab[k];
+    const int M = md.M, n = md.n;
+    const S* vp = v + md.off;
+    const S* Te = md.T + (size_t)md.e * M * M;
+    for (int i = lane; i < M; i += 32) x[i] = vp[(long long)md.e * M + i];
+    __syncwarp();
+    const bool r1 = lane + 32 < M, r2 = lane + 64 < M;
+    S z0 = 0, z1 = 0, z2 = 0;
+    int c = 0;
+    for (; c + 8 <= M; c += 8) {
+      S a0[8], a1[8], a2[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const S* col = Te + (size_t)(c + u) * M;
+        a0[u] = __ldg(col + lane);
+        a1[u] = r1 ? __ldg(col + lane + 32) : S(0);
+        a2[u] = r2 ? __ldg(col + lane + 64) : S(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const S xc = x[c + u];
+        z0 += a0[u] * xc;
+        z1 += a1[u] * xc;
+        z2 += a2[u] * xc;
+      }
+    }
+    for (; c < M; ++c) {
+      const S* col = Te + (size_t)c * M;
+      const S xc = x[c];
+      z0 += __ldg(col + lane) * xc;
+      if (r1) z1 += __ldg(col + lane + 32) * xc;
+      if (r2) z2 += __ldg(col + lane + 64) * xc;
+    }
+    const int ix = md.e % md.mx, iy = md.e / md.mx;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int i = lane + 32 * j;
+      if (i >= M) break;
+      const S zi = j == 0 ? z0 : (j == 1 ? z1 : z2);
+      const int F = i / n, t = i % n;
+      int e2;
+      switch (F) {
+        case 0: e2 = ix > 0 ? md.e - 1 : -1; break;
+        case 1: e2 = ix < md.mx - 1 ? md.e + 1 : -1; break;
+        case 2: e2 = iy > 0 ? md.e - md.mx : -1; break;
+        default: e2 = iy < md.my - 1 ? md.e + md.mx : -1; break;
+      }
+      if (e2 >= 0) {
+        const long long sl = md.off + (long long)e2 * M + (F ^ 1) * n + t;
+        y[sl] = v[sl] + zi;
+      } else {
+        y[md.off + (long long)md.e * M + i] = x[i];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename S>
+inline size_t schur_stream_batch_smem(unsigned ring, int Mmax) {
+  return ring + kRingSlots * (8 + sizeof(ElemMeta<S>)) + (2 * (size_t)Mmax + 256) * sizeof(S) + 64;
+}
+
 inline size_t schur_stream_smem(int M, int stages, size_t elem) {
   return (size_t)stages * M * M * elem + stages * 8 + (2 * (size_t)M + 256) * elem + 64;
 }
@@ -1075,6 +1324,12 @@ struct smpm_batch_s {
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ein = nullptr, eout = nullptr;
   float last_ms = 0;
+  // batched apply y_p = S_p v_p: element list and per-problem tables
+  ElemMeta<double>* dtab64 = nullptr;
+  ElemMeta<float>* dtab32 = nullptr;  // null unless every handle has FP32 factors
+  long long nelem = 0, v_len = 0;
+  int Mmax = 0;
+  int apply_kernel = 1;  // 0: bulk-copy ring (k_schur_stream_batch), 1: warp per element (k_schur_warp_batch)
 };
 
 namespace {
@@ -1245,6 +1500,45 @@ smpm_status batch_layout(smpm_batch b, int T) {
   int per = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kGmresThreads, smem));
   if (per < 1) return fail(SMPM_ECUDA, "the batch kernel does not fit on an SM");
+  return SMPM_OK;
+}
+
+// y_p = S_p v_p for all problems: stages as in launch_schur_stream, sized
+// for the largest element matrix of the batch.
+template <typename S>
+smpm_status batch_apply(smpm_batch b, const ElemMeta<S>* tab, const S* v, S* y, cudaStream_t st) {
+  int dev = 0, sms = 0, optin = 0, per_sm_smem = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CU(cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  const int M = b->Mmax;
+  // two CTAs per SM when a ring of two of the largest element matrices fits
+  // in half the SM, else one CTA; the ring takes the rest of the CTA's share
+  // (less the CTA's reserved and static shared memory: 1 KB each CTA on this
+  // part, with margin)
+  const size_t fixed = schur_stream_batch_smem<S>(0, M);
+  const size_t one = (size_t)M * M * sizeof(S);
+  int cps = 2;
+  size_t share = (size_t)per_sm_smem / 2 - 2048;
+  if (share > (size_t)optin - 1024) share = (size_t)optin - 1024;
+  if (share < fixed + 2 * one) {
+    cps = 1;
+    share = (size_t)optin - 1024;
+  }
+  if (share < fixed + one) return fail(SMPM_EINVAL, "element matrix too large for the batched apply");
+  const unsigned ring = (unsigned)((share - fixed) / 16 * 16);
+  const size_t smem = schur_stream_batch_smem<S>(ring, M);
+  if (b->apply_kernel == 1 && M <= 96) {  // warp per element from global memory
+    const unsigned grid2 = (unsigned)sms * 8;  // 8 CTAs of 8 warps per SM
+    k_schur_warp_batch<S><<<grid2, 256, 0, st>>>(tab, b->nelem, v, y);
+    CU(cudaGetLastError());
+    return SMPM_OK;
+  }
+  CU(set_smem_limit(k_schur_stream_batch<S>, optin));
+  const unsigned grid = (unsigned)std::min<long long>((long long)sms * cps, b->nelem);
+  k_schur_stream_batch<S><<<grid, kElemThreads, smem, st>>>(tab, b->nelem, v, y, ring, M);
+  CU(cudaGetLastError());
   return SMPM_OK;
 }
 
@@ -1847,6 +2141,49 @@ smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs,
   }
   smpm_status st = batch_layout(b, T);
   if (st != SMPM_OK) return bad(st);
+  {
+    // per-element tables of the batched apply
+    std::vector<ElemMeta<double>> t64;
+    std::vector<ElemMeta<float>> t32;
+    bool all32 = true;
+    for (int p = 0; p < count; ++p) all32 = all32 && hs[p]->dT32 != nullptr;
+    long long off = 0;
+    for (int p = 0; p < count; ++p) {
+      smpm_handle h = hs[p];
+      for (long long e = 0; e < h->g.nel; ++e) {
+        ElemMeta<double> a{};
+        a.T = h->dT;
+        a.off = off;
+        a.e = (int)e;
+        a.M = h->g.M;
+        a.n = h->g.n;
+        a.mx = h->g.mx;
+        a.my = h->g.my;
+        t64.push_back(a);
+        if (all32) {
+          ElemMeta<float> c{};
+          c.T = h->dT32;
+          c.off = off;
+          c.e = (int)e;
+          c.M = h->g.M;
+          c.n = h->g.n;
+          c.mx = h->g.mx;
+          c.my = h->g.my;
+          t32.push_back(c);
+        }
+      }
+      off += h->g.kp;
+      b->Mmax = std::max(b->Mmax, h->g.M);
+    }
+    b->nelem = (long long)t64.size();
+    b->v_len = off;
+    if (cudaMalloc(&b->dtab64, t64.size() * sizeof(ElemMeta<double>)) ||
+        (all32 && cudaMalloc(&b->dtab32, t32.size() * sizeof(ElemMeta<float>))))
+      return bad(fail(SMPM_ENOMEM, "batch allocation failed"));
+    if (cudaMemcpy(b->dtab64, t64.data(), t64.size() * sizeof(ElemMeta<double>), cudaMemcpyHostToDevice) ||
+        (all32 && cudaMemcpy(b->dtab32, t32.data(), t32.size() * sizeof(ElemMeta<float>), cudaMemcpyHostToDevice)))
+      return bad(fail(SMPM_ECUDA, "batch table upload failed"));
+  }
   *out = b;
   return SMPM_OK;
 }
@@ -1946,10 +2283,44 @@ smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, 
   return SMPM_OK;
 }
 
+smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, double* end_ms) {
+  if (!b) return fail(SMPM_EINVAL, "null batch");
+  unsigned long long t0 = ~0ull;
+  for (long long i = 0; i < b->ntasks; ++i) t0 = std::min(t0, b->hrep[i].t_begin);
+  for (size_t p = 0; p < b->hs.size(); ++p)
+    for (int k = 0; k < b->nrhs[p]; ++k) {
+      const long long i = b->rhs_base[p] + k;
+      const TaskReport& t = b->hrep[b->task_of[i]];
+      if (team) team[i] = t.team;
+      if (begin_ms) begin_ms[i] = (double)(t.t_begin - t0) * 1e-6;
+      if (end_ms) end_ms[i] = (double)(t.t_end - t0) * 1e-6;
+    }
+  return SMPM_OK;
+}
+
+smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind) {
+  if (!b || kind < 0 || kind > 1) return fail(SMPM_EINVAL, "bad arguments");
+  b->apply_kernel = kind;
+  return SMPM_OK;
+}
+
+smpm_status smpm_batch_apply_schur(smpm_batch b, const double* v, double* y, void* stream) {
+  if (!b || !v || !y) return fail(SMPM_EINVAL, "bad arguments");
+  return batch_apply<double>(b, b->dtab64, v, y, as_stream(stream));
+}
+
+smpm_status smpm_batch_apply_schur32(smpm_batch b, const float* v, float* y, void* stream) {
+  if (!b || !v || !y) return fail(SMPM_EINVAL, "bad arguments");
+  if (!b->dtab32) return fail(SMPM_ESTATE, "not every handle of the batch was factored with precision 1");
+  return batch_apply<float>(b, b->dtab32, v, y, as_stream(stream));
+}
+
 void smpm_batch_destroy(smpm_batch b) {
   if (!b) return;
   if (b->bs) cudaStreamSynchronize(b->bs);
   batch_free_layout(b);
+  cudaFree(b->dtab64);
+  cudaFree(b->dtab32);
   cudaFree(b->dbars);
   cudaFree(b->derr);
   cudaFree(b->dio);

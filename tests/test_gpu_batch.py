@@ -133,3 +133,35 @@ def test_batch_config4_sample(built):
             assert rel(uh[o:o + gr.r], ui.cpu().numpy()) < 1e-8
             o += gr.r
             i += 1
+
+
+@pytest.mark.parametrize("kind", [0, 1], ids=["ring", "warp"])
+def test_batched_apply_matches_single_grid_apply(built, kind):
+    """y_p = S_p v_p for all problems in one launch, FP64 against the oracle's
+    S and FP32 against it to FP32 round-off; uneven n (different element
+    matrix sizes in one launch)."""
+    probs = [(3, 2, 5, 1), (4, 4, 9, 1), (2, 5, 12, 1), (6, 3, 7, 1)]
+    grids = [Grid(mx, my, n) for (mx, my, n, _) in probs]
+    factor_many(grids, precision=1)
+    b = Batch(grids, [1] * len(grids))
+    b.set_apply_kernel(kind)
+    rng = np.random.default_rng(17)
+    ogs = [SMPMGrid(mx, my, n) for (mx, my, n, _) in probs]
+    vs = [rng.standard_normal(og.k) for og in ogs]
+    vp = np.concatenate([og.to_padded(v) for og, v in zip(ogs, vs)])
+    assert vp.size == b.v_len()
+    v64 = torch.as_tensor(vp, dtype=torch.float64, device="cuda")
+    y64 = torch.full_like(v64, 3.0)
+    b.apply_schur(v64, y64)
+    v32 = v64.float()
+    y32 = torch.full_like(v32, 3.0)
+    b.apply_schur32(v32, y32)
+    h64, h32 = y64.cpu().numpy(), y32.double().cpu().numpy()
+    o = 0
+    for og, v in zip(ogs, vs):
+        ref = SchurSystem(og).apply_S(v)
+        assert rel(og.from_padded(h64[o:o + og.kp]), ref) < 1e-12
+        assert rel(og.from_padded(h32[o:o + og.kp]), ref) < 1e-5
+        pad = np.setdiff1d(np.arange(og.kp), og.padded_index)
+        assert np.all(h64[o + pad] == 0) and np.all(h32[o + pad] == 0)
+        o += og.kp
