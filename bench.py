@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch", type=int, default=512,
+                   help="grids of the uneven batch section (0 skips it; 512 is the full seeded batch)")
     p.add_argument("--profile", choices=["gmres", "apply"], default=None,
                    help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
@@ -328,6 +330,8 @@ def run_ours(args):
                    "median_of": 20, **apply,
                    "note": "FP64 is bound by the FP64 ALU (1.26 TFLOP/s) before HBM; FP32 is HBM-bound"}
 
+    batch = run_batch(args, stream, hbm_peak) if args.batch > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle runs in a fresh single-threaded process after the GPU timing
@@ -348,6 +352,7 @@ def run_ours(args):
                                      "post": round(post_ms, 4)}},
             "mixed": mixed,
             "schur_apply": schur_apply,
+            "batch": batch,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},
@@ -373,6 +378,108 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- batch
+def fourier_packed(grids, nrhs, torch, np, inputs):
+    """Packed right-hand sides of a batch: right-hand side j of every grid is
+    the seeded Fourier field of seed 1000 + j, evaluated on the device from
+    the seeded modes (input generation only)."""
+    total = sum(g.r * k for g, k in zip(grids, nrhs))
+    f = torch.empty(total, dtype=torch.float64, device="cuda")
+    o = 0
+    for g, k in zip(grids, nrhs):
+        x, y = g.node_coords()
+        xd = torch.as_tensor(x, device="cuda")
+        yd = torch.as_tensor(y, device="cuda")
+        for j in range(k):
+            acc = torch.zeros_like(xd)
+            for kx, ky, a in inputs.fourier_modes(1000 + j):
+                acc += a * torch.cos(kx * np.pi * xd) * torch.cos(ky * np.pi * yd)
+            f[o:o + g.r] = acc
+            o += g.r
+    return f
+
+
+def run_batch(args, stream, hbm_peak):
+    """The seeded uneven batch (512 grids, m_x, m_y ~ U{4..32}, n ~ U{8..24},
+    1-16 Fourier right-hand sides each): every right-hand side of every grid
+    in ONE persistent launch per solve (graph replay), mixed precision against
+    FP64 on the same factored handles, tol 1e-10; then the batched Schur apply
+    y_p = S_p v_p over all grids (inputs far larger than L2)."""
+    import numpy as np
+    import torch
+    from paper_1601_03432_gb300 import Batch, Grid, factor_many, inputs
+    probs = inputs.uneven_batch(512, seed=7)[:args.batch]
+    grids = [Grid(mx, my, n) for (mx, my, n, k) in probs]
+    nrhs = [p[3] for p in probs]
+    t0 = time.perf_counter()
+    factor_many(grids, tol=WORKLOAD["tol"], restart=WORKLOAD["restart"], precision=1)
+    factor_s = time.perf_counter() - t0
+    f = fourier_packed(grids, nrhs, torch, np, inputs)
+    out = {"workload": "%d grids (seed 7), %d right-hand sides, r_total = %d, tol 1e-10, restart 50"
+                       % (len(grids), sum(nrhs), int(f.numel())),
+           "factor_s": round(factor_s, 2)}
+    sols = {}
+    for name, prec, steps in (("mixed", 1, 2), ("fp64", 0, 1)):
+        b = Batch(grids, nrhs, precision=prec)
+        u = torch.zeros_like(f)
+        b.solve(f, u, allow_notconv=True)  # warm-up (captures the graph)
+        ms = []
+        for _ in range(steps):
+            reps = b.solve(f, u, allow_notconv=True)
+            ms.append(b.info()["last_ms"])
+        its = [r["iterations"] for r in reps]
+        out[name] = {"solves_per_s": len(reps) / (np.median(ms) / 1e3), "ms_per_batch": float(np.median(ms)),
+                     "team_size": b.info()["team_size"], "launches_per_batch": 1,
+                     "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+                     "refinements_max": int(max(r["refinements"] for r in reps)),
+                     "not_converged": int(sum(r["converged"] != 1 for r in reps)),
+                     "schur_relres_max": float(max(r["schur_relres"] for r in reps))}
+        sols[name] = u
+        b.close()
+    # mixed against FP64, per right-hand side
+    uo, um = sols["fp64"].cpu().numpy(), sols["mixed"].cpu().numpy()
+    worst, o = 0.0, 0
+    for g, k in zip(grids, nrhs):
+        for _ in range(k):
+            a, c = um[o:o + g.r], uo[o:o + g.r]
+            worst = max(worst, float(np.linalg.norm(a - c) / max(np.linalg.norm(c), 1e-300)))
+            o += g.r
+    out["mixed_vs_fp64_rel_l2_max"] = worst
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    # batched Schur apply over all grids, FP32 and FP64
+    b = Batch(grids, [1] * len(grids))
+    ent = sum(mx * my * 16 * n * n for (mx, my, n, k) in probs)
+    vlen = b.v_len()
+    apply = {}
+    for name, dt, fn, sz in (("fp32", torch.float32, b.apply_schur32, 4), ("fp64", torch.float64, b.apply_schur, 8)):
+        v = torch.randn(vlen, dtype=dt, device="cuda")
+        y = torch.empty_like(v)
+        for _ in range(3):
+            fn(v, y)
+        ts = []
+        for _ in range(10):
+            a_, c_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            fn(v, y)
+            c_.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a_.elapsed_time(c_))
+        msa = float(np.median(ts))
+        byts = (ent + 3 * vlen) * sz
+        apply[name] = {"ms_per_launch": msa, "bytes_per_launch": byts, "gbs": byts / (msa * 1e-3) / 1e9,
+                       "hbm_frac": byts / (msa * 1e-3) / 1e9 / hbm_peak}
+    apply["roofline"] = {"kernel": "k_schur_warp_batch<float> (batched y = S v, FP32)", "bound": "hbm",
+                         "achieved": apply["fp32"]["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                         "frac": apply["fp32"]["hbm_frac"], "traffic": None,
+                         "note": "operator %.2f GB FP32 / %.2f GB FP64, far above L2: no flush needed"
+                                 % (ent * 4 / 1e9, ent * 8 / 1e9)}
+    out["apply"] = apply
+    b.close()
+    for g in grids:
+        g.close()
+    return out
 
 
 # ------------------------------------------------------------ ncu cases

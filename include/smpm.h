@@ -240,9 +240,11 @@ smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double*
  * shared memory of one CTA at that team size), else all SMs as one team.
  * use_graph != 0 captures the batch's device work (argument copy, barrier
  * resets, the launch, the report copy) in a CUDA graph on the first solve
- * and replays it afterwards.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+ * and replays it afterwards.  precision: -1 each handle's own, 0 FP64 for all,
+ * 1 mixed precision for all (every handle factored with precision 1).
+ * Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
 smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs, int team_size, int use_graph,
-                              smpm_batch* out);
+                              int precision, smpm_batch* out);
 
 /* Sizes of the packed arrays (problem-major, right-hand-side-major within a
  * problem: problem p's k-th right-hand side starts at the sum over q < p of

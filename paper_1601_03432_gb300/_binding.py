@@ -89,7 +89,7 @@ def lib():
         L.smpm_destroy.argtypes = [P]
         L.smpm_destroy.restype = None
         L.smpm_factor_many.argtypes = [P, I, ctypes.POINTER(SmpmOpts), P]
-        L.smpm_batch_create.argtypes = [P, I, P, I, I, ctypes.POINTER(P)]
+        L.smpm_batch_create.argtypes = [P, I, P, I, I, I, ctypes.POINTER(P)]
         L.smpm_batch_info.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL),
                                       ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]
         L.smpm_batch_solve.argtypes = [P, P, P, P, ctypes.POINTER(SmpmReport), P]
@@ -285,14 +285,14 @@ class Batch:
     launch (smpm_batch_*).  f, g, u are packed problem-major: problem p's
     k-th right-hand side starts at offsets()[p] + k * r_p (g: with kp)."""
 
-    def __init__(self, grids, nrhs, team_size=0, use_graph=True):
+    def __init__(self, grids, nrhs, team_size=0, use_graph=True, precision=-1):
         self.grids = list(grids)
         self.nrhs = [int(k) for k in nrhs]
         hs = (ctypes.c_void_p * len(self.grids))(*[g.h for g in self.grids])
         ks = (ctypes.c_int * len(self.grids))(*self.nrhs)
         b = ctypes.c_void_p()
         check(lib().smpm_batch_create(hs, len(self.grids), ks, int(team_size), 1 if use_graph else 0,
-                                      ctypes.byref(b)))
+                                      int(precision), ctypes.byref(b)))
         self.b = b
         info = self.info()
         self.f_len, self.g_len, self.ntasks = info["f_len"], info["g_len"], info["ntasks"]

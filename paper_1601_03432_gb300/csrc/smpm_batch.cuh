@@ -14,7 +14,8 @@
 // Included inside the anonymous namespace of smpm_solver.cu.
 
 struct alignas(16) BatchTask {
-  PrePostArgs P;          // FP64 pre/post and FP64 GMRES arguments (all-global layout)
+  PrePostArgs P;          // FP64 pre/post arguments (all-global layout)
+  GmresArgs<double> a64;  // FP64 GMRES (its own layout: resident or streamed matrices, basis)
   GmresArgs<float> a32;   // FP32 inner GMRES (mixed precision)
   RefineArgs R;           // refinement step (mixed precision)
   int precision;          // 0 FP64, 1 FP32 inner + FP64 refinement
@@ -76,10 +77,16 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
     // per-solve control block of the problem (accumulators, flags, counts)
     if (rank == 0)
       for (int i = 256 / 4 + threadIdx.x; i < ctl_bytes / 4; i += blockDim.x) reinterpret_cast<int*>(T.ctl)[i] = 0;
-    if (!grid_sync(T.P.ga.bar, T.P.ga.err, epoch, T.P.ga.G)) return;
-    if (!pre_body(T.P, body, epoch)) return;
+    // on a failed wait the first failing task and body are recorded beside
+    // the error code (err[1] = task + 1, err[2] = body: 1 start, 2 pre,
+    // 3 GMRES, 4 refinement, 5 post)
+    auto failed = [&](int where) {
+      if (threadIdx.x == 0 && atomicCAS(T.P.ga.err + 1, 0, t + 1) == 0) T.P.ga.err[2] = where;
+    };
+    if (!grid_sync(T.P.ga.bar, T.P.ga.err, epoch, T.P.ga.G)) return failed(1);
+    if (!pre_body(T.P, body, epoch)) return failed(2);
     if (T.precision == 0) {
-      if (!gmres_body<double>(T.P.ga, body, epoch)) return;
+      if (!gmres_body<double>(T.a64, body, epoch)) return failed(3);
     } else {
       for (int ref = 0; ref < kMaxRefine; ++ref) {
         __syncthreads();
@@ -89,16 +96,21 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
           T.R.rn = T.rn + ref;
         }
         __syncthreads();
-        if (!gmres_body<float>(T.a32, body, epoch)) return;
+        if (!gmres_body<float>(T.a32, body, epoch)) return failed(3);
         const int st = refine_body(T.R, body, epoch);
-        if (st < 0) return;
+        if (st < 0) return failed(4);
         if (st == 1) break;
       }
       __syncthreads();
       if (threadIdx.x == 0) T.P.assembled = 1;
       __syncthreads();
     }
-    if (!post_body(T.P, body, epoch)) return;
+    if (!post_body(T.P, body, epoch)) return failed(5);
+    // every CTA of the team is past the task's last reads of the problem's
+    // control block (the zero-mean step reads its accumulator after the last
+    // barrier of post_body) before rank 0 reads the report and the next task
+    // clears the block
+    if (!grid_sync(T.P.ga.bar, T.P.ga.err, epoch, T.P.ga.G)) return failed(5);
     if (rank == 0 && threadIdx.x == 0) {
       const GState* gs = T.P.ga.gs;
       const double* acc8 = T.P.acc;

@@ -66,6 +66,7 @@ struct GmresArgs {
   int basis_smem;      // 1: basis slice resident in shared memory
   int stream_mats;     // 1: owned matrices streamed through two shared buffers (bulk copies)
   int buf_elems;       // elements of S per stream buffer (>= M*M + 4*n*n, multiple of 16 bytes)
+  int nbuf;            // stream buffers (2..kMaxStreamBufs): nbuf - 1 items in flight while one is used
   long long* trace;
   int trace_cap;
   const int* skip;  // when non-null and set on entry, the kernel returns at once
@@ -114,8 +115,12 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     long long spins = 0;
     while ((int)(ld_acquire(bar) - epoch) < 0) {
-      if (++spins > (1LL << 28) || ((spins & 4095) == 0 && *((volatile int*)err))) {
-        atomicExch(err, 1);
+      if (++spins > (1LL << 28)) {  // this CTA's own timeout: code 1 unless a failure is recorded
+        atomicCAS(err, 0, 1);
+        ok = 0;
+        break;
+      }
+      if ((spins & 4095) == 0 && *((volatile int*)err)) {  // another CTA failed: unwind
         ok = 0;
         break;
       }
@@ -144,7 +149,7 @@ struct Smem {
   double* cst;  // staged coarse vector c (d)
   S* V;     // (m+1) * ES when resident
   S* mats;  // resident matrices, or the two stream buffers
-  unsigned long long* mbar;  // two mbarriers of the matrix stream
+  unsigned long long* mbar;  // mbarriers of the matrix stream (kMaxStreamBufs)
 };
 
 template <typename S>
@@ -152,7 +157,7 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
   Smem<S> s;
   const int m = a.m, M = a.g.M;
   double* d = reinterpret_cast<double*>(raw);
-  s.mbar = reinterpret_cast<unsigned long long*>(d); d += 2;
+  s.mbar = reinterpret_cast<unsigned long long*>(d); d += kMaxStreamBufs;
   s.h1 = d; d += m + 3;
   s.h2 = d; d += m + 3;
   s.hs1 = d; d += m + 3;
@@ -187,12 +192,12 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
 
 template <typename S>
 inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
-                               long long d, int stream_elems = 0, bool w_global = false) {
-  size_t dbl = 2 + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
+                               long long d, int stream_elems = 0, bool w_global = false, int nbuf = 2) {
+  size_t dbl = kMaxStreamBufs + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
   size_t sel = 4 * (size_t)M + 256 + (w_global ? 0 : 2 * (size_t)(ES + 1));
   if (basis_smem) sel += (size_t)(m + 1) * ES;
   if (mats_smem) sel += (size_t)nown_b * (2 * (size_t)M * M + 4 * (size_t)n * n) + (size_t)nown_w * M * M;
-  sel += 2 * (size_t)stream_elems;
+  sel += (size_t)nbuf * stream_elems;
   return dbl * sizeof(double) + sel * sizeof(S) + 128;
 }
 
@@ -227,8 +232,10 @@ __device__ __forceinline__ S* basis(const GmresArgs<S>& a, const Smem<S>& s, int
 // ---- matrix stream: bulk copies into two shared-memory buffers ------------
 // Item sequence of a CTA (cyclic, the order in which the phases use them):
 // for each owned block k: [G_k | X_k], [T_e(k)]; then for each owned white
-// element: [T_e].  Item i lives in buffer i % 2; while it is used the next
-// item is in flight.  Thread 0 issues; waits are bounded.
+// element: [T_e].  Item i lives in buffer i % nbuf; while it is used the next
+// nbuf - 1 items are in flight.  Thread 0 issues; waits are bounded.  Every
+// thread orders its earlier shared-memory accesses before the copy engine's
+// writes (fence.proxy.async) ahead of the barrier that precedes an issue.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
@@ -267,7 +274,7 @@ __device__ void ms_issue(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& 
   const long long i = ms.issued++;
   if (threadIdx.x != 0) return;
   const int M = a.g.M, n = a.g.n, G = a.G, rank = team_rank(a);
-  const int it = (int)(i % ms.nitems), b = (int)(i & 1);
+  const int it = (int)(i % ms.nitems), b = (int)(i % a.nbuf);
   S* dst = s.mats + (size_t)b * a.buf_elems;
   unsigned long long* bar = s.mbar + b;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -294,34 +301,44 @@ __device__ void ms_issue(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& 
 template <typename S>
 __device__ const S* ms_acquire(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
   const long long i = ms.consumed;
-  const int b = (int)(i & 1);
-  const unsigned parity = (unsigned)((i >> 1) & 1);
+  const int b = (int)(i % a.nbuf);
+  const unsigned parity = (unsigned)((i / a.nbuf) & 1);
   __shared__ int ok;
   if (threadIdx.x == 0) ok = mbar_wait(s.mbar + b, parity) ? 1 : 0;
   __syncthreads();
   if (!ok) {
-    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, 2);  // code 2: a matrix copy did not complete
     return nullptr;
   }
   return s.mats + (size_t)b * a.buf_elems;
 }
 
-// done with the current item: the buffer is refilled with item consumed + 2
+// done with the current item: the buffer is refilled with item consumed + nbuf
 template <typename S>
 __device__ void ms_release(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   ++ms.consumed;
   ms_issue(a, s, ms);
 }
 
-// wait (bounded) for the copies still in flight before the kernel returns
+// wait (bounded) for the copies still in flight before the body returns,
+// then invalidate the stream's mbarriers: the shared memory they occupy is
+// reused by the next body of a batched solve.  (A copy that never completed
+// leaves its mbarrier as it is: the caller is unwinding with the error flag
+// set and reuses nothing.)
 template <typename S>
 __device__ void ms_drain(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>& ms) {
   if (!a.stream_mats) return;
+  bool all_done = true;
   while (ms.consumed < ms.issued) {
     const long long i = ms.consumed++;
-    if (threadIdx.x == 0) mbar_wait(s.mbar + (i & 1), (unsigned)((i >> 1) & 1));
+    if (threadIdx.x == 0 && !mbar_wait(s.mbar + (i % a.nbuf), (unsigned)((i / a.nbuf) & 1))) all_done = false;
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && all_done)
+    for (int b = 0; b < a.nbuf; ++b)
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(s.mbar + b)) : "memory");
   __syncthreads();
 }
 
@@ -497,28 +514,45 @@ __device__ void owned_dots(const GmresArgs<S>& a, const Smem<S>& s, const S* vec
     double sum = 0;
     if (l < nl) {
       const S* vl = (l == nl - 1) ? vec : basis(a, s, l);
+      // eight entries per step, loaded before they are used: with the basis
+      // in global memory each lane keeps eight independent loads in flight
       if constexpr (sizeof(S) == 4) {
         // FP32 products summed in FP32 over chunks of 16, chunks added in FP64
         int i = lane, cnt = 0;
         float f0 = 0.f;
-        for (; i < E; i += P) {
-          f0 = fmaf((float)vl[i], (float)vec[i], f0);
-          if (++cnt == 16) {
+        for (; i + 7 * P < E; i += 8 * P) {
+          float bv[8], wv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            bv[u] = (float)vl[i + u * P];
+            wv[u] = (float)vec[i + u * P];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) f0 = fmaf(bv[u], wv[u], f0);
+          cnt += 8;
+          if (cnt == 16) {
             sum += (double)f0;
             f0 = 0.f;
             cnt = 0;
           }
         }
+        for (; i < E; i += P) f0 = fmaf((float)vl[i], (float)vec[i], f0);
         sum += (double)f0;
       } else {
-        double s0 = 0, s1 = 0;
+        double acc[4] = {0, 0, 0, 0};
         int i = lane;
-        for (; i + P < E; i += 2 * P) {
-          s0 += (double)vl[i] * (double)vec[i];
-          s1 += (double)vl[i + P] * (double)vec[i + P];
+        for (; i + 7 * P < E; i += 8 * P) {
+          double bv[8], wv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            bv[u] = (double)vl[i + u * P];
+            wv[u] = (double)vec[i + u * P];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u & 3] += bv[u] * wv[u];
         }
-        if (i < E) s0 += (double)vl[i] * (double)vec[i];
-        sum = s0 + s1;
+        for (; i < E; i += P) acc[0] += (double)vl[i] * (double)vec[i];
+        sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
       }
     }
     for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
@@ -647,14 +681,16 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
   msd.issued = msd.consumed = 0;
   MatStream<S>* ms = a.stream_mats ? &msd : nullptr;
   if (ms) {
+    // shared memory written by an earlier body (batched solves) before the
+    // copy engine writes it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
     if (threadIdx.x == 0) {
-      mbar_init(s.mbar);
-      mbar_init(s.mbar + 1);
+      for (int b = 0; b < a.nbuf; ++b) mbar_init(s.mbar + b);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    ms_issue(a, s, msd);
-    ms_issue(a, s, msd);
+    for (int b = 0; b < a.nbuf; ++b) ms_issue(a, s, msd);
   }
 #define GM_FAIL()           \
   do {                      \

@@ -44,6 +44,7 @@ constexpr int kGmresThreads = 256;    // threads per CTA of the persistent GMRES
 // err, done, nref | 8 accumulators | 32 refinement residual norms
 constexpr size_t kCtlBytes = 720;  // + 32 inner iteration counts
 constexpr int kMaxRefine = 8;        // FP64 refinement steps of the mixed-precision path
+constexpr int kMaxStreamBufs = 4;    // shared-memory buffers of the GMRES kernel's matrix stream
 constexpr double kInnerTol = 1e-4;   // relative tolerance of each FP32 inner GMRES
 
 struct GState {
@@ -754,6 +755,113 @@ __global__ void __launch_bounds__(256) k_schur_warp_batch(const ElemMeta<S>* __r
   }
 }
 
+// Register-streamed apply with K = 2 or 4 warps per element, for element
+// lists too short to give every SM enough independent warps at one warp per
+// element (a single grid): warp w of the group takes columns
+// [w ceil(M/K), (w+1) ceil(M/K)); lane l owns rows l, l+32, l+64 (M <= 96)
+// and reads its columns of T_e straight from global memory, eight columns
+// per step (24 independent loads per lane in flight).  The group's partial
+// products meet in shared memory; the K warps of an element sync on a named
+// barrier of their own, so element groups never wait on each other.  A CTA of
+// 8 warps takes 8/K elements per step (grid-stride).
+template <int K>
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(32 * K) : "memory");
+}
+
+template <typename S, int K>
+__global__ void __launch_bounds__(256) k_schur_warpk(const ElemMeta<S>* __restrict__ tab, long long nelem, const S* v,
+                                                     S* y) {
+  constexpr int EPC = 8 / K;  // elements per CTA step
+  __shared__ S xs[EPC][96];
+  __shared__ S zs[EPC][K][96];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, grp = wib / K, part = wib % K;
+  for (long long base = (long long)blockIdx.x * EPC; base < nelem; base += (long long)gridDim.x * EPC) {
+    const long long k = base + grp;
+    const bool live = k < nelem;
+    ElemMeta<S> md{};
+    if (live) md = tab[k];
+    const int M = md.M;
+    S* x = xs[grp];
+    if (live)
+      for (int i = part * 32 + lane; i < M; i += 32 * K) x[i] = v[md.off + (long long)md.e * M + i];
+    group_sync<K>(grp);
+    if (live) {
+      const S* Te = md.T + (size_t)md.e * M * M;
+      const int per = (M + K - 1) / K, c0 = part * per, c1 = min(M, c0 + per);
+      const bool r1 = lane + 32 < M, r2 = lane + 64 < M;
+      S z0 = 0, z1 = 0, z2 = 0;
+      int c = c0;
+      for (; c + 8 <= c1; c += 8) {
+        S a0[8], a1[8], a2[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const S* col = Te + (size_t)(c + u) * M;
+          a0[u] = __ldg(col + lane);
+          a1[u] = r1 ? __ldg(col + lane + 32) : S(0);
+          a2[u] = r2 ? __ldg(col + lane + 64) : S(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const S xc = x[c + u];
+          z0 += a0[u] * xc;
+          z1 += a1[u] * xc;
+          z2 += a2[u] * xc;
+        }
+      }
+      for (; c < c1; ++c) {
+        const S* col = Te + (size_t)c * M;
+        const S xc = x[c];
+        z0 += __ldg(col + lane) * xc;
+        if (r1) z1 += __ldg(col + lane + 32) * xc;
+        if (r2) z2 += __ldg(col + lane + 64) * xc;
+      }
+      zs[grp][part][lane] = z0;
+      if (r1) zs[grp][part][lane + 32] = z1;
+      if (r2) zs[grp][part][lane + 64] = z2;
+    }
+    group_sync<K>(grp);
+    if (live) {
+      const int n = md.n, ix = md.e % md.mx, iy = md.e / md.mx;
+      for (int i = part * 32 + lane; i < M; i += 32 * K) {
+        S zi = zs[grp][0][i];
+#pragma unroll
+        for (int q = 1; q < K; ++q) zi += zs[grp][q][i];
+        const int F = i / n, t = i % n;
+        int e2;
+        switch (F) {
+          case 0: e2 = ix > 0 ? md.e - 1 : -1; break;
+          case 1: e2 = ix < md.mx - 1 ? md.e + 1 : -1; break;
+          case 2: e2 = iy > 0 ? md.e - md.mx : -1; break;
+          default: e2 = iy < md.my - 1 ? md.e + md.mx : -1; break;
+        }
+        if (e2 >= 0) {
+          const long long sl = md.off + (long long)e2 * M + (F ^ 1) * n + t;
+          y[sl] = v[sl] + zi;
+        } else {
+          y[md.off + (long long)md.e * M + i] = x[i];
+        }
+      }
+    }
+    group_sync<K>(grp);
+  }
+}
+
+// Register-streamed apply over an element list (M <= 96): one warp per
+// element when the list gives every SM enough warps, else 2 or 4.
+template <typename S>
+cudaError_t launch_schur_warp(const ElemMeta<S>* tab, long long nelem, const S* v, S* y, int sms, cudaStream_t st) {
+  const long long want = (long long)sms * 48;  // resident warps per SM worth keeping busy
+  if (nelem >= want) {
+    k_schur_warp_batch<S><<<(unsigned)sms * 8, 256, 0, st>>>(tab, nelem, v, y);
+  } else if (2 * nelem >= want) {
+    k_schur_warpk<S, 2><<<(unsigned)((nelem + 3) / 4), 256, 0, st>>>(tab, nelem, v, y);
+  } else {
+    k_schur_warpk<S, 4><<<(unsigned)((nelem + 1) / 2), 256, 0, st>>>(tab, nelem, v, y);
+  }
+  return cudaGetLastError();
+}
+
 template <typename S>
 inline size_t schur_stream_batch_smem(unsigned ring, int Mmax) {
   return ring + kRingSlots * (8 + sizeof(ElemMeta<S>)) + (2 * (size_t)Mmax + 256) * sizeof(S) + 64;
@@ -790,7 +898,8 @@ struct smpm_handle_s {
   int* werr = nullptr;
   GState* wgs = nullptr;
   struct {
-    int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0, stream_mats = 0, buf_elems = 0;
+    int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0, stream_mats = 0, buf_elems = 0,
+        nbuf = 2;
     size_t smem = 0, smem_pp = 0;
   } gm;  // launch shape of the persistent GMRES kernel
   double* wvown = nullptr;
@@ -801,12 +910,15 @@ struct smpm_handle_s {
   double *wr = nullptr, *wcr = nullptr, *wrn = nullptr;
   int *wdone = nullptr, *wnref = nullptr;
   struct {
-    int basis_smem = 0, mats_smem = 0, stream_mats = 0, buf_elems = 0;
+    int basis_smem = 0, mats_smem = 0, stream_mats = 0, buf_elems = 0, nbuf = 2;
     size_t smem = 0, smem_ref = 0;
   } gm32;
   double *wacc8 = nullptr, *wxs = nullptr, *dZtuS = nullptr;
   // transposed system for the adjoint solve (SMPM_FLAG_ADJOINT)
   double *dTa = nullptr, *dRsa = nullptr, *dGa = nullptr, *dXa = nullptr, *dHa = nullptr;
+  // element tables of the register-streamed apply (k_schur_warp_batch / k_schur_warpk)
+  ElemMeta<double>* dtab64 = nullptr;
+  ElemMeta<float>* dtab32 = nullptr;
   double *dfdxT = nullptr, *dfdyT = nullptr, *duSa = nullptr, *dZtuSa = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the GMRES kernel of each solve
   cudaEvent_t evp = nullptr, evq = nullptr;  // start of k_pre, end of k_post
@@ -925,6 +1037,14 @@ smpm_status launch_schur_stream(smpm_handle h, const S* T, const S* v, S* y, cud
 }
 
 smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
+  if (h->g.M <= 96 && h->dtab64) {  // register-streamed from global memory
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(launch_schur_warp<double>(h->dtab64, h->g.nel, v, y, sms, st));
+    ++h->launches;
+    return SMPM_OK;
+  }
   return launch_schur_stream<double>(h, h->dT, v, y, st);
 }
 
@@ -995,21 +1115,22 @@ smpm_status print_trace(smpm_handle h, cudaStream_t st) {
 // buffers) + basis; streamed matrices with the basis in global memory; all
 // global.
 struct Layout {
-  int basis_smem, mats_smem, stream_mats, buf_elems;
+  int basis_smem, mats_smem, stream_mats, buf_elems, nbuf;
   size_t smem;
 };
 
 template <typename S>
 Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, int precond, bool no_smem,
-                     bool force_stream, int smem_optin) {
+                     bool force_stream, int smem_optin, bool w_global = false) {
   Layout L;
   L.buf_elems = g.M * g.M + 4 * g.n * g.n;
   L.basis_smem = no_smem ? 0 : 1;
   L.mats_smem = (no_smem || force_stream) ? 0 : 1;
   L.stream_mats = 0;
+  L.nbuf = 2;
   auto need = [&]() {
     return gmres_smem_bytes<S>(m, g.M, g.n, ES, nown_b, nown_w, L.basis_smem, L.mats_smem, g.d,
-                               L.stream_mats ? L.buf_elems : 0);
+                               L.stream_mats ? L.buf_elems : 0, w_global, L.nbuf);
   };
   if (need() > (size_t)smem_optin) L.mats_smem = 0;
   if (!L.mats_smem && !no_smem && precond > 0) {
@@ -1018,6 +1139,14 @@ Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, i
     if (need() > (size_t)smem_optin) L.stream_mats = 0;
   }
   if (need() > (size_t)smem_optin) L.basis_smem = 0;
+  if (L.stream_mats)  // deepest stream that fits: nbuf - 1 copies in flight during each item
+    while (L.nbuf < kMaxStreamBufs) {
+      ++L.nbuf;
+      if (need() > (size_t)smem_optin) {
+        --L.nbuf;
+        break;
+      }
+    }
   L.smem = need();
   return L;
 }
@@ -1039,7 +1168,7 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   a.precond = h->opts.precond; a.m = h->opts.restart; a.maxit = h->opts.maxit; a.tol = tol;
   a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
   a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
-  a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems;
+  a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems; a.nbuf = h->gm.nbuf;
   a.trace = h->wtrace;
   a.trace_cap = h->wtrace ? kTraceCap : 0;
   a.skip = nullptr;
@@ -1062,7 +1191,7 @@ GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
   a.precond = h->opts.precond; a.m = h->opts.restart; a.maxit = h->opts.restart; a.tol = tol;
   a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
   a.mats_smem = h->gm32.mats_smem; a.basis_smem = h->gm32.basis_smem;
-  a.stream_mats = h->gm32.stream_mats; a.buf_elems = h->gm32.buf_elems;
+  a.stream_mats = h->gm32.stream_mats; a.buf_elems = h->gm32.buf_elems; a.nbuf = h->gm32.nbuf;
   a.trace = nullptr;
   a.trace_cap = 0;
   a.skip = h->wdone;
@@ -1330,6 +1459,7 @@ struct smpm_batch_s {
   long long nelem = 0, v_len = 0;
   int Mmax = 0;
   int apply_kernel = 1;  // 0: bulk-copy ring (k_schur_stream_batch), 1: warp per element (k_schur_warp_batch)
+  int precision = -1;    // -1: each handle's own, 0: FP64, 1: mixed
 };
 
 namespace {
@@ -1389,6 +1519,7 @@ smpm_status batch_layout(smpm_batch b, int T) {
   struct PL {
     int nown_b, nown_w, ES;
     bool wg;
+    Layout lay;  // layout of the GMRES body (FP64, or the FP32 inner solve)
     double* vown64;
     float* vown32;
     double* wscr64;
@@ -1406,28 +1537,31 @@ smpm_status batch_layout(smpm_batch b, int T) {
     L.nown_w = (nw + T - 1) / T;
     L.ES = 2 * g.M * L.nown_b;
     if (L.ES % 2 == 0) L.ES += 1;
-    const bool mixed = h->opts.precision == 1;
-    auto need = [&](bool wg) {
+    const bool mixed = (b->precision < 0 ? h->opts.precision : b->precision) == 1;
+    // the all-global needs of pre/post and refinement, then the richest
+    // GMRES layout that fits beside the argument header (resident or
+    // streamed operator matrices, resident basis)
+    const int budget = optin - kBatchHdr - 1024;
+    auto need_fixed = [&](bool wg) {
       size_t a = prepost_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg);
-      if (mixed) {
-        a = std::max(a, gmres_smem_bytes<float>(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, 0, 0, g.d, 0, wg));
-        a = std::max(a, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg));
-      } else {
-        a = std::max(a, gmres_smem_bytes<double>(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, 0, 0, g.d, 0, wg));
-      }
-      return a + kBatchHdr;
+      if (mixed) a = std::max(a, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg));
+      return a;
     };
-    L.wg = need(false) > (size_t)optin;
-    const size_t nd = need(L.wg);
-    if (nd > (size_t)optin) return fail(SMPM_EINVAL, "a problem of the batch is too large for teams of this size");
+    L.wg = need_fixed(false) > (size_t)budget;
+    const int precond = h->opts.precond;
+    L.lay = mixed ? choose_layout<float>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg)
+                  : choose_layout<double>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg);
+    const size_t nd = kBatchHdr + std::max(need_fixed(L.wg), L.lay.smem);
+    if (nd > (size_t)optin - 1024)
+      return fail(SMPM_EINVAL, "a problem of the batch is too large for teams of this size");
     smem = std::max(smem, nd);
     L.vown64 = nullptr;
     L.vown32 = nullptr;
     L.wscr64 = nullptr;
     L.wscr32 = nullptr;
     const size_t vn = (size_t)T * (m + 1) * L.ES;
-    if (!mixed && (st = balloc(b, &L.vown64, vn))) return st;
-    if (mixed && (st = balloc(b, &L.vown32, vn))) return st;
+    if (!L.lay.basis_smem && !mixed && (st = balloc(b, &L.vown64, vn))) return st;
+    if (!L.lay.basis_smem && mixed && (st = balloc(b, &L.vown32, vn))) return st;
     if (L.wg) {
       if ((st = balloc(b, &L.wscr64, (size_t)T * 2 * (L.ES + 1)))) return st;
       if (mixed && (st = balloc(b, &L.wscr32, (size_t)T * 2 * (L.ES + 1)))) return st;
@@ -1442,7 +1576,7 @@ smpm_status batch_layout(smpm_batch b, int T) {
     for (int p : plist[t]) {
       smpm_handle h = b->hs[p];
       const PL& L = pl[p];
-      const bool mixed = h->opts.precision == 1;
+      const bool mixed = (b->precision < 0 ? h->opts.precision : b->precision) == 1;
       const double tol = h->opts.tol;
       for (int k = 0; k < b->nrhs[p]; ++k) {
         BatchTask bt{};
@@ -1464,14 +1598,28 @@ smpm_status batch_layout(smpm_batch b, int T) {
           a.its_out = nullptr;
         };
         team_fields(bt.P.ga);
-        bt.P.ga.vown = L.vown64;
+        bt.P.ga.vown = nullptr;
         bt.P.ga.wscr = L.wscr64;
+        auto layout_fields = [&](auto& a) {
+          a.mats_smem = L.lay.mats_smem;
+          a.basis_smem = L.lay.basis_smem;
+          a.stream_mats = L.lay.stream_mats;
+          a.buf_elems = L.lay.buf_elems;
+          a.nbuf = L.lay.nbuf;
+        };
         if (mixed) {
           bt.a32 = gmres_args32(h, kInnerTol);
           team_fields(bt.a32);
           bt.a32.vown = L.vown32;
           bt.a32.wscr = L.wscr32;
-          bt.R = refine_args(h, bt.a32, tol);
+          bt.R = refine_args(h, bt.a32, tol);  // all-global (refine_args clears the layout)
+          layout_fields(bt.a32);
+        } else {
+          bt.a64 = gmres_args(h, tol);
+          team_fields(bt.a64);
+          layout_fields(bt.a64);
+          bt.a64.vown = L.vown64;
+          bt.a64.wscr = L.wscr64;
         }
         bt.precision = mixed ? 1 : 0;
         bt.has_g = 1;
@@ -1529,10 +1677,8 @@ smpm_status batch_apply(smpm_batch b, const ElemMeta<S>* tab, const S* v, S* y, 
   if (share < fixed + one) return fail(SMPM_EINVAL, "element matrix too large for the batched apply");
   const unsigned ring = (unsigned)((share - fixed) / 16 * 16);
   const size_t smem = schur_stream_batch_smem<S>(ring, M);
-  if (b->apply_kernel == 1 && M <= 96) {  // warp per element from global memory
-    const unsigned grid2 = (unsigned)sms * 8;  // 8 CTAs of 8 warps per SM
-    k_schur_warp_batch<S><<<grid2, 256, 0, st>>>(tab, b->nelem, v, y);
-    CU(cudaGetLastError());
+  if (b->apply_kernel == 1 && M <= 96) {  // register-streamed, warps per element
+    CU(launch_schur_warp<S>(tab, b->nelem, v, y, sms, st));
     return SMPM_OK;
   }
   CU(set_smem_limit(k_schur_stream_batch<S>, optin));
@@ -1546,7 +1692,7 @@ smpm_status batch_apply(smpm_batch b, const ElemMeta<S>* tab, const S* v, S* y, 
 smpm_status batch_enqueue(smpm_batch b, cudaStream_t st) {
   CU(cudaMemcpyAsync(b->dio, b->hio, sizeof(BatchIO), cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(b->dbars, 0, sizeof(unsigned) * b->grid, st));
-  CU(cudaMemsetAsync(b->derr, 0, sizeof(int), st));
+  CU(cudaMemsetAsync(b->derr, 0, 4 * sizeof(int), st));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kGmresThreads);
@@ -1561,7 +1707,7 @@ smpm_status batch_enqueue(smpm_batch b, cudaStream_t st) {
   CU(cudaLaunchKernelEx(&cfg, k_batch, (const BatchTask*)b->dtasks, (const int*)b->dbegin, (const int*)b->dteam,
                         (const BatchIO*)b->dio, b->drep, ctl));
   CU(cudaMemcpyAsync(b->hrep, b->drep, sizeof(TaskReport) * b->ntasks, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(b->herr, b->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(b->herr, b->derr, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   return SMPM_OK;
 }
 
@@ -1795,6 +1941,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       gm.mats_smem = L.mats_smem;
       gm.stream_mats = L.stream_mats;
       gm.buf_elems = L.buf_elems;
+      gm.nbuf = L.nbuf;
       gm.smem = L.smem;
     }
     CU(set_smem_limit(k_gmres<double>, smem_optin));
@@ -1811,6 +1958,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       g32.mats_smem = L.mats_smem;
       g32.stream_mats = L.stream_mats;
       g32.buf_elems = L.buf_elems;
+      g32.nbuf = L.nbuf;
       g32.smem = L.smem;
       CU(set_smem_limit(k_gmres<float>, smem_optin));
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<float>, kGmresThreads, g32.smem));
@@ -1847,6 +1995,32 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
         for (int t = 0; t < g.n; ++t) ztus[j] += h->f.uS[e * g.M + F * g.n + t];
       }
     if ((s = upload(h, &h->dZtuS, ztus, st))) return s;
+    {
+      std::vector<ElemMeta<double>> t64(g.nel);
+      std::vector<ElemMeta<float>> t32(h->dT32 ? g.nel : 0);
+      for (long long e = 0; e < g.nel; ++e) {
+        ElemMeta<double> a{};
+        a.T = h->dT;
+        a.e = (int)e;
+        a.M = g.M;
+        a.n = g.n;
+        a.mx = g.mx;
+        a.my = g.my;
+        t64[e] = a;
+        if (h->dT32) {
+          ElemMeta<float> c{};
+          c.T = h->dT32;
+          c.e = (int)e;
+          c.M = g.M;
+          c.n = g.n;
+          c.mx = g.mx;
+          c.my = g.my;
+          t32[e] = c;
+        }
+      }
+      if ((s = upload(h, &h->dtab64, t64, st))) return s;
+      if (h->dT32 && (s = upload(h, &h->dtab32, t32, st))) return s;
+    }
     if (h->f.has_adjoint) {
       // T~_e = T_e^T: its column-major device copy is T_e row-major
       std::vector<double> Gca = transpose_blocks(h->f.Ga, g.M, h->f.black.size()),
@@ -1953,6 +2127,14 @@ smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* st
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
+  if (h->g.M <= 96 && h->dtab32) {
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(launch_schur_warp<float>(h->dtab32, h->g.nel, v, y, sms, as_stream(stream)));
+    ++h->launches;
+    return SMPM_OK;
+  }
   return launch_schur_stream<float>(h, h->dT32, v, y, as_stream(stream));
 }
 
@@ -2089,18 +2271,22 @@ void smpm_destroy(smpm_handle h) {
 
 
 smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs, int team_size, int use_graph,
-                              smpm_batch* out) {
-  if (!hs || count < 1 || !nrhs || !out) return fail(SMPM_EINVAL, "bad arguments");
+                              int precision, smpm_batch* out) {
+  if (!hs || count < 1 || !nrhs || !out || precision < -1 || precision > 1)
+    return fail(SMPM_EINVAL, "bad arguments");
   *out = nullptr;
   for (int p = 0; p < count; ++p) {
     if (!hs[p] || nrhs[p] < 1) return fail(SMPM_EINVAL, "null handle or nrhs < 1 in the batch");
     if (!hs[p]->factored) return fail(SMPM_ESTATE, "a handle of the batch has not been factored");
+    if (precision == 1 && !hs[p]->dT32)
+      return fail(SMPM_ESTATE, "mixed precision needs every handle factored with precision 1");
     for (int q = 0; q < p; ++q)
       if (hs[q] == hs[p]) return fail(SMPM_EINVAL, "a handle appears twice in the batch");
   }
   smpm_batch b = new smpm_batch_s();
   b->hs.assign(hs, hs + count);
   b->nrhs.assign(nrhs, nrhs + count);
+  b->precision = precision;
   b->use_graph = use_graph ? 1 : 0;
   long long fo = 0, go = 0, rb = 0;
   for (int p = 0; p < count; ++p) {
@@ -2121,10 +2307,10 @@ smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs,
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
     return bad(fail(SMPM_ECUDA, "no CUDA device"));
-  if (cudaMalloc(&b->dbars, sizeof(unsigned) * sms) || cudaMalloc(&b->derr, sizeof(int)) ||
+  if (cudaMalloc(&b->dbars, sizeof(unsigned) * sms) || cudaMalloc(&b->derr, 4 * sizeof(int)) ||
       cudaMalloc(&b->dio, sizeof(BatchIO)) || cudaMalloc(&b->drep, sizeof(TaskReport) * b->ntasks) ||
       cudaMallocHost(&b->hio, sizeof(BatchIO)) || cudaMallocHost(&b->hrep, sizeof(TaskReport) * b->ntasks) ||
-      cudaMallocHost(&b->herr, sizeof(int)) || cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) ||
+      cudaMallocHost(&b->herr, 4 * sizeof(int)) || cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) ||
       cudaEventCreate(&b->ein) || cudaEventCreate(&b->eout))
     return bad(fail(SMPM_ENOMEM, "batch allocation failed"));
   int T = team_size;
@@ -2234,7 +2420,17 @@ smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, dou
   CU(cudaStreamWaitEvent(us, b->eout, 0));
   CU(cudaStreamSynchronize(b->bs));
   CU(cudaEventElapsedTime(&b->last_ms, b->ein, b->eout));
-  if (*b->herr) return fail(SMPM_ETIMEOUT, "a team barrier of the batch kernel timed out");
+  if (b->herr[0]) {  // code, first failing task + 1, body (see k_batch)
+    std::string where = "unknown";
+    const long long t = (long long)b->herr[1] - 1;
+    for (size_t p = 0; p < b->hs.size() && t >= 0; ++p)
+      for (int k = 0; k < b->nrhs[p]; ++k)
+        if (b->task_of[b->rhs_base[p] + k] == t) where = "problem " + std::to_string(p) + " rhs " + std::to_string(k);
+    static const char* what[] = {"?", "start barrier", "pre", "GMRES", "refinement", "post"};
+    const int w = (b->herr[2] >= 0 && b->herr[2] <= 5) ? b->herr[2] : 0;
+    return fail(SMPM_ETIMEOUT, std::string(b->herr[0] == 2 ? "a matrix copy wait" : "a team barrier") +
+                                   " of the batch kernel timed out (first failure: " + where + ", " + what[w] + ")");
+  }
   smpm_status worst = SMPM_OK;
   for (size_t p = 0; p < b->hs.size(); ++p)
     for (int k = 0; k < b->nrhs[p]; ++k) {

@@ -106,6 +106,27 @@ def test_batch_without_g_and_autotune(built):
         o += ref.size
 
 
+def test_batch_precision_override(built):
+    """Handles factored for mixed precision, solved as a batch in FP64 and in
+    mixed precision (the factors hold both)."""
+    probs = [(4, 3, 6, 2), (3, 5, 8, 1)]
+    grids = [Grid(mx, my, n) for (mx, my, n, _) in probs]
+    factor_many(grids, tol=1e-12, precision=1)
+    fs, gs, refs = make_inputs(probs, 12)
+    f, g = packed(fs), packed(gs)
+    for prec, bound in ((0, 1e-10), (1, 1e-9)):
+        b = Batch(grids, [k for *_, k in probs], precision=prec)
+        u = torch.zeros_like(f)
+        reps = b.solve(f, u, g=g)
+        assert all(r["refinements"] == 0 for r in reps) == (prec == 0)
+        uh = u.cpu().numpy()
+        o = 0
+        for ref in refs:
+            assert rel(uh[o:o + ref.size], ref) < bound
+            o += ref.size
+        b.close()
+
+
 def test_batch_config4_sample(built):
     """The first 12 problems of the seeded uneven config-4 batch (mixed
     precision, 1e-10): each right-hand side against the single-grid solve of
