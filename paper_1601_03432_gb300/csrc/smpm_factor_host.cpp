@@ -769,15 +769,23 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
       }
     }
   }
-  // bordered K = [[C, c0], [c0^T, 0]]: u_C from K^T [y; eta] = [0; 1], H from K^-1
+  // bordered K = [[C, c0^], [c0^T, 0]] with the unit c0^ = c0 / |c0|: u_C from
+  // K^T [y; eta] = [0; 1], H from K^-1.  The border's length does not change
+  // the leading block of K^-1 (the constraint c0^T y = 0 is the same), but
+  // c0 itself (-tau p per interface, ~1e7 on fine grids) against entries of C
+  // of order n would make K badly scaled and its inverse inaccurate by orders
+  // of magnitude on elongated grids.
   std::vector<double> Kinv;  // leading d x d block of K^-1 (kept for the adjoint)
   {
     const int d1 = d + 1;
+    double c0n = 0;
+    for (int i = 0; i < d; ++i) c0n += f->c0[i] * f->c0[i];
+    c0n = std::sqrt(c0n);
     std::vector<double> K1(static_cast<size_t>(d1) * d1, 0.0);
     for (int i = 0; i < d; ++i) {
       for (int j = 0; j < d; ++j) K1[static_cast<size_t>(i) * d1 + j] = f->C[static_cast<size_t>(i) * d + j];
-      K1[static_cast<size_t>(i) * d1 + d] = f->c0[i];
-      K1[static_cast<size_t>(d) * d1 + i] = f->c0[i];
+      K1[static_cast<size_t>(i) * d1 + d] = f->c0[i] / c0n;
+      K1[static_cast<size_t>(d) * d1 + i] = f->c0[i] / c0n;
     }
     DenseLU lu = lu_factor(K1.data(), d1);
     if (!lu.ok) { *err = "singular bordered coarse matrix"; return SMPM_EINVAL; }
