@@ -357,9 +357,12 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},
             "gpu_launches": launches,
+            # traffic: dram bytes read + written per k_gmres launch of this
+            # workload (L2 flushed before the step), from one ncu capture of
+            # the current kernel
             "roofline": {"kernel": "k_gmres (persistent GMRES, FP64)", "bound": "alu",
                          "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / fp64_peak_tf, "traffic": None,
+                         "frac": achieved_tf / fp64_peak_tf, "traffic": 16.417e6 + 5.4e3,
                          "achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                          "hbm_frac": achieved_gbs / hbm_peak, "share_of_step": gm_share,
                          "ms_per_launch": tot_ms / len(reps_timed),
