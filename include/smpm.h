@@ -73,6 +73,8 @@ typedef struct {
 #define SMPM_FLAG_NO_SMEM_RESIDENCY 1
 #define SMPM_FLAG_STREAM_MATRICES 2
 #define SMPM_FLAG_ADJOINT 4        /* also build the transposed system for schur_solve_adjoint */
+#define SMPM_FLAG_WARP_ELEMS 8     /* one warp per block / element in the GMRES phases even when few
+                                      are owned per CTA (the default from 4 per CTA; for testing) */
 
 /* Per-solve report, written by schur_solve when the pointer is non-null. */
 typedef struct {

@@ -67,6 +67,8 @@ struct GmresArgs {
   int stream_mats;     // 1: owned matrices streamed through two shared buffers (bulk copies)
   int buf_elems;       // elements of S per stream buffer (>= M*M + 4*n*n, multiple of 16 bytes)
   int nbuf;            // stream buffers (2..kMaxStreamBufs): nbuf - 1 items in flight while one is used
+  int warp_elems;      // 1: each warp works on its own block / white element (many per CTA); 0: the
+                       // whole CTA works on one element at a time
   long long* trace;
   int trace_cap;
   const int* skip;  // when non-null and set on entry, the kernel returns at once
@@ -141,6 +143,10 @@ __device__ __forceinline__ long long block_slot(const DevGeo& g, int e, int i) {
   return e2 >= 0 ? (long long)e2 * M + (F ^ 1) * n + t : -1;
 }
 
+// per-warp scratch of the warp-per-element phases: p, q (the block's own and
+// facing slots), r1, a, z
+__host__ __device__ __forceinline__ int warp_scratch(int M) { return 5 * M; }
+
 template <typename S>
 struct Smem {
   double *h1, *h2, *hs1, *hs2, *gcs, *gsn, *gg, *col, *invb, *misc, *cs;
@@ -149,6 +155,7 @@ struct Smem {
   double* cst;  // staged coarse vector c (d)
   S* V;     // (m+1) * ES when resident
   S* mats;  // resident matrices, or the two stream buffers
+  S* wb;    // warp_elems: per-warp element scratch, kWarpScratch(M) entries per warp
   unsigned long long* mbar;  // mbarriers of the matrix stream (kMaxStreamBufs)
 };
 
@@ -183,6 +190,13 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
     s.w = q; q += a.ES + 1;
     s.w2 = q; q += a.ES + 1;
   }
+  if (a.warp_elems) {  // 16-byte aligned base; each warp's 5M entries keep that alignment (M = 4n)
+    q = reinterpret_cast<S*>((reinterpret_cast<size_t>(q) + 15) & ~size_t(15));
+    s.wb = q;
+    q += (size_t)(blockDim.x / 32) * warp_scratch(M);
+  } else {
+    s.wb = nullptr;
+  }
   s.V = q;
   if (a.basis_smem) q += (size_t)(m + 1) * a.ES;
   q = reinterpret_cast<S*>((reinterpret_cast<size_t>(q) + 15) & ~size_t(15));
@@ -192,9 +206,11 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
 
 template <typename S>
 inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
-                               long long d, int stream_elems = 0, bool w_global = false, int nbuf = 2) {
+                               long long d, int stream_elems = 0, bool w_global = false, int nbuf = 2,
+                               bool warp_elems = false) {
   size_t dbl = kMaxStreamBufs + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
   size_t sel = 4 * (size_t)M + 256 + (w_global ? 0 : 2 * (size_t)(ES + 1));
+  if (warp_elems) sel += (size_t)(kGmresThreads / 32) * warp_scratch(M) + 16 / sizeof(S);
   if (basis_smem) sel += (size_t)(m + 1) * ES;
   if (mats_smem) sel += (size_t)nown_b * (2 * (size_t)M * M + 4 * (size_t)n * n) + (size_t)nown_w * M * M;
   sel += (size_t)nbuf * stream_elems;
@@ -585,10 +601,142 @@ __device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
   return block_slot(a.g, a.black[ib], ii);
 }
 
+// ---- warp-per-element phases -------------------------------------------
+// z[r] = sum_c A[c*M + r] x[c] for r < M by one warp: lane l owns rows
+// l, l+32, l+64, l+96 (M <= 128); A column-major in shared or global memory
+// (read-only), four columns per step with their loads issued first; x and z
+// in the warp's shared scratch.  Ends with __syncwarp.
+template <typename S>
+__device__ __forceinline__ void warp_gemv(const S* A, const S* x, S* z, int M, int lane) {
+  S acc[4] = {S(0), S(0), S(0), S(0)};
+  const int nr = (M - lane + 31) / 32;  // rows of this lane (0..4)
+  int c = 0;
+  for (; c + 4 <= M; c += 4) {
+    S av[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) av[u][j] = j < nr ? A[(size_t)(c + u) * M + lane + 32 * j] : S(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const S xc = x[c + u];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] += av[u][j] * xc;
+    }
+  }
+  for (; c < M; ++c) {
+    const S xc = x[c];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nr) acc[j] += A[(size_t)c * M + lane + 32 * j] * xc;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (j < nr) z[lane + 32 * j] = acc[j];
+  __syncwarp();
+}
+
+// Black block solves with one warp per owned block (blocks k = warp,
+// warp + nwarps, ...): vb = sc * (own slice or src), r1 = p - X q, a = G r1,
+// z = T_e a, t = [a; q - z] on the block's slots.
+template <typename S>
+__device__ void black_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const S* src, double sc, const S* own) {
+  const DevGeo& g = a.g;
+  const int M = g.M, n = g.n, G = a.G, rank = team_rank(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  S* p = s.wb + (size_t)warp * warp_scratch(M);
+  S* q = p + M;
+  S* r1 = q + M;
+  S* av = r1 + M;
+  S* z = av + M;
+  for (int k = warp; k < a.nown_b; k += nwarps) {
+    const int ib = rank + k * G;
+    if (ib >= a.nblack) break;
+    const int e = a.black[ib];
+    for (int i = lane; i < 2 * M; i += 32) {
+      S v;
+      if (own) {
+        v = (S)(sc * (double)own[k * 2 * M + i]);
+      } else {
+        const long long sl = block_slot(g, e, i);
+        v = sl >= 0 ? (S)(sc * (double)ldcg(src + sl)) : S(0);
+      }
+      p[i] = v;  // p and q are contiguous: q = p + M
+    }
+    __syncwarp();
+    const S* X = mat_X(a, s, k, ib);
+    for (int i = lane; i < M; i += 32) {
+      const int F = i / n, t = i % n;
+      const S* xf = X + (size_t)F * n * n;
+      S acc = 0;
+      for (int c = 0; c < n; ++c) acc += xf[c * n + t] * q[F * n + c];
+      r1[i] = p[i] - acc;
+    }
+    __syncwarp();
+    warp_gemv(mat_G(a, s, k, ib), r1, av, M, lane);
+    warp_gemv(mat_Tb(a, s, k, e), av, z, M, lane);
+    for (int i = lane; i < 2 * M; i += 32) {
+      const long long sl = block_slot(g, e, i);
+      if (sl >= 0) a.t[sl] = i < M ? av[i] : (S)(q[i - M] - z[i - M]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// White elements with one warp per element: y = S t on the black slots
+// facing e, y = sc*v on e's slots, c = Z^T y on e's interfaces (with_c).
+template <typename S>
+__device__ void white_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const S* v, double sc, bool with_c) {
+  const DevGeo& g = a.g;
+  const int M = g.M, n = g.n, G = a.G, rank = team_rank(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  S* p = s.wb + (size_t)warp * warp_scratch(M);
+  S* z = p + M;
+  double* ci = reinterpret_cast<double*>(z + M + (M & 1));  // M doubles (within the 5M scratch for S = float
+                                                             // and for S = double)
+  for (int k = warp; k < a.nown_w; k += nwarps) {
+    const int iw = rank + k * G;
+    if (iw >= a.nwhite) break;
+    const int e = a.white[iw];
+    for (int i = lane; i < M; i += 32) p[i] = ldcg(a.t + (size_t)e * M + i);
+    __syncwarp();
+    warp_gemv(mat_Tw(a, s, k, e), p, z, M, lane);
+    for (int i = lane; i < M; i += 32) {
+      const int F = i / n, tt = i % n, e2 = dev_neighbour(g, e, F);
+      const S vo = (S)(sc * (double)ldcg(v + (size_t)e * M + i));
+      a.y[(size_t)e * M + i] = vo;
+      double c1 = 0;
+      if (e2 >= 0) {
+        const size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
+        const S ys = ldcg(a.t + sl) + z[i];
+        a.y[sl] = ys;
+        c1 = (double)vo + (double)ys;
+      }
+      ci[i] = c1;
+    }
+    __syncwarp();
+    if (with_c && lane < 4) {  // face F summed by lane F
+      const int F = lane, j = dev_iface(g, e, F);
+      if (j >= 0) {
+        double sum = 0;
+        for (int tt = 0; tt < n; ++tt) sum += ci[F * n + tt];
+        a.c[j] = sum;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
 // black block solves of this CTA from the global vector sc * src
 template <typename S>
 __device__ bool black_phase(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S>* ms, const S* src, double sc,
                             const S* own) {
+  if (a.warp_elems) {
+    black_phase_warps(a, s, src, sc, own);
+    return true;
+  }
   const DevGeo& g = a.g;
   const int M = g.M, G = a.G;
   for (int k = 0; k < a.nown_b; ++k) {
@@ -635,7 +783,8 @@ __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, 
   GM_TRACE(20);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(21);
-  for (int k = 0; k < a.nown_w; ++k) {
+  if (a.warp_elems) white_phase_warps(a, s, src, sc, a.precond == 2);
+  for (int k = 0; k < (a.warp_elems ? 0 : a.nown_w); ++k) {
     int iw = team_rank(a) + k * G;
     if (iw >= a.nwhite) break;
     if (ms) {

@@ -33,8 +33,8 @@ struct RefineArgs {
 };
 
 inline size_t refine_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, long long d,
-                                bool w_global = false) {
-  return gmres_smem_bytes<float>(m, M, n, ES, nown_b, nown_w, 0, 0, d, 0, w_global) +
+                                bool w_global = false, bool warp_elems = false) {
+  return gmres_smem_bytes<float>(m, M, n, ES, nown_b, nown_w, 0, 0, d, 0, w_global, 2, warp_elems) +
          (2 * (size_t)M + 256 + 16) * sizeof(double);
 }
 

@@ -45,6 +45,7 @@ constexpr int kGmresThreads = 256;    // threads per CTA of the persistent GMRES
 constexpr size_t kCtlBytes = 720;  // + 32 inner iteration counts
 constexpr int kMaxRefine = 8;        // FP64 refinement steps of the mixed-precision path
 constexpr int kMaxStreamBufs = 4;    // shared-memory buffers of the GMRES kernel's matrix stream
+constexpr int kWarpElemsMin = 4;     // owned blocks per CTA from which each warp takes its own element
 constexpr double kInnerTol = 1e-4;   // relative tolerance of each FP32 inner GMRES
 
 struct GState {
@@ -899,7 +900,7 @@ struct smpm_handle_s {
   GState* wgs = nullptr;
   struct {
     int grid = 0, nown_b = 0, nown_w = 0, ES = 0, mats_smem = 0, basis_smem = 0, stream_mats = 0, buf_elems = 0,
-        nbuf = 2;
+        nbuf = 2, warp_elems = 0;
     size_t smem = 0, smem_pp = 0;
   } gm;  // launch shape of the persistent GMRES kernel
   double* wvown = nullptr;
@@ -910,7 +911,7 @@ struct smpm_handle_s {
   double *wr = nullptr, *wcr = nullptr, *wrn = nullptr;
   int *wdone = nullptr, *wnref = nullptr;
   struct {
-    int basis_smem = 0, mats_smem = 0, stream_mats = 0, buf_elems = 0, nbuf = 2;
+    int basis_smem = 0, mats_smem = 0, stream_mats = 0, buf_elems = 0, nbuf = 2, warp_elems = 0;
     size_t smem = 0, smem_ref = 0;
   } gm32;
   double *wacc8 = nullptr, *wxs = nullptr, *dZtuS = nullptr;
@@ -1115,14 +1116,15 @@ smpm_status print_trace(smpm_handle h, cudaStream_t st) {
 // buffers) + basis; streamed matrices with the basis in global memory; all
 // global.
 struct Layout {
-  int basis_smem, mats_smem, stream_mats, buf_elems, nbuf;
+  int basis_smem, mats_smem, stream_mats, buf_elems, nbuf, warp_elems;
   size_t smem;
 };
 
 template <typename S>
 Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, int precond, bool no_smem,
-                     bool force_stream, int smem_optin, bool w_global = false) {
+                     bool force_stream, int smem_optin, bool w_global = false, bool warp = false) {
   Layout L;
+  L.warp_elems = warp ? 1 : 0;  // warps read their matrices resident or from global memory: no stream
   L.buf_elems = g.M * g.M + 4 * g.n * g.n;
   L.basis_smem = no_smem ? 0 : 1;
   L.mats_smem = (no_smem || force_stream) ? 0 : 1;
@@ -1130,10 +1132,10 @@ Layout choose_layout(const Geometry& g, int m, int ES, int nown_b, int nown_w, i
   L.nbuf = 2;
   auto need = [&]() {
     return gmres_smem_bytes<S>(m, g.M, g.n, ES, nown_b, nown_w, L.basis_smem, L.mats_smem, g.d,
-                               L.stream_mats ? L.buf_elems : 0, w_global, L.nbuf);
+                               L.stream_mats ? L.buf_elems : 0, w_global, L.nbuf, warp);
   };
   if (need() > (size_t)smem_optin) L.mats_smem = 0;
-  if (!L.mats_smem && !no_smem && precond > 0) {
+  if (!L.mats_smem && !no_smem && precond > 0 && !warp) {
     L.stream_mats = 1;
     if (need() > (size_t)smem_optin) L.basis_smem = 0;
     if (need() > (size_t)smem_optin) L.stream_mats = 0;
@@ -1169,6 +1171,7 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
   a.mats_smem = h->gm.mats_smem; a.basis_smem = h->gm.basis_smem;
   a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems; a.nbuf = h->gm.nbuf;
+  a.warp_elems = h->gm.warp_elems;
   a.trace = h->wtrace;
   a.trace_cap = h->wtrace ? kTraceCap : 0;
   a.skip = nullptr;
@@ -1192,6 +1195,7 @@ GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
   a.nown_b = h->gm.nown_b; a.nown_w = h->gm.nown_w; a.ES = h->gm.ES;
   a.mats_smem = h->gm32.mats_smem; a.basis_smem = h->gm32.basis_smem;
   a.stream_mats = h->gm32.stream_mats; a.buf_elems = h->gm32.buf_elems; a.nbuf = h->gm32.nbuf;
+  a.warp_elems = h->gm32.warp_elems;
   a.trace = nullptr;
   a.trace_cap = 0;
   a.skip = h->wdone;
@@ -1210,6 +1214,7 @@ PrePostArgs prepost_args(smpm_handle h, double tol, const double* f, const doubl
   P.ga.mats_smem = 0;
   P.ga.basis_smem = 0;
   P.ga.stream_mats = 0;
+  P.ga.warp_elems = 0;  // the pre/post kernels' shared memory has no per-warp scratch
   P.ga.trace = nullptr;
   P.fdx = h->dfdx; P.fdy = h->dfdy; P.D = h->dD; P.uL = h->duL; P.uS = h->duS; P.what = h->dwhat;
   P.ZtuS = h->dZtuS; P.f = f; P.gn = gn; P.b = h->wb; P.bS = h->wbS; P.rg = h->wrg; P.cb = h->wcb;
@@ -1549,8 +1554,11 @@ smpm_status batch_layout(smpm_batch b, int T) {
     };
     L.wg = need_fixed(false) > (size_t)budget;
     const int precond = h->opts.precond;
-    L.lay = mixed ? choose_layout<float>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg)
-                  : choose_layout<double>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg);
+    const bool warp = precond > 0 && L.nown_b >= kWarpElemsMin;
+    L.lay = mixed ? choose_layout<float>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg, warp)
+                  : choose_layout<double>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg, warp);
+    if (mixed && warp)  // the refinement body runs the warp phases too
+      L.lay.smem = std::max(L.lay.smem, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, L.wg, true));
     const size_t nd = kBatchHdr + std::max(need_fixed(L.wg), L.lay.smem);
     if (nd > (size_t)optin - 1024)
       return fail(SMPM_EINVAL, "a problem of the batch is too large for teams of this size");
@@ -1606,6 +1614,7 @@ smpm_status batch_layout(smpm_batch b, int T) {
           a.stream_mats = L.lay.stream_mats;
           a.buf_elems = L.lay.buf_elems;
           a.nbuf = L.lay.nbuf;
+          a.warp_elems = L.lay.warp_elems;
         };
         if (mixed) {
           bt.a32 = gmres_args32(h, kInnerTol);
@@ -1613,6 +1622,7 @@ smpm_status batch_layout(smpm_batch b, int T) {
           bt.a32.vown = L.vown32;
           bt.a32.wscr = L.wscr32;
           bt.R = refine_args(h, bt.a32, tol);  // all-global (refine_args clears the layout)
+          bt.R.ga.warp_elems = L.lay.warp_elems;
           layout_fields(bt.a32);
         } else {
           bt.a64 = gmres_args(h, tol);
@@ -1934,14 +1944,18 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
     const int m = opts.restart;
     const bool no_smem = (opts.flags & SMPM_FLAG_NO_SMEM_RESIDENCY) != 0;
     const bool force_stream = (opts.flags & SMPM_FLAG_STREAM_MATRICES) != 0;
+    // one warp per element when every CTA owns several blocks (or on request)
+    const bool warp = opts.precond > 0 && !force_stream &&
+                      (gm.nown_b >= kWarpElemsMin || (opts.flags & SMPM_FLAG_WARP_ELEMS) != 0);
     {
       Layout L = choose_layout<double>(g, m, gm.ES, gm.nown_b, gm.nown_w, opts.precond, no_smem, force_stream,
-                                       smem_optin);
+                                       smem_optin, false, warp);
       gm.basis_smem = L.basis_smem;
       gm.mats_smem = L.mats_smem;
       gm.stream_mats = L.stream_mats;
       gm.buf_elems = L.buf_elems;
       gm.nbuf = L.nbuf;
+      gm.warp_elems = L.warp_elems;
       gm.smem = L.smem;
     }
     CU(set_smem_limit(k_gmres<double>, smem_optin));
@@ -1952,18 +1966,19 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       // FP32 inner GMRES: FP32 copies of the operator, its own layout, the
       // refinement kernel, FP32 work vectors and the FP64 residual
       Layout L = choose_layout<float>(g, m, gm.ES, gm.nown_b, gm.nown_w, opts.precond, no_smem, force_stream,
-                                      smem_optin);
+                                      smem_optin, false, warp);
       auto& g32 = h->gm32;
       g32.basis_smem = L.basis_smem;
       g32.mats_smem = L.mats_smem;
       g32.stream_mats = L.stream_mats;
       g32.buf_elems = L.buf_elems;
       g32.nbuf = L.nbuf;
+      g32.warp_elems = L.warp_elems;
       g32.smem = L.smem;
       CU(set_smem_limit(k_gmres<float>, smem_optin));
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gmres<float>, kGmresThreads, g32.smem));
       if (per_sm < 1) return fail(SMPM_ECUDA, "the FP32 GMRES kernel does not fit on an SM");
-      g32.smem_ref = refine_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d);
+      g32.smem_ref = refine_smem_bytes(m, g.M, g.n, gm.ES, gm.nown_b, gm.nown_w, g.d, false, g32.warp_elems != 0);
       if (g32.smem_ref > (size_t)smem_optin) return fail(SMPM_EINVAL, "grid too large for the refinement kernel");
       CU(set_smem_limit(k_refine, smem_optin));
       CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, kGmresThreads, g32.smem_ref));

@@ -53,7 +53,7 @@ def pair(request, built):
     return og, osys, lg
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2], ids=["smem", "global", "stream"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 8], ids=["smem", "global", "stream", "warps"])
 @pytest.mark.parametrize("precond", [0, 1, 2])
 def test_adjoint_matches_oracle(pair, precond, flags):
     og, osys, lg = pair

@@ -86,7 +86,7 @@ def test_null_vectors(pair):
         assert np.linalg.norm(got - ref) < 1e-12
 
 
-@pytest.mark.parametrize("flags", [0, 1, 2], ids=["smem", "global", "stream"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 8, 9], ids=["smem", "global", "stream", "warps", "warps-global"])
 @pytest.mark.parametrize("precond", [0, 1, 2])
 def test_solve_matches_oracle(pair, precond, flags):
     og, osys, lg = pair
@@ -208,7 +208,7 @@ def test_config2_full_size(built):
     assert rel(host(u), ud) < 1e-8
 
 
-@pytest.mark.parametrize("flags", [0, 2], ids=["smem", "stream"])
+@pytest.mark.parametrize("flags", [0, 2, 8], ids=["smem", "stream", "warps"])
 def test_mixed_precision_matches_oracle(pair, flags):
     """FP32 inner GMRES inside FP64 iterative refinement: the solution
     matches the exact discrete solution to a relative L2 error of 1e-9."""
