@@ -63,7 +63,36 @@ __device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& 
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
   // ---- R5: r = b_S - S x_S (FP64), ||r||^2, Z^T r
   double pr = 0;
-  for (long long e = rank; e < g.nel; e += G) {
+  if (a.warp_elems) {  // one warp per element (elements rank + k G, k = warp, warp + nwarps, ...)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    double* pw = reinterpret_cast<double*>(s.wb + (size_t)warp * warp_scratch(M));  // 2M doubles fit in 5M floats
+    double* zw = pw + M;
+    for (long long e = rank + (long long)warp * G; e < g.nel; e += (long long)nwarps * G) {
+      for (int i = lane; i < M; i += 32) pw[i] = __ldcg(R.xS + e * M + i);
+      __syncwarp();
+      warp_gemv(R.Tc64 + (size_t)e * M * M, pw, zw, M, lane);
+      for (int i = lane; i < M; i += 32) {  // pw is free again: it takes the residual entries
+        const int F = i / n, t = i % n, e2 = dev_neighbour(g, (int)e, F);
+        double rr = 0;
+        if (e2 >= 0) {
+          const size_t sl = (size_t)e2 * M + (F ^ 1) * n + t;
+          rr = R.bS[sl] - (__ldcg(R.xS + sl) + zw[i]);
+          R.r[sl] = rr;
+          pr += rr * rr;
+        }
+        pw[i] = rr;
+      }
+      __syncwarp();
+      if (lane < 4) {  // face F summed by lane F
+        const int F = lane, j = dev_iface(g, (int)e, F);
+        double sum = 0;
+        for (int t = 0; t < n; ++t) sum += pw[F * n + t];
+        if (j >= 0 && sum != 0.0) atomicAdd(R.cr + j, sum);
+      }
+      __syncwarp();
+    }
+  }
+  for (long long e = rank; e < (a.warp_elems ? 0 : g.nel); e += G) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) p64[i] = __ldcg(R.xS + e * M + i);
     __syncthreads();
     gemv_split(R.Tc64 + (size_t)e * M * M, M, p64, z64, M, M, red64);

@@ -1552,11 +1552,16 @@ smpm_status batch_layout(smpm_batch b, int T) {
       if (mixed) a = std::max(a, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, wg));
       return a;
     };
-    L.wg = need_fixed(false) > (size_t)budget;
     const int precond = h->opts.precond;
     const bool warp = precond > 0 && L.nown_b >= kWarpElemsMin;
-    L.lay = mixed ? choose_layout<float>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg, warp)
-                  : choose_layout<double>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, L.wg, warp);
+    auto lay_for = [&](bool wg) {
+      return mixed ? choose_layout<float>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, wg, warp)
+                   : choose_layout<double>(g, m, L.ES, L.nown_b, L.nown_w, precond, false, false, budget, wg, warp);
+    };
+    // w, w2 move to global scratch when either the pre/post bodies or the
+    // GMRES body (with its per-warp scratch) would not fit beside them
+    L.wg = need_fixed(false) > (size_t)budget || lay_for(false).smem > (size_t)budget;
+    L.lay = lay_for(L.wg);
     if (mixed && warp)  // the refinement body runs the warp phases too
       L.lay.smem = std::max(L.lay.smem, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, L.wg, true));
     const size_t nd = kBatchHdr + std::max(need_fixed(L.wg), L.lay.smem);
