@@ -100,6 +100,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------- ranks
+def job_rate(local_ms, steps, world, dist=None, device="cpu"):
+    """Whole-job rate of a weak-scaling run: each rank times its own steps,
+    the job's time is the MAX over ranks, and the job processed world x
+    steps units in it.  Returns (max ms, units per second)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
+def rank_seed(seed, rank):
+    """Right-hand-side seed of a rank: every replica solves its own problem."""
+    return seed + rank
+
+
 # ----------------------------------------------------------- CPU oracle
 def oracle_solve_seconds(steps, warmup, seed):
     """Time the oracle's Algorithm 3 on the bench workload in a fresh
@@ -182,7 +200,7 @@ def run_ours(args):
     g.factor(tol=W["tol"], restart=W["restart"])
     factor_s = time.perf_counter() - t0
     x, y = g.node_coords()
-    f, _ = inputs.fourier_rhs(x, y, seed=W["seed"] + rank)
+    f, _ = inputs.fourier_rhs(x, y, seed=rank_seed(W["seed"], rank))
     fd = torch.as_tensor(f, dtype=torch.float64, device="cuda")
     ud = torch.zeros_like(fd)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -218,12 +236,7 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms = float(t.item())
-    value = world * args.steps / (dev_ms / 1e3)
+    dev_ms, value = job_rate(sum(a.elapsed_time(b) for a, b in evs), args.steps, world, dist, "cuda")
 
     # ---- end to end through the host-pointer entry point
     fh = torch.empty(g.r, dtype=torch.float64).pin_memory()
@@ -239,10 +252,7 @@ def run_ours(args):
         a = time.perf_counter()
         g.solve_host(fnp, unp)
         e2e_ms += (time.perf_counter() - a) * 1e3
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / (float(t.item()) / 1e3)
+    _, e2e_value = job_rate(e2e_ms, args.steps, world, dist, "cuda")
     err_e2e = float(np.abs(unp - ud.cpu().numpy()).max())
 
     # ---- roofline of the dominant kernel: the persistent GMRES kernel
@@ -288,15 +298,13 @@ def run_ours(args):
         b_.record(stream)
         torch.cuda.synchronize()
         mix_ms += a_.elapsed_time(b_)
-    t = torch.tensor([mix_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    mixed = {"value": world * args.steps / (float(t.item()) / 1e3), "unit": "solves/s",
-             "ms_per_step": float(t.item()) / args.steps, "inner_iterations": mix_rep["iterations"],
+    mix_max, mix_rate = job_rate(mix_ms, args.steps, world, dist, "cuda")
+    mixed = {"value": mix_rate, "unit": "solves/s",
+             "ms_per_step": mix_max / args.steps, "inner_iterations": mix_rep["iterations"],
              "refinements": mix_rep["refinements"], "schur_relres": mix_rep["schur_relres"],
              "precision": "FP32 inner GMRES (FP32 operator, FP64 coarse/Givens/dot accumulation) + FP64 refinement"}
 
-    # ---- Schur apply y = S v (push form, one CTA per element) at a size
+    # ---- Schur apply y = S v (register-streamed, several warps per element) at a size
     # whose factor does not stay in L2 between launches: 32x32 elements,
     # n = 24 (T_e: 75.5 MB FP64, 37.7 MB FP32); L2 flushed before each launch.
     ga = Grid(32, 32, 24)
