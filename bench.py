@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch", type=int, default=512,
                    help="grids of the uneven batch section (0 skips it; 512 is the full seeded batch)")
-    p.add_argument("--profile", choices=["gmres", "apply", "bapply"], default=None,
+    p.add_argument("--profile", choices=["gmres", "apply", "bapply", "batch"], default=None,
                    help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
 
@@ -519,6 +519,24 @@ def run_profile(which):
         ud = torch.zeros_like(fd)
         for _ in range(3):
             g.solve(fd, ud)
+    elif which == "batch":
+        # four grids of the uneven batch (large to small), two right-hand
+        # sides each, mixed precision, teams of 8: three batched solves
+        from paper_1601_03432_gb300 import Batch, factor_many
+        probs = [(30, 27, 23, 2), (17, 25, 24, 2), (30, 17, 11, 2), (11, 13, 10, 2)]
+        grids = [Grid(mx, my, n) for (mx, my, n, k) in probs]
+        factor_many(grids, tol=W["tol"], restart=W["restart"], precision=1)
+        import numpy as np
+        f = fourier_packed(grids, [p[3] for p in probs], torch, np, inputs)
+        b = Batch(grids, [p[3] for p in probs], team_size=8, use_graph=False)
+        u = torch.zeros_like(f)
+        for _ in range(3):
+            b.solve(f, u)
+        torch.cuda.synchronize()
+        team, t0, t1 = b.task_times()
+        print("ok", b.info()["last_ms"], [round(x, 2) for x in (t1 - t0)])
+        b.close()
+        return
     elif which == "bapply":
         # the first 40 grids of the seeded uneven batch (0.25 GB FP32 operator)
         from paper_1601_03432_gb300 import Batch, factor_many

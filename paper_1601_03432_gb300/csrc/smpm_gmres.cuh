@@ -604,21 +604,24 @@ __device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
 // ---- warp-per-element phases -------------------------------------------
 // z[r] = sum_c A[c*M + r] x[c] for r < M by one warp: lane l owns rows
 // l, l+32, l+64, l+96 (M <= 128); A column-major in shared or global memory
-// (read-only), four columns per step with their loads issued first; x and z
-// in the warp's shared scratch.  Ends with __syncwarp.
+// (read-only), eight columns per step (four in FP64, whose registers and
+// pipe bind first) with all their loads issued first (up to 32 independent
+// loads per lane in flight: from global memory each step is one round trip);
+// x and z in the warp's shared scratch.  Ends with __syncwarp.
 template <typename S>
 __device__ __forceinline__ void warp_gemv(const S* A, const S* x, S* z, int M, int lane) {
+  constexpr int U = sizeof(S) == 4 ? 8 : 4;  // FP64: fewer registers, and its pipe, not latency, bounds it sooner
   S acc[4] = {S(0), S(0), S(0), S(0)};
   const int nr = (M - lane + 31) / 32;  // rows of this lane (0..4)
   int c = 0;
-  for (; c + 4 <= M; c += 4) {
-    S av[4][4];
+  for (; c + U <= M; c += U) {
+    S av[U][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int j = 0; j < 4; ++j) av[u][j] = j < nr ? A[(size_t)(c + u) * M + lane + 32 * j] : S(0);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       const S xc = x[c + u];
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[j] += av[u][j] * xc;
