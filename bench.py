@@ -339,6 +339,7 @@ def run_ours(args):
                    "note": "FP64 is bound by the FP64 ALU (1.26 TFLOP/s) before HBM; FP32 is HBM-bound"}
 
     batch = run_batch(args, stream, hbm_peak) if args.batch > 0 else None
+    config3 = run_config3(args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -361,6 +362,7 @@ def run_ours(args):
             "mixed": mixed,
             "schur_apply": schur_apply,
             "batch": batch,
+            "config3": config3,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},
@@ -389,6 +391,55 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------ precision config
+def run_config3(args, stream):
+    """32x32 elements, n = 24, 8 seeded Fourier right-hand sides, tol 1e-10:
+    mixed precision (FP32 inner GMRES, FP64 refinement) against FP64, as
+    8 consecutive solves on the handle and as one batched launch (the 8
+    right-hand sides of the one grid, all SMs as one team)."""
+    import numpy as np
+    import torch
+    from paper_1601_03432_gb300 import Batch, Grid, inputs
+    W = WORKLOAD
+    out = {"workload": "32x32 elements, n=24 (r=589824), 8 Fourier right-hand sides (seeds 1000-1007), tol 1e-10"}
+    grids = {}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        g = Grid(32, 32, 24)
+        g.factor(tol=W["tol"], restart=W["restart"], precision=prec)
+        grids[name] = g
+    f = fourier_packed([grids["fp64"]], [8], torch, np, inputs)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sols = {}
+    for name, g in grids.items():
+        u = torch.zeros_like(f)
+        g.solve(f, u, nrhs=8)  # warm-up
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        reps = g.solve(f, u, nrhs=8)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms = a_.elapsed_time(b_)
+        b = Batch([g], [8], team_size=sms)
+        ub = torch.zeros_like(f)
+        b.solve(f, ub)
+        rb = b.solve(f, ub)
+        out[name] = {"solves_per_s": 8 / (ms / 1e3), "ms_for_8": ms,
+                     "iterations": [r["iterations"] for r in reps],
+                     "refinements_max": max(r["refinements"] for r in reps),
+                     "all_converged": all(r["converged"] == 1 for r in reps),
+                     "batched_one_launch": {"solves_per_s": 8 / (b.info()["last_ms"] / 1e3),
+                                            "ms_for_8": b.info()["last_ms"],
+                                            "all_converged": all(r["converged"] == 1 for r in rb)}}
+        sols[name] = u.cpu().numpy().reshape(8, -1)
+        b.close()
+    out["mixed_vs_fp64_rel_l2_max"] = float(max(np.linalg.norm(sols["mixed"][k] - sols["fp64"][k]) /
+                                                np.linalg.norm(sols["fp64"][k]) for k in range(8)))
+    out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    for g in grids.values():
+        g.close()
+    return out
 
 
 # ------------------------------------------------------------- batch

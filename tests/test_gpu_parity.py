@@ -257,3 +257,59 @@ def test_handles_of_different_sizes_interleaved(built):
         lg.solve(dev(f), u)
         ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, f)
         assert rel(host(u), ud) < 1e-10
+
+
+@pytest.mark.slow
+def test_config3_full_size_properties(built):
+    """32 x 32 elements, n = 24, 8 seeded Fourier right-hand sides, mixed
+    precision and FP64 to tol 1e-10.  The oracle's Algorithm 3 is too slow
+    at this size, so the check uses properties that hold at any size, with
+    the oracle's own operator L (assembled independently of the library):
+    the library's u_L is a left null vector of L; every solution has zero
+    GLL mean; and its residual meets the bound the method implies.  With
+    u = A^-1 (b~ - E x_S) and L = A + E B, L u - b~ = E r_S for the Schur
+    residual r_S = b_S - S x_S, and both solvers stop at
+    |r_S| <= tol |P b_S| (GMRES on P S M^-1 starting from 0; the refinement
+    test), so |L u - b~| <= sqrt(2) tol |P b_S| (E adds at most two slots
+    into a corner node); the check allows a factor 2 on that for rounding.
+    Mixed and FP64 solutions agree."""
+    og = SMPMGrid(32, 32, 24)
+    Lm = og.assemble_L()
+    x, y = og.coords()
+    F = np.stack([inputs.fourier_rhs(x, y, seed=1000 + k)[0] for k in range(8)])
+    w = og.mass()
+    tol = 1e-10
+    sols, pbs = {}, []
+    for prec in (0, 1):
+        lg = Grid(32, 32, 24)
+        lg.factor(tol=tol, precision=prec)
+        u = torch.zeros((8, og.r), dtype=torch.float64, device="cuda")
+        reps = lg.solve(dev(F), u, nrhs=8)
+        assert all(r["converged"] == 1 for r in reps), reps
+        sols[prec] = host(u)
+        if prec == 0:
+            uL = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+            uS = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+            uC = torch.zeros(og.d, dtype=torch.float64, device="cuda")
+            lg.null_vectors(uL, uS, uC)
+            uL, uSd = host(uL), uS
+            for k in range(8):   # |P b_S| of each right-hand side
+                bt = F[k] - uL * (uL @ F[k])
+                bS = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+                lg.schur_rhs(dev(bt), bS)
+                bS -= uSd * (uSd @ bS)
+                pb = torch.zeros_like(bS)
+                lg.apply_deflation(bS, pb)
+                pbs.append(float(torch.linalg.norm(pb)))
+        lg.close()
+    v = np.random.default_rng(1).standard_normal(og.r)
+    v /= np.linalg.norm(v)
+    assert np.linalg.norm(Lm.T @ uL) <= 1e-9 * np.linalg.norm(Lm.T @ v)
+    for prec, U in sols.items():
+        for k in range(8):
+            bt = F[k] - uL * (uL @ F[k])
+            res = np.linalg.norm(Lm @ U[k] - bt)
+            assert res <= 2 * np.sqrt(2) * tol * pbs[k], (prec, k, res, tol * pbs[k])
+            assert abs(w @ U[k]) <= 1e-12 * np.abs(w).sum() * np.abs(U[k]).max()
+    for k in range(8):
+        assert rel(sols[1][k], sols[0][k]) < 1e-8
