@@ -274,7 +274,7 @@ def run_ours(args):
         tot_ms += r_["gmres_ms"]
     achieved_tf = tot_flops / (tot_ms * 1e-3) / 1e12
     achieved_gbs = tot_bytes / (tot_ms * 1e-3) / 1e9
-    fp64_peak_tf = 152 * 2070e6 * 4 / 1e12    # 2 FP64 FMA / clk / SM at the max clock
+    fp64_peak_tf = 152 * 2070e6 * 4 / 1e12    # 152 SMs x 2 FP64 FMA (4 flop) per clock at the 2.07 GHz max clock
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
