@@ -993,11 +993,17 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
         double bsq = s.misc[1] - s.misc[5];
         double ib = bsq > 0 ? rsqrt(bsq) : 0.0;
         double bnext = bsq > 0 ? bsq * ib : 0.0;
+        // the rotated entry is carried in a register: one dependent FMA per
+        // rotation (the products with the unrotated entries do not depend
+        // on the chain)
+        double xi = s.col[0];
         for (int i = 0; i < j; ++i) {
-          double x0 = s.col[i], x1 = s.col[i + 1];
-          s.col[i] = s.gcs[i] * x0 + s.gsn[i] * x1;
-          s.col[i + 1] = -s.gsn[i] * x0 + s.gcs[i] * x1;
+          const double x1 = s.col[i + 1], c = s.gcs[i], sn = s.gsn[i];
+          const double cx1 = c * x1, sx1 = sn * x1;
+          s.col[i] = fma(c, xi, sx1);
+          xi = fma(-sn, xi, cx1);
         }
+        s.col[j] = xi;
         double hh = s.col[j] * s.col[j] + bnext * bnext;
         double iden = hh > 0 ? rsqrt(hh) : 0.0;
         double cc = hh > 0 ? s.col[j] * iden : 1.0, ss = bnext * iden;
