@@ -372,7 +372,7 @@ def run_ours(args):
             # the current kernel
             "roofline": {"kernel": "k_gmres (persistent GMRES, FP64)", "bound": "alu",
                          "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / fp64_peak_tf, "traffic": 16.422e6 + 4.6e3,
+                         "frac": achieved_tf / fp64_peak_tf, "traffic": 16.420e6 + 4.9e3,
                          "achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                          "hbm_frac": achieved_gbs / hbm_peak, "share_of_step": gm_share,
                          "ms_per_launch": tot_ms / len(reps_timed),
