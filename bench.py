@@ -338,8 +338,11 @@ def run_ours(args):
                    "median_of": 20, **apply,
                    "note": "FP64 is bound by the FP64 ALU (1.26 TFLOP/s) before HBM; FP32 is HBM-bound"}
 
-    batch = run_batch(args, stream, hbm_peak) if args.batch > 0 else None
-    config3 = run_config3(args, stream)
+    # the batch and precision-config sections run on single-GPU runs only: a
+    # multi-GPU run measures the replicated headline solve and holds every GPU
+    # for as short a time as that takes
+    batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and world == 1 else None
+    config3 = run_config3(args, stream) if world == 1 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
