@@ -279,18 +279,21 @@ smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, 
  * from the earliest start.  Host arrays of ntasks entries; any may be null. */
 smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, double* end_ms);
 
-/* y_p = S_p v_p for every problem p of the batch in one launch (one vector
- * per problem): v, y device, packed problem-major with kp_p entries each
- * (v_len = sum of kp_p).  The element matrices of all problems stream
- * through shared memory with bulk copies (as smpm_apply_schur does for one
- * grid).  The FP32 variant needs every handle factored with precision 1.
+/* y_p = S_p v_p (Eq. schur_complement_system) for every problem p of the
+ * batch in one launch (one vector per problem): v, y device, packed
+ * problem-major with kp_p entries each (v_len = sum of kp_p).  By default one
+ * warp per element reads the element's T_e column by column straight from
+ * global memory with many loads in flight (see smpm_batch_set_apply_kernel).
+ * The FP32 variant needs every handle factored with precision 1.
  * Asynchronous on stream.  Errors: EINVAL, ESTATE, ECUDA. */
 smpm_status smpm_batch_apply_schur(smpm_batch b, const double* v, double* y, void* stream);
-/* Kernel of the batched apply: 1 (default) one warp per element reading T_e
- * from global memory (element matrices up to 96 x 96, i.e. n <= 24; larger
- * ones use 0), 0 bulk copies of T_e into a shared-memory ring per CTA. */
-smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind);
 smpm_status smpm_batch_apply_schur32(smpm_batch b, const float* v, float* y, void* stream);
+
+/* Kernel of the batched apply: 1 (default) warps per element reading T_e
+ * from global memory (element matrices up to 96 x 96, i.e. n <= 24; larger
+ * ones take kind 0), 0 bulk copies of T_e into a shared-memory ring per CTA
+ * (measured slower; kept selectable).  Errors: EINVAL. */
+smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind);
 
 /* Release the batch (not its handles; null is ignored). */
 void smpm_batch_destroy(smpm_batch b);
