@@ -313,3 +313,35 @@ def test_config3_full_size_properties(built):
             assert abs(w @ U[k]) <= 1e-12 * np.abs(w).sum() * np.abs(U[k]).max()
     for k in range(8):
         assert rel(sols[1][k], sols[0][k]) < 1e-8
+
+
+@pytest.mark.parametrize("mx,my,n", [(2, 3, 32), (3, 3, 29)])
+def test_largest_polynomial_order(built, mx, my, n):
+    """n up to 32, the library's limit (element matrices 128 x 128): FP64
+    and mixed-precision solves (also with one warp per element), the FP32
+    and FP64 single-grid applies and the batched apply, against the oracle."""
+    from paper_1601_03432_gb300 import Batch
+    og = SMPMGrid(mx, my, n)
+    osys = SchurSystem(og)
+    f = inputs.white_noise(og.r, 41)
+    gs = np.random.default_rng(42).standard_normal(og.kp)
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, og.rhs(f, gs))
+    lg = Grid(mx, my, n)
+    for prec, flags, bound in ((0, 0, 1e-10), (0, B.FLAG_WARP_ELEMS, 1e-10), (1, 0, 1e-9)):
+        lg.factor(tol=1e-12 if prec == 0 else 1e-11, precision=prec, flags=flags)
+        u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+        rep = lg.solve(dev(f), u, g=dev(gs))[0]
+        assert rep["converged"] == 1 and rel(host(u), ud) < bound, (prec, flags, rep)
+    v = np.random.default_rng(43).standard_normal(og.k)
+    ref = osys.apply_S(v)
+    out = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    lg.apply_schur(dev(og.to_padded(v)), out)
+    assert rel(og.from_padded(host(out)), ref) < 1e-12
+    out32 = torch.zeros(og.kp, dtype=torch.float32, device="cuda")
+    lg.apply_schur32(dev(og.to_padded(v)).float(), out32)
+    assert rel(og.from_padded(out32.double().cpu().numpy()), ref) < 1e-5
+    b = Batch([lg], [1])
+    yb = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    b.apply_schur(dev(og.to_padded(v)), yb)
+    assert rel(og.from_padded(host(yb)), ref) < 1e-12
+    b.close()
