@@ -125,17 +125,34 @@ def default_opts(**kw):
     return o
 
 
-def _ptr(x):
-    """Device or host pointer of a torch tensor / NumPy array (or None)."""
+def _dev(x, n, name, dtype="float64", optional=False):
+    """Pointer of a contiguous CUDA tensor of `dtype` holding at least n
+    entries.  The C ABI takes lengths from the handle, so a short, host or
+    wrongly typed buffer is refused here rather than read out of bounds."""
     if x is None:
-        return None
-    if isinstance(x, np.ndarray):
-        if x.dtype != np.float64 or not x.flags.c_contiguous:
-            raise TypeError("arrays must be contiguous float64")
-        return x.ctypes.data
-    if str(x.dtype) not in ("torch.float64", "torch.float32") or not x.is_contiguous():
-        raise TypeError("tensors must be contiguous float64 (float32 for the FP32 operator)")
+        if optional:
+            return None
+        raise TypeError("%s: a CUDA tensor is required" % name)
+    if isinstance(x, np.ndarray) or not getattr(x, "is_cuda", False):
+        raise TypeError("%s: expected a CUDA tensor" % name)
+    if str(x.dtype) != "torch." + dtype or not x.is_contiguous():
+        raise TypeError("%s: expected a contiguous %s tensor, got %s" % (name, dtype, x.dtype))
+    if x.numel() < n:
+        raise ValueError("%s: %d entries, %d needed" % (name, x.numel(), n))
     return x.data_ptr()
+
+
+def _host(x, n, name, optional=False):
+    """Pointer of a contiguous float64 NumPy array of at least n entries."""
+    if x is None:
+        if optional:
+            return None
+        raise TypeError("%s: a NumPy array is required" % name)
+    if not isinstance(x, np.ndarray) or x.dtype != np.float64 or not x.flags.c_contiguous:
+        raise TypeError("%s: expected a contiguous float64 NumPy array" % name)
+    if x.size < n:
+        raise ValueError("%s: %d entries, %d needed" % (name, x.size, n))
+    return x.ctypes.data
 
 
 def _stream(stream):
@@ -210,7 +227,8 @@ class Grid:
     def solve(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
         """schur_solve on device tensors (float64, contiguous); returns the reports."""
         reps = (SmpmReport * nrhs)()
-        st = lib().schur_solve(self.h, _ptr(f), _ptr(g), float(tol), nrhs, _ptr(u), reps, _stream(stream))
+        st = lib().schur_solve(self.h, _dev(f, self.r * nrhs, "f"), _dev(g, self.kp * nrhs, "g", optional=True),
+                               float(tol), nrhs, _dev(u, self.r * nrhs, "u"), reps, _stream(stream))
         check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
         return [r.as_dict() for r in reps]
 
@@ -218,20 +236,25 @@ class Grid:
         """schur_solve_adjoint on device tensors: dl/df (and dl/dg) from dl/du;
         needs factor(flags=FLAG_ADJOINT)."""
         reps = (SmpmReport * nrhs)()
-        st = lib().schur_solve_adjoint(self.h, _ptr(gbar_u), float(tol), nrhs, _ptr(gbar_f), _ptr(gbar_g), reps,
-                                       _stream(stream))
+        st = lib().schur_solve_adjoint(self.h, _dev(gbar_u, self.r * nrhs, "gbar_u"), float(tol), nrhs,
+                                       _dev(gbar_f, self.r * nrhs, "gbar_f"),
+                                       _dev(gbar_g, self.kp * nrhs, "gbar_g", optional=True), reps, _stream(stream))
         check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
         return [r.as_dict() for r in reps]
 
     def solve_host(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
         """schur_solve_host on host NumPy arrays."""
         reps = (SmpmReport * nrhs)()
-        st = lib().schur_solve_host(self.h, _ptr(f), _ptr(g), float(tol), nrhs, _ptr(u), reps, _stream(stream))
+        st = lib().schur_solve_host(self.h, _host(f, self.r * nrhs, "f"), _host(g, self.kp * nrhs, "g", optional=True),
+                                    float(tol), nrhs, _host(u, self.r * nrhs, "u"), reps, _stream(stream))
         check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
         return [r.as_dict() for r in reps]
 
-    def _op(self, name, v, out, stream=None):
-        check(getattr(lib(), name)(self.h, _ptr(v), _ptr(out), _stream(stream)))
+    def _op(self, name, v, out, stream=None, n_in=None, n_out=None, dtype="float64"):
+        n_in = self.kp if n_in is None else n_in
+        n_out = self.kp if n_out is None else n_out
+        check(getattr(lib(), name)(self.h, _dev(v, n_in, "v", dtype), _dev(out, n_out, "out", dtype),
+                                   _stream(stream)))
         return out
 
     def apply_schur(self, v, out, stream=None):
@@ -239,7 +262,7 @@ class Grid:
 
     def apply_schur32(self, v, out, stream=None):
         """y = S v in FP32 (float32 tensors; needs factor(precision=1))."""
-        return self._op("smpm_apply_schur32", v, out, stream)
+        return self._op("smpm_apply_schur32", v, out, stream, dtype="float32")
 
     def apply_precond(self, v, out, stream=None):
         return self._op("smpm_apply_precond", v, out, stream)
@@ -259,14 +282,17 @@ class Grid:
         return self._op("smpm_apply_deflation_q", v, out, stream)
 
     def schur_rhs(self, b, out, stream=None):
-        return self._op("smpm_schur_rhs", b, out, stream)
+        return self._op("smpm_schur_rhs", b, out, stream, n_in=self.r)
 
     def recover(self, b, x, out, stream=None):
-        check(lib().smpm_recover(self.h, _ptr(b), _ptr(x), _ptr(out), _stream(stream)))
+        check(lib().smpm_recover(self.h, _dev(b, self.r, "b"), _dev(x, self.kp, "x"), _dev(out, self.r, "out"),
+                                 _stream(stream)))
         return out
 
     def null_vectors(self, uL, uS, uC, stream=None):
-        check(lib().smpm_null_vectors(self.h, _ptr(uL), _ptr(uS), _ptr(uC), _stream(stream)))
+        check(lib().smpm_null_vectors(self.h, _dev(uL, self.r, "uL", optional=True),
+                                      _dev(uS, self.kp, "uS", optional=True), _dev(uC, self.d, "uC", optional=True),
+                                      _stream(stream)))
 
 
 def factor_many(grids, stream=None, **opts):
@@ -315,7 +341,8 @@ class Batch:
 
     def solve(self, f, u, g=None, stream=None, allow_notconv=False):
         reps = (SmpmReport * self.ntasks)()
-        st = lib().smpm_batch_solve(self.b, _ptr(f), _ptr(g), _ptr(u), reps, _stream(stream))
+        st = lib().smpm_batch_solve(self.b, _dev(f, self.f_len, "f"), _dev(g, self.g_len, "g", optional=True),
+                                    _dev(u, self.f_len, "u"), reps, _stream(stream))
         check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
         return [r.as_dict() for r in reps]
 
@@ -323,7 +350,8 @@ class Batch:
         cands = (ctypes.c_int * len(candidates))(*candidates)
         ms = (ctypes.c_double * len(candidates))()
         chosen = ctypes.c_int()
-        check(lib().smpm_batch_autotune(self.b, _ptr(f), _ptr(g), _ptr(u), _stream(stream), cands, len(candidates),
+        check(lib().smpm_batch_autotune(self.b, _dev(f, self.f_len, "f"), _dev(g, self.g_len, "g", optional=True),
+                                        _dev(u, self.f_len, "u"), _stream(stream), cands, len(candidates),
                                         ms, ctypes.byref(chosen)))
         return chosen.value, {c: ms[i] for i, c in enumerate(candidates)}
 
@@ -337,12 +365,15 @@ class Batch:
 
     def apply_schur(self, v, y, stream=None):
         """y_p = S_p v_p for every problem (packed slot vectors, float64)."""
-        check(lib().smpm_batch_apply_schur(self.b, _ptr(v), _ptr(y), _stream(stream)))
+        n = self.v_len()
+        check(lib().smpm_batch_apply_schur(self.b, _dev(v, n, "v"), _dev(y, n, "y"), _stream(stream)))
         return y
 
     def apply_schur32(self, v, y, stream=None):
         """As apply_schur with the FP32 factors (float32 vectors)."""
-        check(lib().smpm_batch_apply_schur32(self.b, _ptr(v), _ptr(y), _stream(stream)))
+        n = self.v_len()
+        check(lib().smpm_batch_apply_schur32(self.b, _dev(v, n, "v", "float32"), _dev(y, n, "y", "float32"),
+                                             _stream(stream)))
         return y
 
     def task_times(self):

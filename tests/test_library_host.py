@@ -43,11 +43,67 @@ def test_bad_arguments():
         g.factor_host_only()
     assert ei.value.status == B.SMPM_ENOINTERFACE
     g2 = B.Grid(2, 2, 5)
-    import torch
-    f = torch.zeros(g2.r, dtype=torch.float64)
+    f = np.zeros(g2.r)
+    st = B.lib().schur_solve(g2.h, f.ctypes.data, None, 0.0, 1, f.ctypes.data, None, None)
+    assert st == B.SMPM_ESTATE              # no factor yet (nothing is read)
     with pytest.raises(B.SmpmError) as ei:
-        g2.solve(f, f)                      # no factor yet
+        g2.solve_host(f, f)
     assert ei.value.status == B.SMPM_ESTATE
+
+
+class _FakeCudaTensor:
+    """Just enough of a CUDA tensor for the binding's argument checks.  Its
+    pointer is null: every case below is refused before the library call,
+    and the library would refuse a null vector with EINVAL anyway."""
+    is_cuda = True
+
+    def __init__(self, n, dtype="torch.float64", contiguous=True):
+        self.n, self.dtype, self.contiguous = n, dtype, contiguous
+
+    def is_contiguous(self):
+        return self.contiguous
+
+    def numel(self):
+        return self.n
+
+    def data_ptr(self):
+        return 0
+
+
+def test_binding_refuses_short_host_or_mistyped_buffers():
+    """The C ABI takes vector lengths from the handle, so the binding checks
+    every buffer's length, dtype, device and layout before the call."""
+    import torch
+    g = B.Grid(3, 2, 5)
+    T = _FakeCudaTensor
+    with pytest.raises(TypeError):
+        g.solve(torch.zeros(g.r, dtype=torch.float64), T(g.r))           # host tensor for a device entry
+    with pytest.raises(TypeError):
+        g.solve(np.zeros(g.r), T(g.r))                                    # NumPy array for a device entry
+    with pytest.raises(ValueError):
+        g.solve(T(g.r - 1), T(g.r))                                       # f one entry short
+    with pytest.raises(ValueError):
+        g.solve(T(3 * g.r), T(3 * g.r - 1), nrhs=3)                      # u short for 3 right-hand sides
+    with pytest.raises(ValueError):
+        g.solve(T(g.r), T(g.r), g=T(g.kp - 1))                            # g short
+    with pytest.raises(TypeError):
+        g.solve(T(g.r, "torch.float32"), T(g.r))                          # FP32 into an FP64 entry
+    with pytest.raises(TypeError):
+        g.solve(T(g.r, contiguous=False), T(g.r))
+    with pytest.raises(TypeError):
+        g.apply_schur32(T(g.kp), T(g.kp, "torch.float32"))                # FP64 into the FP32 operator
+    with pytest.raises(ValueError):
+        g.schur_rhs(T(g.kp), T(g.kp))                                     # b has r entries, not kp
+    with pytest.raises(ValueError):
+        g.recover(T(g.r), T(g.kp - 1), T(g.r))
+    with pytest.raises(ValueError):
+        g.null_vectors(None, None, T(g.d - 1))
+    with pytest.raises(ValueError):
+        g.solve_adjoint(T(g.r), T(g.r - 1))
+    with pytest.raises(ValueError):
+        g.solve_host(np.zeros(g.r), np.zeros(g.r - 1))
+    with pytest.raises(TypeError):
+        g.solve_host(np.zeros(g.r, dtype=np.float32), np.zeros(g.r))
 
 
 GRIDS = [(2, 2, 6, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (4, 3, 7, 1.0, 2.0), (5, 4, 4, 1.0, 1.0)]
