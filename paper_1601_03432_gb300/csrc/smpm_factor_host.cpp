@@ -24,10 +24,15 @@
 //
 // Identical element matrices (same face types; h is uniform per direction)
 // are computed once and copied: the stored factors are per element.
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -684,7 +689,29 @@ void diff_matrix(const std::vector<double>& x, std::vector<double>* D) {
   }
 }
 
-int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
+// The coarse solve is dense (Sec. 2): C, the bordered K, its LU, the leading
+// block of K^-1, H = C^+ and its adjoint hold up to 6 (d+1)^2 doubles on the
+// host at once.  Refused before any work when that exceeds the machine's
+// physical memory.
+static int coarse_memory_check(const Geometry& g, std::string* err) {
+  const double dd = static_cast<double>(g.d + 1);
+  const double need = 6.0 * dd * dd * sizeof(double);
+  const long pages = sysconf(_SC_PHYS_PAGES), page = sysconf(_SC_PAGE_SIZE);
+  const double have = static_cast<double>(pages) * static_cast<double>(page);
+  if (pages <= 0 || page <= 0 || need <= have) return SMPM_OK;
+  char msg[200];
+  std::snprintf(msg, sizeof msg,
+                "the dense coarse matrices (d = %lld interfaces) need %.3g GB of host memory, more than this "
+                "machine has (%.3g GB)", g.d, need * 1e-9, have * 1e-9);
+  *err = msg;
+  return SMPM_ENOMEM;
+}
+
+static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
+  {
+    const int st = coarse_memory_check(g, err);
+    if (st != SMPM_OK) return st;
+  }
   const int n = g.n, M = g.M;
   const double nn1 = n * (n - 1.0);
   f->tau_x = -o.tau_scale * nn1 / g.hx;
@@ -933,6 +960,22 @@ int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* 
     f->has_adjoint = true;
   }
   return SMPM_OK;
+}
+
+// The factor step throws nothing: it runs inside OpenMP regions (one grid
+// per thread in smpm_factor_many) and behind the C ABI.  A failed host
+// allocation -- e.g. the dense d x d coarse matrix of a very large grid --
+// or a container asked for more than it can hold becomes ENOMEM.
+int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
+  try {
+    return factor_host_body(g, o, f, err);
+  } catch (const std::bad_alloc&) {
+    *err = "host allocation failed in the factor step";
+  } catch (const std::exception& e) {
+    *err = std::string("factor step: ") + e.what();
+  }
+  *f = Factors();
+  return SMPM_ENOMEM;
 }
 
 }  // namespace smpm

@@ -23,7 +23,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -939,6 +941,22 @@ smpm_status fail(smpm_status s, const std::string& msg) {
   return s;
 }
 
+// No C++ exception crosses the C ABI: every entry point that returns a
+// status catches what the standard library throws (a failed host
+// allocation, e.g. the dense d x d coarse matrix of a very large grid, or a
+// container asked for more than it can hold) and reports it as ENOMEM.
+smpm_status host_exception() {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return fail(SMPM_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(SMPM_ENOMEM, std::string("host error: ") + e.what());
+  } catch (...) {
+    return fail(SMPM_ENOMEM, "unknown host error");
+  }
+}
+
 #define CU(call)                                                                                  \
   do {                                                                                            \
     cudaError_t e_ = (call);                                                                      \
@@ -1744,7 +1762,7 @@ void smpm_default_opts(smpm_opts* o) {
 
 const char* smpm_last_error(void) { return g_last_error.c_str(); }
 
-smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* out) {
+smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* out) try {
   if (!out) return fail(SMPM_EINVAL, "null handle pointer");
   *out = nullptr;
   if (mx < 1 || my < 1 || mx > 4096 || my > 4096 || n < 2 || n > kMaxN)
@@ -1765,9 +1783,11 @@ smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle*
   smpm_default_opts(&h->opts);
   *out = h;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d, long long* k, long long* nblack) {
+smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d, long long* k, long long* nblack) try {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   if (r) *r = h->g.r;
   if (kp) *kp = h->g.kp;
@@ -1779,9 +1799,11 @@ smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d,
     *nblack = c;
   }
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_node_coords(smpm_handle h, double* x, double* y) {
+smpm_status smpm_node_coords(smpm_handle h, double* x, double* y) try {
   if (!h || !x || !y) return fail(SMPM_EINVAL, "null argument");
   const Geometry& g = h->g;
   std::vector<double> xi, w;
@@ -1796,9 +1818,11 @@ smpm_status smpm_node_coords(smpm_handle h, double* x, double* y) {
       }
   }
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_node_mass(smpm_handle h, double* wq) {
+smpm_status smpm_node_mass(smpm_handle h, double* wq) try {
   if (!h || !wq) return fail(SMPM_EINVAL, "null argument");
   const Geometry& g = h->g;
   std::vector<double> xi, w;
@@ -1807,6 +1831,8 @@ smpm_status smpm_node_mass(smpm_handle h, double* wq) {
     for (int b = 0; b < g.n; ++b)
       for (int a = 0; a < g.n; ++a) wq[e * g.nn + b * g.n + a] = w[a] * w[b] * g.hx * g.hy / 4.0;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 }  // extern "C"
@@ -1839,7 +1865,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st);
 
 extern "C" {
 
-smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
+smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) try {
   smpm_opts opts;
   smpm_status cs = check_factor_opts(h, o, &opts);
   if (cs != SMPM_OK) return cs;
@@ -1851,9 +1877,11 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) {
   int rc = factor_host(h->g, opts, &h->f, &err);
   if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
   return factor_device(h, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* o, void* stream) {
+smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* o, void* stream) try {
   if (!hs || count < 1) return fail(SMPM_EINVAL, "bad arguments");
   smpm_opts opts;
   for (int i = 0; i < count; ++i) {
@@ -1886,6 +1914,8 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
     if (s != SMPM_OK) return s;
   }
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 }  // extern "C"
@@ -2079,7 +2109,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
 extern "C" {
 
 smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double tol, int nrhs, double* u,
-                        smpm_report* rep, void* stream) {
+                        smpm_report* rep, void* stream) try {
   if (!h || !f || !u || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
   if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
   double t = tol > 0 ? tol : h->opts.tol;
@@ -2092,10 +2122,12 @@ smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double
     else if (s != SMPM_OK) return s;
   }
   return worst;
+} catch (...) {
+  return host_exception();
 }
 
 smpm_status schur_solve_adjoint(smpm_handle h, const double* gbar_u, double tol, int nrhs, double* gbar_f,
-                                double* gbar_g, smpm_report* rep, void* stream) {
+                                double* gbar_g, smpm_report* rep, void* stream) try {
   if (!h || !gbar_u || !gbar_f || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
   if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
   if (!h->f.has_adjoint) return fail(SMPM_ESTATE, "schur_factor was called without SMPM_FLAG_ADJOINT");
@@ -2109,10 +2141,12 @@ smpm_status schur_solve_adjoint(smpm_handle h, const double* gbar_u, double tol,
     else if (s != SMPM_OK) return s;
   }
   return worst;
+} catch (...) {
+  return host_exception();
 }
 
 smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, double tol, int nrhs, double* u,
-                             smpm_report* rep, void* stream) {
+                             smpm_report* rep, void* stream) try {
   if (!h || !f || !u || nrhs < 1) return fail(SMPM_EINVAL, "bad arguments");
   if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called");
   cudaStream_t st = as_stream(stream);
@@ -2129,6 +2163,8 @@ smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, d
   CU(cudaMemcpyAsync(u, h->su, rn * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   return s;
+} catch (...) {
+  return host_exception();
 }
 
 #define NEED_FACTOR()                                                              \
@@ -2137,13 +2173,15 @@ smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, d
     if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called"); \
   } while (0)
 
-smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream) {
+smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream) try {
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   return launch_schur(h, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* stream) {
+smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* stream) try {
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
@@ -2156,21 +2194,27 @@ smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* st
     return SMPM_OK;
   }
   return launch_schur_stream<float>(h, h->dT32, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream) {
+smpm_status smpm_apply_precond(smpm_handle h, const double* v, double* t, void* stream) try {
   NEED_FACTOR();
   if (!v || !t) return fail(SMPM_EINVAL, "null vector");
   return launch_precond(h, v, t, nullptr, nullptr, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, void* stream) {
+smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, void* stream) try {
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   return launch_precond(h, v, h->wt, y, h->wc, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream) {
+smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream) try {
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   cudaStream_t st = as_stream(stream);
@@ -2178,9 +2222,11 @@ smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void
   if ((s = launch_zt(h, v, h->wc, st))) return s;
   if ((s = launch_coarse(h, h->wc, h->wchat, st))) return s;
   return launch_defl(h, v, h->wchat, -1, y, st);
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream) {
+smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream) try {
   NEED_FACTOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   cudaStream_t st = as_stream(stream);
@@ -2191,9 +2237,11 @@ smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, vo
   k_assemble<<<blocks_for(h->g.kp, kSlotsPerBlock), kSlotsPerBlock, 0, st>>>(h->dg, v, h->wchat, nullptr, y);
   CHECK_LAUNCH();
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream) {
+smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream) try {
   NEED_FACTOR();
   if (!b || !bS) return fail(SMPM_EINVAL, "null vector");
   cudaStream_t st = as_stream(stream);
@@ -2201,35 +2249,43 @@ smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* str
   k_schur_rhs<<<(unsigned)h->g.nel, kElemThreads, elem_smem(h->g.n), st>>>(h->dg, h->dfdx, h->dfdy, h->dD, b, bS);
   CHECK_LAUNCH();
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_recover(smpm_handle h, const double* b, const double* x, double* u, void* stream) {
+smpm_status smpm_recover(smpm_handle h, const double* b, const double* x, double* u, void* stream) try {
   NEED_FACTOR();
   if (!b || !x || !u) return fail(SMPM_EINVAL, "null vector");
   k_recover<<<(unsigned)h->g.nel, kElemThreads, elem_smem(h->g.n), as_stream(stream)>>>(h->dg, h->dfdx, h->dfdy, b,
                                                                                         x, u);
   CHECK_LAUNCH();
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_null_vectors(smpm_handle h, double* uL, double* uS, double* uC, void* stream) {
+smpm_status smpm_null_vectors(smpm_handle h, double* uL, double* uS, double* uC, void* stream) try {
   NEED_FACTOR();
   cudaStream_t st = as_stream(stream);
   if (uL) CU(cudaMemcpyAsync(uL, h->duL, h->g.r * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (uS) CU(cudaMemcpyAsync(uS, h->duS, h->g.kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (uC) CU(cudaMemcpyAsync(uC, h->duC, h->g.d * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_coarse_matrix(smpm_handle h, double* C) {
+smpm_status smpm_coarse_matrix(smpm_handle h, double* C) try {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   if (h->f.C.empty()) return fail(SMPM_ESTATE, "no factors: call schur_factor or smpm_factor_host_only");
   if (!C) return fail(SMPM_EINVAL, "null pointer");
   std::memcpy(C, h->f.C.data(), h->f.C.size() * sizeof(double));
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o) {
+smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o) try {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   smpm_opts opts;
   smpm_default_opts(&opts);
@@ -2242,9 +2298,11 @@ smpm_status smpm_factor_host_only(smpm_handle h, const smpm_opts* o) {
   if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
   h->f = std::move(f);
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long long count, long long* len) {
+smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long long count, long long* len) try {
   if (!h || !name) return fail(SMPM_EINVAL, "null argument");
   const Factors& f = h->f;
   std::vector<double> tmp;
@@ -2281,6 +2339,8 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
   if (count != (long long)src->size()) return fail(SMPM_EINVAL, "count does not match the factor length");
   std::memcpy(out, src->data(), src->size() * sizeof(double));
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 void smpm_destroy(smpm_handle h) {
@@ -2291,7 +2351,7 @@ void smpm_destroy(smpm_handle h) {
 
 
 smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs, int team_size, int use_graph,
-                              int precision, smpm_batch* out) {
+                              int precision, smpm_batch* out) try {
   if (!hs || count < 1 || !nrhs || !out || precision < -1 || precision > 1)
     return fail(SMPM_EINVAL, "bad arguments");
   *out = nullptr;
@@ -2392,10 +2452,12 @@ smpm_status smpm_batch_create(const smpm_handle* hs, int count, const int* nrhs,
   }
   *out = b;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 smpm_status smpm_batch_info(smpm_batch b, long long* f_len, long long* g_len, long long* ntasks, int* team_size,
-                            int* nteams, double* last_ms) {
+                            int* nteams, double* last_ms) try {
   if (!b) return fail(SMPM_EINVAL, "null batch");
   if (f_len) *f_len = b->f_len;
   if (g_len) *g_len = b->g_len;
@@ -2404,10 +2466,12 @@ smpm_status smpm_batch_info(smpm_batch b, long long* f_len, long long* g_len, lo
   if (nteams) *nteams = b->nteams;
   if (last_ms) *last_ms = b->last_ms;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, double* u, smpm_report* rep,
-                             void* stream) {
+                             void* stream) try {
   if (!b || !f || !u) return fail(SMPM_EINVAL, "bad arguments");
   cudaStream_t us = as_stream(stream);
   b->hio->f = f;
@@ -2472,10 +2536,12 @@ smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, dou
     }
   if (worst != SMPM_OK) return fail(worst, "a batched solve did not converge");
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
 smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, double* u, void* stream,
-                                const int* candidates, int ncand, double* ms_out, int* chosen) {
+                                const int* candidates, int ncand, double* ms_out, int* chosen) try {
   if (!b || !f || !u || !candidates || ncand < 1) return fail(SMPM_EINVAL, "bad arguments");
   int best = -1;
   double best_ms = 1e300;
@@ -2497,9 +2563,11 @@ smpm_status smpm_batch_autotune(smpm_batch b, const double* f, const double* g, 
   if (st != SMPM_OK) return st;
   if (chosen) *chosen = best;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, double* end_ms) {
+smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, double* end_ms) try {
   if (!b) return fail(SMPM_EINVAL, "null batch");
   unsigned long long t0 = ~0ull;
   for (long long i = 0; i < b->ntasks; ++i) t0 = std::min(t0, b->hrep[i].t_begin);
@@ -2512,23 +2580,31 @@ smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, dou
       if (end_ms) end_ms[i] = (double)(t.t_end - t0) * 1e-6;
     }
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind) {
+smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind) try {
   if (!b || kind < 0 || kind > 1) return fail(SMPM_EINVAL, "bad arguments");
   b->apply_kernel = kind;
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_batch_apply_schur(smpm_batch b, const double* v, double* y, void* stream) {
+smpm_status smpm_batch_apply_schur(smpm_batch b, const double* v, double* y, void* stream) try {
   if (!b || !v || !y) return fail(SMPM_EINVAL, "bad arguments");
   return batch_apply<double>(b, b->dtab64, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
-smpm_status smpm_batch_apply_schur32(smpm_batch b, const float* v, float* y, void* stream) {
+smpm_status smpm_batch_apply_schur32(smpm_batch b, const float* v, float* y, void* stream) try {
   if (!b || !v || !y) return fail(SMPM_EINVAL, "bad arguments");
   if (!b->dtab32) return fail(SMPM_ESTATE, "not every handle of the batch was factored with precision 1");
   return batch_apply<float>(b, b->dtab32, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
 }
 
 void smpm_batch_destroy(smpm_batch b) {

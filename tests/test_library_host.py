@@ -51,6 +51,25 @@ def test_bad_arguments():
     assert ei.value.status == B.SMPM_ESTATE
 
 
+
+def test_coarse_step_beyond_host_memory_is_refused_before_any_work():
+    """A 4096 x 4096 grid has d = 33,546,240 interfaces: its dense coarse
+    matrices (about 6 d^2 doubles) exceed any host, and the factor step says
+    so with ENOMEM at once instead of allocating the element factors first."""
+    import time
+    g = B.Grid(4096, 4096, 2)
+    assert g.d == 2 * 4096 * 4095
+    t0 = time.perf_counter()
+    with pytest.raises(B.SmpmError) as ei:
+        g.factor_host_only()
+    assert ei.value.status == B.SMPM_ENOMEM
+    assert "coarse" in str(ei.value)
+    with pytest.raises(B.SmpmError) as ei:
+        B.factor_many([B.Grid(3, 2, 4), g])
+    assert ei.value.status == B.SMPM_ENOMEM
+    assert time.perf_counter() - t0 < 5.0
+
+
 class _FakeCudaTensor:
     """Just enough of a CUDA tensor for the binding's argument checks.  Its
     pointer is null: every case below is refused before the library call,
