@@ -26,6 +26,42 @@ def test_gmres_against_dense_solve():
     assert info["iterations"] <= n and info["true_relres"] < 1e-12
 
 
+def test_gmres_is_the_minimal_residual_method():
+    """GMRES's defining property: after j steps from x0 = 0 the residual is
+    min over x in K_j(A, b) of ||b - A x||.  Checked step by step against a
+    least-squares solve on an orthonormal basis of the Krylov space (a
+    different route to the same minimum), plus the properties that follow:
+    a non-increasing history, a returned iterate whose true residual is that
+    minimum, and termination in 3 steps when A has 3 distinct eigenvalues
+    (minimal polynomial of degree 3)."""
+    rng = np.random.default_rng(8)
+    n = 30
+    A = np.eye(n) * 2 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    _, info = gmres(lambda v: A @ v, b, 1e-14, restart=n, maxit=12)
+    K = np.empty((n, 12))
+    k = b / np.linalg.norm(b)
+    for j in range(12):
+        K[:, j] = k
+        k = A @ k
+        k /= np.linalg.norm(k)
+    for j in range(1, 13):
+        Qj, _ = np.linalg.qr(K[:, :j])
+        c, *_ = np.linalg.lstsq(A @ Qj, b, rcond=None)
+        rmin = np.linalg.norm(b - A @ (Qj @ c)) / np.linalg.norm(b)
+        assert abs(info["history"][j - 1] - rmin) <= 1e-10 + 1e-8 * rmin, (j, info["history"][j - 1], rmin)
+    h = info["history"]
+    assert all(h[i + 1] <= h[i] * (1 + 1e-12) for i in range(len(h) - 1))
+    assert abs(info["true_relres"] - h[-1]) <= 1e-10 + 1e-8 * h[-1]   # the iterate attains the minimum
+    # three distinct eigenvalues, non-normal (a random similarity)
+    X = rng.standard_normal((n, n)) + np.sqrt(n) * np.eye(n)
+    D = np.repeat([1.0, 2.0, 3.5], [10, 10, 10])
+    A3 = X @ np.diag(D) @ np.linalg.inv(X)
+    x, info = gmres(lambda v: A3 @ v, b, 1e-9, restart=n, maxit=n)
+    assert info["converged"] and info["iterations"] <= 3, info["iterations"]
+    np.testing.assert_allclose(x, np.linalg.solve(A3, b), rtol=1e-7)
+
+
 @pytest.mark.parametrize("mx,my,n,Lx,Ly", [(2, 2, 8, 1.0, 1.0), (3, 2, 6, 1.5, 0.75), (4, 4, 5, 1.0, 1.0)])
 def test_algorithms_match_direct_solve(mx, my, n, Lx, Ly):
     g = SMPMGrid(mx, my, n, Lx, Ly)
