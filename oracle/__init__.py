@@ -30,6 +30,9 @@ adjoint  Reverse-mode derivative of u(f, g): the transposed bordered direct
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (closed forms, the Fig. 1 node list, polynomial exactness, spectral
 convergence, operator identities, agreement of Algorithms 1-3 with the direct
-solve; for the adjoint, brute-force transposition of the forward map, the
-inner-product identity and central differences).  No function is "parity unpinned".
+solve, GMRES's minimal-residual definition checked by least squares on the
+Krylov space; for the adjoint, brute-force transposition of the forward map,
+the inner-product identity and central differences).  Planted mistakes in the
+operator, the Schur and deflation objects, the algorithms, GMRES and the
+adjoint are each caught by one of those pins.  No function is "parity unpinned".
 """
