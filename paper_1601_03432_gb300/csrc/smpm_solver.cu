@@ -1,20 +1,35 @@
 // CUDA solve path and C ABI of the deflated Schur-complement method
 // (Joshi & Diamessis, Algorithms 1-3).  See include/smpm.h for the contract.
 //
-// One GMRES step of Algorithm 3 (x_1 := GMRES(P S M^-1, P b_S)) runs as:
-//   k_black   per black element: t = M^-1 v on its block (Fig. 2), in the
-//             reduced form a = G (p - X q), b = q - T_e a;
-//   k_white   per white element: y = S t; because M_b = S[block, block], the
-//             rows of S on white-owned slots reduce to y = v, so only the
-//             white elements' T_e products remain (each T_e is read once per
-//             step across the two kernels); also c = Z^T y per interface;
-//   k_coarse  c_hat = C^+ c with the precomputed regularised inverse;
-//   k_defl    w = y - (S Z) c_hat (Eq. projection1) fused with the first
-//             classical Gram-Schmidt pass h = V^T w;
-//   k_cgs2    w' = w - V h, h2 = V^T w' (re-orthogonalisation);
-//   k_cgs3    v_{j+1} = w' - V h2, ||v_{j+1}||, Givens update (FP64) and the
-//             convergence test on the rotated residual;
-//   k_scale   v_{j+1} /= ||v_{j+1}||.
+// A solve (schur_solve) is three cooperative, persistent launches on the
+// caller's stream; the host synchronises once, to read the report:
+//   k_pre    b <- b - u_L u_L^T b (Eq. regularize_poisson), b_S = B A^-1 b
+//            by fast-diagonalisation element solves and Robin flux pushes,
+//            b_S <- b_S - u_S u_S^T b_S (Eq. regularize_schur), Z^T b_S and
+//            the GMRES right-hand side P b_S (smpm_prepost.cuh);
+//   k_gmres  the whole restarted GMRES on P S M^-1 (smpm_gmres.cuh): five
+//            phases per Arnoldi step separated by grid barriers;
+//   k_post   x_S = Q M^-1 x_1 + Z C^+ Z^T b_S (Eq. deflated_schur), the
+//            recovery u = A^-1 (b - E x_S), the true Schur residual and the
+//            zero GLL-weighted mean (smpm_prepost.cuh).
+// Mixed precision replaces k_gmres by a fixed sequence of
+// (k_gmres<float>, k_refine) pairs (smpm_refine.cuh); the adjoint solve runs
+// the same kernels on the transposed factor set.
+//
+// Many grids and right-hand sides are solved in one launch by k_batch
+// (smpm_batch.cuh): teams of CTAs run the same bodies with team barriers.
+//
+// The single-operator entry points use small one-pass kernels:
+//   y = S v          k_schur_warpk (several warps per element, M <= 96),
+//                    k_schur_stream (bulk-copy ring, larger M), k_schur
+//                    (from global memory when one matrix exceeds the ring);
+//                    batched: k_schur_warp_batch, k_schur_stream_batch;
+//   S M^-1 and M^-1  k_black (block solves a = G (p - X q), b = q - T_e a),
+//                    k_white (white elements' T_e products, c = Z^T y);
+//   P and Q          k_zt (c = Z^T v), k_coarse (c_hat = C^+ c),
+//                    k_defl_dots, k_sub, k_assemble;
+//   b_S, recovery    k_schur_rhs, k_recover;
+//   allocation-free  k_deflate_noalloc.
 #include <cuda_runtime.h>
 
 #include <algorithm>
