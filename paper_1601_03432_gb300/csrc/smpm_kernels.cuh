@@ -1,12 +1,13 @@
-// Device kernels of the deflated Schur-complement solve (sm_103a).
+// Device geometry and small helpers shared by the kernels of the deflated
+// Schur-complement solve (sm_103a): neighbour and interface lookups, warp
+// sums and the element GEMVs.
 //
 // Vectors live in two layouts: node vectors (element-major, n*n nodes per
 // element, x index fastest) and padded slot vectors (4n slots per element,
 // faces W,E,S,N, face node t increasing along the face; slots on physical
-// boundary faces are kept at zero).  Every per-element kernel runs one CTA per
-// element (or per checkerboard block) and stages the element's small vectors
-// in shared memory; the element matrices are stored column-major and read
-// once, coalesced across the threads that own consecutive rows.
+// boundary faces are kept at zero).  Element matrices are stored
+// column-major, so the threads (or lanes) that own consecutive rows read
+// each column coalesced.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
