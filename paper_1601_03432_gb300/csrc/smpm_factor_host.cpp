@@ -369,29 +369,60 @@ void element_T(const Ctx& c, int e, double* T) {
 }
 
 // ----------------------------------------------------- slot operators (host)
+// Class representatives.  Elements with the same face-type mask hold
+// identical T_e, and black blocks with the same key (own mask, then the four
+// neighbours' masks) identical G_b and X_b: the factor step computes each
+// once and copies it.  The host operators below read the representative's
+// copy, which gives the same arithmetic from a cache-resident working set.
+struct ClassReps {
+  std::vector<long long> t;  // per element: element whose T_e it reads
+  std::vector<long long> b;  // per black block: block whose G_b, X_b it reads
+};
+
+ClassReps class_reps(const Geometry& g, const std::vector<int>& black) {
+  ClassReps c;
+  c.t.resize(g.nel);
+  std::map<int, long long> first_t;
+  for (long long e = 0; e < g.nel; ++e) c.t[e] = first_t.emplace(g.mask(static_cast<int>(e)), e).first->second;
+  c.b.resize(black.size());
+  std::map<long long, long long> first_b;
+  for (size_t ib = 0; ib < black.size(); ++ib) {
+    const int e = black[ib];
+    long long key = g.mask(e);
+    for (int F = 0; F < 4; ++F) {
+      const int e2 = g.neighbour(e, F);
+      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
+    }
+    c.b[ib] = first_b.emplace(key, static_cast<long long>(ib)).first->second;
+  }
+  return c;
+}
+
 // out = S^T y on padded slot vectors: out_e = y_e + T_e^T yhat_e, yhat_e the
-// neighbours' slots facing e.
-void apply_ST(const Geometry& g, const Factors& f, const double* y, double* out) {
+// neighbours' slots facing e (T_e read row by row).
+void apply_ST(const Geometry& g, const Factors& f, const ClassReps& cr, const double* y, double* out) {
   const int n = g.n, M = g.M;
 #pragma omp parallel for schedule(static)
   for (long long e = 0; e < g.nel; ++e) {
-    double yh[4 * kMaxN];
+    double yh[4 * kMaxN], acc[4 * kMaxN];
     for (int F = 0; F < 4; ++F) {
       int e2 = g.neighbour(static_cast<int>(e), F);
       for (int t = 0; t < n; ++t) yh[F * n + t] = e2 >= 0 ? y[e2 * M + opposite(F) * n + t] : 0.0;
     }
-    const double* T = f.T.data() + static_cast<size_t>(e) * M * M;
-    for (int col = 0; col < M; ++col) {
-      double s = y[e * M + col];
-      for (int row = 0; row < M; ++row) s += T[row * M + col] * yh[row];
-      out[e * M + col] = s;
+    const double* T = f.T.data() + static_cast<size_t>(cr.t[e]) * M * M;
+    for (int col = 0; col < M; ++col) acc[col] = y[e * M + col];
+    for (int row = 0; row < M; ++row) {
+      const double yr = yh[row];
+      const double* Tr = T + static_cast<size_t>(row) * M;
+      for (int col = 0; col < M; ++col) acc[col] += Tr[col] * yr;
     }
+    for (int col = 0; col < M; ++col) out[e * M + col] = acc[col];
   }
 }
 
 // out = M^-T y, block by block: with M_b = [[I, X], [Y, I]],
 // M_b^T [a; b] = [p; q] gives a = G^T (p - Y^T q), b = q - X^T a.
-void apply_MinvT(const Geometry& g, const Factors& f, const double* y, double* out) {
+void apply_MinvT(const Geometry& g, const Factors& f, const ClassReps& cr, const double* y, double* out) {
   const int n = g.n, M = g.M;
   const long long nb = static_cast<long long>(f.black.size());
 #pragma omp parallel for schedule(static)
@@ -406,18 +437,20 @@ void apply_MinvT(const Geometry& g, const Factors& f, const double* y, double* o
         q[F * n + t] = nb4[F] >= 0 ? y[nb4[F] * M + opposite(F) * n + t] : 0.0;
       }
     }
-    const double* T = f.T.data() + static_cast<size_t>(e) * M * M;
-    const double* Gm = f.G.data() + static_cast<size_t>(ib) * M * M;
-    const double* X = f.X.data() + static_cast<size_t>(ib) * 4 * n * n;
-    for (int c2 = 0; c2 < M; ++c2) {
-      double s = p[c2];
-      for (int row = 0; row < M; ++row) s -= T[row * M + c2] * q[row];
-      r1[c2] = s;
+    const double* T = f.T.data() + static_cast<size_t>(cr.t[e]) * M * M;
+    const double* Gm = f.G.data() + static_cast<size_t>(cr.b[ib]) * M * M;
+    const double* X = f.X.data() + static_cast<size_t>(cr.b[ib]) * 4 * n * n;
+    for (int c2 = 0; c2 < M; ++c2) r1[c2] = p[c2];
+    for (int row = 0; row < M; ++row) {  // r1 = p - T^T q, rows of T in order
+      const double qr = q[row];
+      const double* Tr = T + static_cast<size_t>(row) * M;
+      for (int c2 = 0; c2 < M; ++c2) r1[c2] -= Tr[c2] * qr;
     }
-    for (int c2 = 0; c2 < M; ++c2) {
-      double s = 0;
-      for (int row = 0; row < M; ++row) s += Gm[row * M + c2] * r1[row];
-      a[c2] = s;
+    for (int c2 = 0; c2 < M; ++c2) a[c2] = 0.0;
+    for (int row = 0; row < M; ++row) {  // a = G^T r1
+      const double rr = r1[row];
+      const double* Gr = Gm + static_cast<size_t>(row) * M;
+      for (int c2 = 0; c2 < M; ++c2) a[c2] += Gr[c2] * rr;
     }
     for (int F = 0; F < 4; ++F) {
       for (int t = 0; t < n; ++t) {
@@ -447,9 +480,10 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   double an = std::sqrt(dot(a, a));
   for (auto& v : a) v /= an;
   std::vector<double> tmp(kp), tmp2(kp);
+  const ClassReps cr = class_reps(g, f->black);
   auto op = [&](const std::vector<double>& z, std::vector<double>& out) {
-    apply_MinvT(g, *f, z.data(), tmp.data());
-    apply_ST(g, *f, tmp.data(), tmp2.data());
+    apply_MinvT(g, *f, cr, z.data(), tmp.data());
+    apply_ST(g, *f, cr, tmp.data(), tmp2.data());
     double eta = z[kp], s = 0;
     for (size_t i = 0; i < kp; ++i) {
       out[i] = tmp2[i] + a[i] * eta;
@@ -477,23 +511,36 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
     for (; j < m && total < maxit; ++j) {
       op(V[j], w);
       // classical Gram-Schmidt, twice: h = V^T w in one pass over the
-      // basis, then w -= V h in one pass (both split over entries)
+      // basis, then w -= V h in one pass; both split into blocks of entries
+      // in which each basis vector is read contiguously
       for (int sweep = 0; sweep < 2; ++sweep) {
+        constexpr long long kBlk = 2048;
+        const long long nblk = (static_cast<long long>(N) + kBlk - 1) / kBlk;
         std::vector<double> h(j + 1, 0.0);
 #pragma omp parallel
         {
           std::vector<double> hp(j + 1, 0.0);
 #pragma omp for schedule(static) nowait
-          for (long long q = 0; q < (long long)N; ++q)
-            for (int i = 0; i <= j; ++i) hp[i] += V[i][q] * w[q];
+          for (long long b = 0; b < nblk; ++b) {
+            const long long q0 = b * kBlk, q1 = std::min<long long>(q0 + kBlk, static_cast<long long>(N));
+            for (int i = 0; i <= j; ++i) {
+              const double* Vi = V[i].data();
+              double acc = 0;
+              for (long long q = q0; q < q1; ++q) acc += Vi[q] * w[q];
+              hp[i] += acc;
+            }
+          }
 #pragma omp critical
           for (int i = 0; i <= j; ++i) h[i] += hp[i];
         }
 #pragma omp parallel for schedule(static)
-        for (long long q = 0; q < (long long)N; ++q) {
-          double acc = w[q];
-          for (int i = 0; i <= j; ++i) acc -= h[i] * V[i][q];
-          w[q] = acc;
+        for (long long b = 0; b < nblk; ++b) {
+          const long long q0 = b * kBlk, q1 = std::min<long long>(q0 + kBlk, static_cast<long long>(N));
+          for (int i = 0; i <= j; ++i) {
+            const double* Vi = V[i].data();
+            const double hi = h[i];
+            for (long long q = q0; q < q1; ++q) w[q] -= hi * Vi[q];
+          }
         }
         for (int i = 0; i <= j; ++i) H[i * m + j] = (sweep ? H[i * m + j] : 0.0) + h[i];
       }
@@ -533,7 +580,7 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
     return SMPM_ENOTCONV;
   }
   std::vector<double> y(kp);
-  apply_MinvT(g, *f, x.data(), y.data());
+  apply_MinvT(g, *f, cr, x.data(), y.data());
   double nrm = std::sqrt(dot(y, y));
   size_t imax = 0;
   for (size_t i = 0; i < kp; ++i)
