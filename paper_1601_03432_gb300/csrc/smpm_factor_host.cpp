@@ -371,9 +371,10 @@ void element_T(const Ctx& c, int e, double* T) {
 // ----------------------------------------------------- slot operators (host)
 // Class representatives.  Elements with the same face-type mask hold
 // identical T_e, and black blocks with the same key (own mask, then the four
-// neighbours' masks) identical G_b and X_b: the factor step computes each
-// once and copies it.  The host operators below read the representative's
-// copy, which gives the same arithmetic from a cache-resident working set.
+// neighbours' masks) identical G_b and X_b: the factor step computes T_e and
+// G_b once per class and copies them, and gathers X_b from the neighbours'
+// identical T.  The host operators below read the representative's copy,
+// which gives the same arithmetic from a cache-resident working set.
 struct ClassReps {
   std::vector<long long> t;  // per element: element whose T_e it reads
   std::vector<long long> b;  // per black block: block whose G_b, X_b it reads
