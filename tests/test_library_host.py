@@ -353,3 +353,37 @@ def test_coarse_inverse_accuracy_on_elongated_grid():
     r -= uC * (uC @ r)
     y = H @ r
     assert np.linalg.norm(C @ y - r) <= 1e-12 * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("mx,my,n", [(5, 4, 6), (8, 7, 5)])
+def test_factors_are_identical_within_a_class(mx, my, n):
+    """The host null-vector solve reads one representative per class: T_e of
+    elements with the same face-type mask, G_b and X_b of black blocks with
+    the same own and neighbour masks.  That is exact only if the stored
+    per-element copies are bitwise equal within a class."""
+    g = B.Grid(mx, my, n)
+    g.factor_host_only()
+    M = 4 * n
+    T = g.host_factor("T").reshape(mx * my, M, M)
+    Gb = g.host_factor("G").reshape(-1, M, M)
+    Xb = g.host_factor("X").reshape(-1, 4 * n * n)
+    black = g.host_factor("black").astype(int)
+
+    def nb(e, F):
+        ix, iy = e % mx, e // mx
+        return [e - 1 if ix > 0 else -1, e + 1 if ix < mx - 1 else -1,
+                e - mx if iy > 0 else -1, e + mx if iy < my - 1 else -1][F]
+
+    def mask(e):
+        return sum(1 << F for F in range(4) if nb(e, F) >= 0)
+
+    first = {}
+    for e in range(mx * my):
+        r = first.setdefault(mask(e), e)
+        assert np.array_equal(T[e], T[r])
+    firstb = {}
+    for ib, e in enumerate(black):
+        key = (mask(e),) + tuple(mask(nb(e, F)) if nb(e, F) >= 0 else 0 for F in range(4))
+        r = firstb.setdefault(key, ib)
+        assert np.array_equal(Gb[ib], Gb[r]) and np.array_equal(Xb[ib], Xb[r])
+    assert len(first) <= 9
