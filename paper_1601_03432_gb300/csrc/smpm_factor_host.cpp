@@ -470,11 +470,15 @@ double dot(const std::vector<double>& a, const std::vector<double>& b) {
   return s;
 }
 
-// Restarted right-preconditioned GMRES (MGS) on the bordered transposed
+// Restarted right-preconditioned GMRES (CGS2) on the bordered transposed
 // system for u_S, with the unit border vector a = B1 / ||B1||.  Unknown
 // z = [y (kp); eta]; operator K P z = [S^T (M^-T y) + a eta; a^T (M^-T y)].
 // The true residual is recomputed at every restart and the solve repeats
-// (iterative refinement) until it stops decreasing or reaches round-off.
+// (iterative refinement, three digits per cycle) until the residual is
+// below 1e-14 or stops decreasing.  Below 1e-12 a cycle takes at most 40
+// steps: there the null vector itself no longer improves (||S^T u_S|| is set
+// by the operator's round-off), and short cycles recompute the true residual
+// more often than long stagnating ones.
 int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   const size_t kp = static_cast<size_t>(g.kp), N = kp + 1;
   std::vector<double> a(f->B1);
@@ -492,7 +496,7 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
     }
     out[kp] = s;
   };
-  const int m = 300, maxit = 4000;
+  const int m = 300, m_tail = 40, maxit = 4000;
   std::vector<double> x(N, 0.0), r(N, 0.0), w(N);
   r[kp] = 1.0;  // b = [0; 1], x0 = 0
   std::vector<std::vector<double>> V;
@@ -501,49 +505,66 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   double beta = 1.0, best = 1e300;
   while (total < maxit) {
     beta = std::sqrt(dot(r, r));
-    if (beta <= 1e-16 || beta >= 0.5 * best) break;  // round-off reached or no progress
+    if (beta <= 1e-14 || beta >= 0.5 * best) break;  // accurate enough, or no progress
     best = beta;
     const double tol = 1e-3 * beta;                   // each cycle gains three digits
     V.assign(1, r);
     for (auto& v : V[0]) v /= beta;
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
+    const int mcyc = beta < 1e-12 ? m_tail : m;
     int j = 0;
-    for (; j < m && total < maxit; ++j) {
+    for (; j < mcyc && total < maxit; ++j) {
       op(V[j], w);
-      // classical Gram-Schmidt, twice: h = V^T w in one pass over the
-      // basis, then w -= V h in one pass; both split into blocks of entries
-      // in which each basis vector is read contiguously
-      for (int sweep = 0; sweep < 2; ++sweep) {
+      // classical Gram-Schmidt, twice: h1 = V^T w; w -= V h1 and, in the
+      // same pass over each block, h2 = V^T w; then w -= V h2.  Blocks of
+      // entries in which each basis vector is read contiguously; every
+      // thread sums its blocks in order, then the threads' sums are added.
+      {
         constexpr long long kBlk = 2048;
         const long long nblk = (static_cast<long long>(N) + kBlk - 1) / kBlk;
-        std::vector<double> h(j + 1, 0.0);
-#pragma omp parallel
-        {
-          std::vector<double> hp(j + 1, 0.0);
-#pragma omp for schedule(static) nowait
-          for (long long b = 0; b < nblk; ++b) {
-            const long long q0 = b * kBlk, q1 = std::min<long long>(q0 + kBlk, static_cast<long long>(N));
-            for (int i = 0; i <= j; ++i) {
-              const double* Vi = V[i].data();
-              double acc = 0;
-              for (long long q = q0; q < q1; ++q) acc += Vi[q] * w[q];
-              hp[i] += acc;
+        std::vector<double> h1(j + 1, 0.0), h2(j + 1, 0.0);
+        auto dots = [&](long long q0, long long q1, std::vector<double>& hp) {
+          for (int i = 0; i <= j; ++i) {  // four partial sums: independent add chains
+            const double* Vi = V[i].data();
+            double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            long long q = q0;
+            for (; q + 4 <= q1; q += 4) {
+              a0 += Vi[q] * w[q];
+              a1 += Vi[q + 1] * w[q + 1];
+              a2 += Vi[q + 2] * w[q + 2];
+              a3 += Vi[q + 3] * w[q + 3];
             }
+            for (; q < q1; ++q) a0 += Vi[q] * w[q];
+            hp[i] += (a0 + a1) + (a2 + a3);
           }
-#pragma omp critical
-          for (int i = 0; i <= j; ++i) h[i] += hp[i];
-        }
-#pragma omp parallel for schedule(static)
-        for (long long b = 0; b < nblk; ++b) {
-          const long long q0 = b * kBlk, q1 = std::min<long long>(q0 + kBlk, static_cast<long long>(N));
+        };
+        auto subtract = [&](long long q0, long long q1, const std::vector<double>& hv) {
           for (int i = 0; i <= j; ++i) {
             const double* Vi = V[i].data();
-            const double hi = h[i];
+            const double hi = hv[i];
             for (long long q = q0; q < q1; ++q) w[q] -= hi * Vi[q];
           }
+        };
+        for (int pass = 0; pass < 2; ++pass) {  // pass 0: h1; pass 1: subtract h1, h2
+          std::vector<double>& hout = pass ? h2 : h1;
+#pragma omp parallel
+          {
+            std::vector<double> hp(j + 1, 0.0);
+#pragma omp for schedule(static) nowait
+            for (long long b = 0; b < nblk; ++b) {
+              const long long q0 = b * kBlk, q1 = std::min<long long>(q0 + kBlk, static_cast<long long>(N));
+              if (pass) subtract(q0, q1, h1);
+              dots(q0, q1, hp);
+            }
+#pragma omp critical
+            for (int i = 0; i <= j; ++i) hout[i] += hp[i];
+          }
         }
-        for (int i = 0; i <= j; ++i) H[i * m + j] = (sweep ? H[i * m + j] : 0.0) + h[i];
+#pragma omp parallel for schedule(static)
+        for (long long b = 0; b < nblk; ++b)
+          subtract(b * kBlk, std::min<long long>((b + 1) * kBlk, static_cast<long long>(N)), h2);
+        for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
       }
       double hn = std::sqrt(dot(w, w));
       H[(j + 1) * m + j] = hn;
