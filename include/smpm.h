@@ -24,7 +24,12 @@
  * owns every buffer it passes.  Device pointers must be valid on the current
  * CUDA device for the given stream.  Calls on one handle are not thread-safe.
  * Every entry point returns an smpm_status; on error the output buffers are
- * unspecified unless stated.  smpm_last_error() gives a message.
+ * unspecified unless stated.  smpm_last_error() gives a message (per host
+ * thread).  No C++ exception leaves the library: a failed host allocation in
+ * any entry point is reported as SMPM_ENOMEM.  The library never checks the
+ * length of a caller's buffer (lengths come from the handle); a short buffer
+ * is undefined behaviour, so the Python binding checks lengths before the
+ * call.
  */
 #ifndef SMPM_H
 #define SMPM_H
