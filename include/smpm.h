@@ -80,6 +80,8 @@ typedef struct {
 #define SMPM_FLAG_ADJOINT 4        /* also build the transposed system for schur_solve_adjoint */
 #define SMPM_FLAG_WARP_ELEMS 8     /* one warp per block / element in the GMRES phases even when few
                                       are owned per CTA (the default from 4 per CTA; for testing) */
+#define SMPM_FLAG_ROBIN_LITERAL 16 /* Robin flux R = I + n.grad with identity weight p_F = 1 on every face
+                                      (the literal form of Sec. 1.2); robin_scale is then unused */
 
 /* Per-solve report, written by schur_solve when the pointer is non-null. */
 typedef struct {
@@ -192,7 +194,7 @@ smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, 
 smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream);
 /* y = Q v, Q = I - Z C^-1 Z^T S (Eq. projection2). */
 smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream);
-/* b_S = B A^-1 b (Algorithm 1, step 2); b: r, bS: kp. */
+/* b_S = B A^-1 b (right-hand side of Eq. schur_complement_system); b: r, bS: kp. */
 smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream);
 /* u = A^-1 (b - E x) (back-substitution of Sec. 1.3); b: r, x: kp, u: r. */
 smpm_status smpm_recover(smpm_handle h, const double* b, const double* x, double* u, void* stream);
@@ -226,10 +228,15 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
  * every GPU loading this library holds until exit.  Grids with more than
  * 32768 interfaces are rejected with SMPM_EINVAL.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
- * the one array: calls that overlap on the GPU (different streams, threads or
- * handles) race and must be serialised by the caller.  Asynchronous on
- * stream; a failed internal grid barrier (not expected) leaves y = NaN.
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process: it is not valid after cudaDeviceReset
+ * (or any other teardown of the device's primary context), so do not call
+ * this entry point again after one.  Every call shares the one array: calls
+ * that overlap on the GPU (different streams, threads or handles) race and
+ * must be serialised by the caller.  Asynchronous on stream: the status only
+ * covers the checks and the launch.  A failed internal grid barrier (not
+ * expected: every CTA is co-resident) still returns SMPM_OK and leaves y =
+ * NaN, so a caller that must detect it checks y.
  * Errors: EINVAL, ESTATE, ECUDA. */
 smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream);
 

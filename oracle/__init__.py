@@ -28,7 +28,10 @@ adjoint  Reverse-mode derivative of u(f, g): the transposed bordered direct
          vectors), with dl/df and dl/dg.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
-(closed forms, the Fig. 1 node list, polynomial exactness, spectral
+(closed forms, the Fig. 1 node list, the operator L entry by entry against a
+hand derivation for n = 2 and a derivation from Lagrange polynomials in
+physical coordinates for n <= 5 -- which pins the penalty and the Robin
+identity weight under both readings --, polynomial exactness, spectral
 convergence, operator identities, agreement of Algorithms 1-3 with the direct
 solve, GMRES's minimal-residual definition checked by least squares on the
 Krylov space; for the adjoint, brute-force transposition of the forward map,

@@ -11,19 +11,23 @@ from .gmres import gmres
 
 
 def project_rhs(sysm, b):
-    """Algorithm 1, step 1 (Eq. regularize_poisson): b <- b - u_L u_L^T b."""
+    """Projection of the right-hand side out of the left null space of L
+    (Eq. regularize_poisson, Sec. 1.4): b <- b - u_L u_L^T b."""
     return b - sysm.u_L * (sysm.u_L @ b)
 
 
 def schur_rhs_projected(sysm, b):
-    """Algorithm 1, steps 2-3 (Eq. regularize_schur): b_S = B A^-1 b, then
+    """Schur right-hand side of Eq. schur_complement_system, b_S = B A^-1 b,
+    projected out of the left null space of S (Eq. regularize_schur):
     b_S <- b_S - u_S (u_S^T b_S)."""
     bS = sysm.schur_rhs(b)
     return bS - sysm.u_S * (sysm.u_S @ bS)
 
 
 def algorithm1(sysm, b, tol=1e-10, restart=50, maxit=2000):
-    """Algorithm 1: Schur complement method with null-space projections."""
+    """Algorithm 1 (Sec. 1.4): GMRES on the regularised Schur system
+    S x_S = b_S (Eqs. schur_complement_system, regularize_schur), then
+    u = A^-1 (b - E x_S) and the zero-mean normalisation."""
     g = sysm.grid
     b = project_rhs(sysm, b)
     bS = schur_rhs_projected(sysm, b)
@@ -49,14 +53,16 @@ def algorithm3(sysm, b, tol=1e-10, restart=50, maxit=2000):
     Eq. (deflated_schur):
         x_S = Z C\\(Z^T - u_C u_C^T Z^T) b_S + Q M^-1 GMRES(P S M^-1, P b_S)."""
     g = sysm.grid
-    b = project_rhs(sysm, b)                                   # step 1
-    bS = schur_rhs_projected(sysm, b)                          # steps 2-3
+    b = project_rhs(sysm, b)
+    bS = schur_rhs_projected(sysm, b)
+    # the deflated, right-preconditioned system P S M^-1 y = P b_S and the two
+    # terms of Eq. deflated_schur
     op = lambda v: sysm.apply_P(sysm.apply_S(sysm.apply_Minv(v)))
-    x1, info = gmres(op, sysm.apply_P(bS), tol, restart, maxit)  # step 4
-    x1 = sysm.apply_Q(sysm.apply_Minv(x1))                     # step 5
-    x2 = sysm.Z @ sysm.coarse_solve(sysm.Z.T @ bS)             # steps 6-7
-    x = x1 + x2                                                # step 8
-    u = sysm.recover(b, x)                                     # step 9
+    y, info = gmres(op, sysm.apply_P(bS), tol, restart, maxit)
+    x1 = sysm.apply_Q(sysm.apply_Minv(y))
+    x2 = sysm.Z @ sysm.coarse_solve(sysm.Z.T @ bS)
+    x = x1 + x2
+    u = sysm.recover(b, x)
     info["schur_relres"] = float(np.linalg.norm(bS - sysm.apply_S(x)) / max(np.linalg.norm(bS), 1e-300))
     return g.zero_mean(u), info
 

@@ -111,7 +111,7 @@ class SchurSystem:
         return v + self.E.T @ self.AT_solve(self.B.T @ v)
 
     def schur_rhs(self, b):
-        """b_S = B A^-1 b (Algorithm 1, step 2)."""
+        """b_S = B A^-1 b (right-hand side of Eq. schur_complement_system)."""
         return self.B @ self.A_solve(b)
 
     def recover(self, b, x):

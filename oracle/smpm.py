@@ -21,6 +21,8 @@ passage cited):
   default.  alpha = 1 makes the face terms equal the GLL-quadrature weak form
   divided by the nodal mass; p_F is the weight of the identity in R relative
   to the normal derivative, expressed in the element's own length scale.
+  The literal reading of R = I + n.grad (p_F = 1 on every face, whatever the
+  element size) is available with robin_literal=True.
 * Interface unknowns (Sec. 1.3): one slot per (element, interface face, face
   node), so each interface carries 2n slots (n on either side) and a corner node
   of an element appears in two slots.  Padded slot index e * 4n + F * n + t;
@@ -42,13 +44,14 @@ OPPOSITE = {W: E, E: W, S: N, N: S}
 class SMPMGrid:
     """Geometry, indexing and operators of one SMPM grid."""
 
-    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0, tau_scale=1.0, robin_scale=0.25):
+    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0, tau_scale=1.0, robin_scale=0.25, robin_literal=False):
         if mx < 1 or my < 1 or n < 2:
             raise ValueError("bad grid")
         self.mx, self.my, self.n = int(mx), int(my), int(n)
         self.Lx, self.Ly = float(Lx), float(Ly)
         self.tau_scale = float(tau_scale)
         self.robin_scale = float(robin_scale)
+        self.robin_literal = bool(robin_literal)
         self.x1d, self.w1d = gll_nodes_weights(self.n)
         self.D = diff_matrix(self.x1d)
         self.hx, self.hy = self.Lx / self.mx, self.Ly / self.my
@@ -87,7 +90,10 @@ class SMPMGrid:
         return -self.tau_scale * self.n * (self.n - 1) / h
 
     def robin_weight(self, F):
-        """Weight p_F of the identity in the Robin flux R (reading: beta n(n-1)/h_perp)."""
+        """Weight p_F of the identity in the Robin flux R of Sec. 1.2 (reading:
+        beta n(n-1)/h_perp; 1 under the literal reading R = I + n.grad)."""
+        if self.robin_literal:
+            return 1.0
         h = self.hx if F in (W, E) else self.hy
         return self.robin_scale * self.n * (self.n - 1) / h
 

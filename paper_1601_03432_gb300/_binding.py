@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmpm.so")
 
-FLAG_NO_SMEM_RESIDENCY, FLAG_STREAM_MATRICES, FLAG_ADJOINT, FLAG_WARP_ELEMS = 1, 2, 4, 8
+FLAG_NO_SMEM_RESIDENCY, FLAG_STREAM_MATRICES, FLAG_ADJOINT, FLAG_WARP_ELEMS, FLAG_ROBIN_LITERAL = 1, 2, 4, 8, 16
 
 SMPM_OK, SMPM_EINVAL, SMPM_ENOINTERFACE, SMPM_ENOMEM, SMPM_ECUDA, SMPM_ENOTCONV, SMPM_EBREAKDOWN, SMPM_ENAN, \
     SMPM_ESTATE, SMPM_ETIMEOUT = range(10)

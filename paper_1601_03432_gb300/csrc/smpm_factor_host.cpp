@@ -785,8 +785,11 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
   const double nn1 = n * (n - 1.0);
   f->tau_x = -o.tau_scale * nn1 / g.hx;
   f->tau_y = -o.tau_scale * nn1 / g.hy;
-  f->p_x = o.robin_scale * nn1 / g.hx;
-  f->p_y = o.robin_scale * nn1 / g.hy;
+  // identity weight of the Robin flux R = p_F I + n.grad: scaled by the
+  // element's own length, or 1 under the literal reading R = I + n.grad
+  const bool literal = (o.flags & SMPM_FLAG_ROBIN_LITERAL) != 0;
+  f->p_x = literal ? 1.0 : o.robin_scale * nn1 / g.hx;
+  f->p_y = literal ? 1.0 : o.robin_scale * nn1 / g.hy;
   gll(n, &f->x1d, &f->w1d);
   diff_matrix(f->x1d, &f->D);
 

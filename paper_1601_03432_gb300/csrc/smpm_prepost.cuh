@@ -4,7 +4,8 @@
 // CTA c owns the checkerboard blocks and white elements c, c+G, ..., and for
 // node-level work the elements e = c, c+G, ...
 //
-// k_pre (Algorithm 3 steps 1-3 and the GMRES right-hand side):
+// k_pre (the projections of Sec. 1.4, the Schur right-hand side of
+// Eq. schur_complement_system and the GMRES right-hand side P b_S):
 //   P1  b = f + tau g on the owned elements; u_L^T b accumulated
 //   P2  b <- b - u_L (u_L^T b); w = A_e^-1 b_e (fast diagonalisation); the
 //       Robin fluxes of w are pushed into the neighbours' facing slots
@@ -13,7 +14,8 @@
 //   P3  b_S <- b_S - u_S (u_S^T b_S) enters through Z^T b_S - (u_S^T b_S) Z^T u_S;
 //       c_hat_b = C^+ Z^T b_S (coarse rows)
 //   P4  owner entries: b_S projected in place, rhs = P b_S = b_S - S Z c_hat_b
-// k_post (steps 5-9 and the zero-mean normalisation):
+// k_post (the assembly of Eq. deflated_schur, the recovery u = A^-1 (b - E x)
+// and the zero-mean normalisation):
 //   Q1  t = M^-1 x on the owned blocks
 //   Q2  white elements: y = S t, c = Z^T y
 //   Q3  c_hat = C^+ c

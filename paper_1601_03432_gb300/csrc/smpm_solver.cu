@@ -193,7 +193,7 @@ __device__ __forceinline__ const double* fd_y(const DevGeo& g, const double* fdy
   return fdy + (size_t)cls * (2 * g.n * g.n + g.n);
 }
 
-// b_S = B A^-1 b (Algorithm 1 step 2): one CTA per element; the flux of
+// b_S = B A^-1 b (Eq. schur_complement_system): one CTA per element; the flux of
 // w = A_e^-1 b_e into the slot (nbr, opp F, t) is -tau_F (p_F w - n_F.grad w).
 // Slots on boundary faces are not written (the caller zeroes b_S).
 __global__ void k_schur_rhs(DevGeo g, const double* __restrict__ fdx, const double* __restrict__ fdy,
@@ -2656,7 +2656,9 @@ namespace {
 constexpr long long kNoAllocMaxInterfaces = 32768;  // d limit: 2 x 32768 doubles = 512 KiB
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxInterfaces + 32];
 
-// Device address of g_noalloc_scratch per device, taken once with that device current.
+// Device address of g_noalloc_scratch per device, taken once with that device
+// current and kept for the life of the process (it does not survive a
+// cudaDeviceReset, after which the module is loaded again).
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[256] = {nullptr};
 
@@ -2699,7 +2701,7 @@ __global__ void __launch_bounds__(256) k_deflate_noalloc(DevGeo g, const double*
 
 }  // namespace
 
-extern "C" smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream) {
+extern "C" smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream) try {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   if (h->g.d > kNoAllocMaxInterfaces)
     return fail(SMPM_EINVAL, "smpm_apply_deflation_noalloc supports at most " +
@@ -2733,4 +2735,6 @@ extern "C" smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double*
   CU(cudaLaunchCooperativeKernel((const void*)k_deflate_noalloc, dim3(sms), dim3(256), args, 0, st));
   CHECK_LAUNCH();
   return SMPM_OK;
+} catch (...) {
+  return host_exception();
 }

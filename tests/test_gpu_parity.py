@@ -345,3 +345,33 @@ def test_largest_polynomial_order(built, mx, my, n):
     b.apply_schur(dev(og.to_padded(v)), yb)
     assert rel(og.from_padded(host(yb)), ref) < 1e-12
     b.close()
+
+
+@pytest.mark.parametrize("mx,my,n,Lx,Ly", [(3, 2, 5, 1.5, 0.75), (4, 4, 6, 1.0, 1.0), (2, 3, 7, 1.0, 2.0)])
+def test_literal_robin_reading(built, mx, my, n, Lx, Ly):
+    """The literal Robin flux R = I + n.grad (Sec. 1.2; identity weight 1 on
+    every face) through the library flag, against the oracle built with the
+    same reading: the Schur apply, the null vectors and the whole solve."""
+    og = SMPMGrid(mx, my, n, Lx, Ly, robin_literal=True)
+    osys = SchurSystem(og)
+    lg = Grid(mx, my, n, Lx, Ly)
+    lg.factor(tol=1e-12, flags=B.FLAG_ROBIN_LITERAL)
+    rng = np.random.default_rng(41)
+    v = rng.standard_normal(og.k)
+    out = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    lg.apply_schur(dev(og.to_padded(v)), out)
+    assert rel(og.from_padded(host(out)), osys.apply_S(v)) < 1e-12
+    uS = torch.zeros(og.kp, dtype=torch.float64, device="cuda")
+    lg.null_vectors(None, uS, None)
+    got = og.from_padded(host(uS))
+    assert np.linalg.norm(got * np.sign(got @ osys.u_S) - osys.u_S) < 1e-12
+    f = inputs.white_noise(og.r, 42)
+    gslots = rng.standard_normal(og.kp)
+    b = og.rhs(f, gslots)
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, b)
+    uo, info = methods.algorithm3(osys, b, tol=1e-12, restart=50)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    rep = lg.solve(dev(f), u, g=dev(gslots), tol=1e-12)[0]
+    assert rep["converged"] == 1
+    assert rel(host(u), ud) < 1e-10
+    assert abs(rep["iterations"] - info["iterations"]) <= 1, (rep, info["iterations"])

@@ -1,11 +1,19 @@
 """Planted mistakes: each plausible error in the oracle's operator must make at
-least one of its pins fail.  The mistakes are planted in the oracle, on the CPU."""
+least one of its pins fail.  The mistakes are planted in the oracle, on the CPU.
+
+The identity weight p_F of the Robin flux is invisible to the operator
+identities (L 1 = 0, polynomial exactness and mass symmetry hold for any p_F),
+so its mistakes are checked against the entry-by-entry pins: the hand-derived
+n = 2 operators and the polynomial derivation of L."""
+import os
+
 import numpy as np
 import pytest
 
 import oracle.smpm as sm
 from oracle.smpm import SMPMGrid
 from paper_1601_03432_gb300 import inputs
+from smpm_by_polynomials import operator_by_polynomials, read_golden_n2, golden_matrix
 
 
 def pins_hold(mx=3, my=2, n=5, Lx=1.5, Ly=0.75):
@@ -104,3 +112,94 @@ def test_planted_mistake_is_caught(monkeypatch, name, fn):
     except Exception:
         ok = False
     assert not ok
+
+
+# ---- the Robin identity weight p_F -------------------------------------------
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "L_n2_two_element_grids.txt")
+
+
+def robin_pins_hold():
+    gold = read_golden_n2(GOLDEN)
+    for grid, (mx, my) in (("2x1", (2, 1)), ("1x2", (1, 2))):
+        for literal in (False, True):
+            hx, hy = 3.0 / mx, 2.0 / my
+            px, py = (1.0, 1.0) if literal else (0.5 / hx, 0.5 / hy)
+            Lg = golden_matrix(gold[grid], hx, hy, px, py)
+            Lo = SMPMGrid(mx, my, 2, 3.0, 2.0, robin_literal=literal).assemble_L().toarray()
+            if np.abs(Lo - Lg).max() > 1e-13 * np.abs(Lg).max():
+                return False
+    for mx, my, n in ((2, 2, 3), (2, 3, 4)):
+        Lp = operator_by_polynomials(mx, my, n, 1.5, 0.6)
+        Lo = SMPMGrid(mx, my, n, 1.5, 0.6).assemble_L().toarray()
+        if np.abs(Lo - Lp).max() > 1e-11 * np.abs(Lp).max():
+            return False
+    return True
+
+
+def _robin_h_swapped(self, F):
+    if self.robin_literal:
+        return 1.0
+    h = self.hy if F in (sm.W, sm.E) else self.hx     # mistake: h_perp taken along the face
+    return self.robin_scale * self.n * (self.n - 1) / h
+
+
+def _robin_hx_everywhere(self, F):
+    if self.robin_literal:
+        return 1.0
+    return self.robin_scale * self.n * (self.n - 1) / self.hx   # mistake: h_x on S/N faces too
+
+
+def _robin_no_quarter(self, F):
+    if self.robin_literal:
+        return 1.0
+    h = self.hx if F in (sm.W, sm.E) else self.hy
+    return self.n * (self.n - 1) / h                  # mistake: the factor 1/4 dropped
+
+
+def _robin_master_gradient(self, F):
+    if self.robin_literal:
+        return 1.0
+    h = self.hx if F in (sm.W, sm.E) else self.hy
+    return 2.0 / h                                    # mistake: 2/h (master-element scale) for n(n-1)/(4h)
+
+
+def _robin_literal_ignored(self, F):
+    h = self.hx if F in (sm.W, sm.E) else self.hy
+    return self.robin_scale * self.n * (self.n - 1) / h   # mistake: the literal reading not honoured
+
+
+def _robin_identity_on_own_side_only(self, F, t):
+    G = sm.OPPOSITE[F]
+    return -self.normal_derivative_row(G, t)          # mistake: neighbour's p_F u' term dropped
+
+
+ROBIN_MUTATIONS = [
+    ("robin_weight", _robin_h_swapped),
+    ("robin_weight", _robin_hx_everywhere),
+    ("robin_weight", _robin_no_quarter),
+    ("robin_weight", _robin_master_gradient),
+    ("robin_weight", _robin_literal_ignored),
+    ("neighbour_robin_row", _robin_identity_on_own_side_only),
+]
+
+
+def test_unmutated_robin_pins_hold():
+    assert robin_pins_hold()
+
+
+@pytest.mark.parametrize("name,fn", ROBIN_MUTATIONS, ids=[f.__name__ for _, f in ROBIN_MUTATIONS])
+def test_planted_robin_mistake_is_caught(monkeypatch, name, fn):
+    monkeypatch.setattr(sm.SMPMGrid, name, fn)
+    try:
+        ok = robin_pins_hold()
+    except Exception:
+        ok = False
+    assert not ok
+
+
+@pytest.mark.parametrize("fn", [_robin_h_swapped, _robin_no_quarter], ids=["h_swapped", "no_quarter"])
+def test_robin_mistakes_pass_the_operator_identities(monkeypatch, fn):
+    """Why the entry-by-entry pins are needed: these weight mistakes keep
+    L 1 = 0, polynomial exactness and mass symmetry."""
+    monkeypatch.setattr(sm.SMPMGrid, "robin_weight", fn)
+    assert pins_hold()

@@ -121,7 +121,7 @@ def _no_poisson_projection(sysm, b):
 
 
 def _algorithm3_without_coarse_part(sysm, b, tol=1e-10, restart=50, maxit=2000):
-    """Algorithm 3 with steps 6-7 (x2 = Z C^+ Z^T b_S) left out."""
+    """Algorithm 3 with the coarse term of Eq. deflated_schur (x2 = Z C^+ Z^T b_S) left out."""
     g = sysm.grid
     b = methods.project_rhs(sysm, b)
     bS = methods.schur_rhs_projected(sysm, b)

@@ -21,10 +21,12 @@ def built():
     assert torch.cuda.is_available()
 
 
+@pytest.mark.parametrize("opts", [{}, {"precision": 1}, {"precond": 1}, {"precond": 0}],
+                         ids=["fp64", "mixed", "block-jacobi", "no-precond"])
 @pytest.mark.parametrize("shape", [(4, 3, 6), (16, 16, 8), (9, 7, 5)])
-def test_matches_allocating_entry_point(built, shape):
+def test_matches_allocating_entry_point(built, shape, opts):
     g = Grid(*shape)
-    g.factor()
+    g.factor(**opts)
     rng = np.random.default_rng(31)
     for call in range(2):
         v = torch.as_tensor(rng.standard_normal(g.kp), dtype=torch.float64, device="cuda")
@@ -45,3 +47,11 @@ def test_rejects_grids_beyond_the_scratch(built):
         g.apply_deflation_noalloc(v, torch.empty_like(v))
     assert ei.value.status == B.SMPM_EINVAL
     assert "32768" in str(ei.value)
+
+
+def test_rejects_an_unfactored_handle(built):
+    g = Grid(4, 3, 6)
+    v = torch.zeros(g.kp, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.SmpmError) as ei:
+        g.apply_deflation_noalloc(v, torch.empty_like(v))
+    assert ei.value.status == B.SMPM_ESTATE
