@@ -32,7 +32,32 @@ sys.path.insert(0, ROOT)
 METRIC = "GMRES solves/s to 1e-10 residual (mixed vs FP64); Schur-apply HBM GB/s"
 WORKLOAD = {"mx": 16, "my": 16, "n": 16, "nrhs": 1, "tol": 1e-10, "restart": 50, "seed": 1000}
 WORKLOAD_NAME = "SMPM Poisson-Neumann, 16x16 elements, n=16 (r=65536), FP64, 1 Fourier RHS, GMRES(50) to 1e-10"
-L2_FLUSH_BYTES = 512 << 20          # > 4x the 126 MB L2
+L2_FLUSH_BYTES = 512 << 20          # written between timed steps: 3.9x the 135.5 MB L2 of a GB300
+CONFIG = {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": "fp64", "precond": "block-Jacobi + deflation"}
+GMRES_PROFILE = os.path.join(ROOT, "profiles", "k_gmres_16x16_n16_fp64.md")
+GMRES_SOURCES = [os.path.join(ROOT, "paper_1601_03432_gb300", "csrc", f) for f in ("smpm_gmres.cuh", "smpm_kernels.cuh")]
+
+
+def kernel_traffic():
+    """DRAM bytes (read + write) per k_gmres launch of the bench workload from
+    the kept ncu summary, or None when the kernel's sources changed since that
+    capture (the summary records their SHA-256)."""
+    import hashlib
+    import re
+    try:
+        text = open(GMRES_PROFILE).read()
+    except OSError:
+        return None, "no profile summary"
+    h = hashlib.sha256()
+    for f in GMRES_SOURCES:
+        h.update(open(f, "rb").read())
+    m_sha = re.search(r"sources sha256: ([0-9a-f]{16})", text)
+    m_tr = re.search(r"traffic per launch \(read \+ write\): ([\d,]+) bytes", text)
+    if not m_sha or not m_tr:
+        return None, "profile summary without traffic or source hash"
+    if m_sha.group(1) != h.hexdigest()[:16]:
+        return None, "kernel changed since the ncu capture"
+    return float(m_tr.group(1).replace(",", "")), "ncu capture " + os.path.basename(GMRES_PROFILE)
 
 
 def parse():
@@ -119,9 +144,10 @@ def rank_seed(seed, rank):
 
 
 # ----------------------------------------------------------- CPU oracle
-def oracle_solve_seconds(steps, warmup, seed):
-    """Time the oracle's Algorithm 3 on the bench workload in a fresh
-    single-threaded process; returns (per-solve seconds list, iterations)."""
+def oracle_solve_seconds(steps, warmup, seed, threads=1):
+    """Time the oracle's Algorithm 3 on the bench workload in a fresh process
+    with `threads` BLAS/OpenMP threads; returns (per-solve seconds list,
+    iterations)."""
     code = r"""
 import json, os, sys, time
 sys.path.insert(0, %r)
@@ -146,7 +172,7 @@ print(json.dumps({"times": times, "iterations": its}))
 """ % (ROOT, WORKLOAD, warmup, steps, warmup)
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -166,7 +192,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, **WORKLOAD, "precision": "fp64", "l2": "n/a (CPU)"},
+        "config": dict(CONFIG), "l2": "n/a (CPU)",
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "%d oracle Algorithm-3 solves of the bench workload (setup excluded), "
                                    "%d GMRES iterations each" % (len(times), its)},
@@ -343,13 +369,18 @@ def run_ours(args):
     # for as short a time as that takes
     batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and world == 1 else None
     config3 = run_config3(args, stream) if world == 1 else None
+    sweeps = run_sweeps() if world == 1 else None
 
+    traffic, traffic_src = kernel_traffic()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle runs in a fresh single-threaded process after the GPU timing
+        # the oracle runs in fresh processes after the GPU timing, with one
+        # BLAS thread and with all of the host's cores
         cpu = {}
         try:
-            cpu["times"], cpu["its"] = oracle_solve_seconds(2, 0, WORKLOAD["seed"])
+            cpu["times"], cpu["its"] = oracle_solve_seconds(2, 0, WORKLOAD["seed"], 1)
+            cpu["ncores"] = os.cpu_count() or 1
+            cpu["times_all"], _ = oracle_solve_seconds(2, 0, WORKLOAD["seed"], cpu["ncores"])
         except Exception as ex:  # reported, not fatal
             cpu["error"] = str(ex)
     if rank == 0:
@@ -357,25 +388,26 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, **W, "precision": "fp64", "precond": "block-Jacobi + deflation",
-                       "l2": "flushed between steps (512 MiB write, not timed)", "factor_s": round(factor_s, 3),
-                       "gmres_iterations": iters[-1], "wall_s": round(wall, 3),
-                       "device_ms": {"pre": round(pre_ms, 4), "gmres": round(tot_ms / len(reps_timed), 4),
-                                     "post": round(post_ms, 4)}},
+            "config": dict(CONFIG),
+            "l2": "flushed between steps (512 MiB write, not timed)",
+            "run": {"factor_s": round(factor_s, 3), "gmres_iterations": iters[-1], "wall_s": round(wall, 3),
+                    "device_ms": {"pre": round(pre_ms, 4), "gmres": round(tot_ms / len(reps_timed), 4),
+                                  "post": round(post_ms, 4)}},
             "mixed": mixed,
             "schur_apply": schur_apply,
             "batch": batch,
             "config3": config3,
+            "paper_sweeps": sweeps,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
                     "d2h_bytes_per_step": 8 * g.r, "max_abs_diff_vs_device": err_e2e},
             "gpu_launches": launches,
             # traffic: dram bytes read + written per k_gmres launch of this
-            # workload (L2 flushed before the step), from one ncu capture of
-            # the current kernel
+            # workload (L2 flushed before the step), from the kept ncu
+            # capture of the current kernel (null once the kernel changed)
             "roofline": {"kernel": "k_gmres (persistent GMRES, FP64)", "bound": "alu",
                          "achieved": achieved_tf, "peak": fp64_peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / fp64_peak_tf, "traffic": 16.420e6 + 4.9e3,
+                         "frac": achieved_tf / fp64_peak_tf, "traffic": traffic, "traffic_source": traffic_src,
                          "achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                          "hbm_frac": achieved_gbs / hbm_peak, "share_of_step": gm_share,
                          "ms_per_launch": tot_ms / len(reps_timed),
@@ -383,11 +415,15 @@ def run_ours(args):
                                  "working set L2-resident after the first iteration"},
         }
         if cpu is not None:
-            if "times" in cpu:
+            if "times_all" in cpu:
                 cv = len(cpu["times"]) / sum(cpu["times"])
-                line["cpu_baseline"] = {"value": cv, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                ca = len(cpu["times_all"]) / sum(cpu["times_all"])
+                best, cores = (ca, cpu["ncores"]) if ca > cv else (cv, 1)
+                line["cpu_baseline"] = {"value": best, "unit": "solves/s", "cores": cores, "kind": "oracle",
                                         "sample": "%d oracle Algorithm-3 solves of the bench workload (setup "
-                                                  "excluded), %d GMRES iterations" % (len(cpu["times"]), cpu["its"])}
+                                                  "excluded), %d GMRES iterations; the faster of 1 BLAS thread and "
+                                                  "%d" % (len(cpu["times"]), cpu["its"], cpu["ncores"]),
+                                        "one_thread": cv, "all_cores": {"value": ca, "threads": cpu["ncores"]}}
             else:
                 line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                         "sample": "failed: " + cpu.get("error", "")[:200]}
@@ -443,6 +479,38 @@ def run_config3(args, stream):
     for g in grids.values():
         g.close()
     return out
+
+
+# ------------------------------------------------------ paper's studies
+def run_sweeps():
+    """The paper's h- and p-refinement studies (Sec. 3.2, 3.3) through the GPU
+    path: GMRES iterations of Algorithms 1, 2, 3 on the lambda = 7 cosine
+    problem (unit square, homogeneous Neumann, tol 1e-10, GMRES(200)) for
+    m_x = m_y = 4..32 at n = 5 and n = 5..15 at m = 4, and for a nodal white
+    noise right-hand side in the p-study; the paper's own figures beside them."""
+    import torch
+    from paper_1601_03432_gb300 import Grid, inputs
+
+    def iters(m, n, f_of):
+        g = Grid(m, m, n)
+        x, y = g.node_coords()
+        f = torch.as_tensor(f_of(x, y, g.r), dtype=torch.float64, device="cuda")
+        out = []
+        for p in (0, 1, 2):
+            g.factor(tol=1e-10, restart=200, precond=p)
+            u = torch.zeros_like(f)
+            out.append(g.solve(f, u)[0]["iterations"])
+        g.close()
+        return out
+
+    cos = lambda x, y, r: inputs.paper_problem(x, y)[0]
+    noise = lambda x, y, r: inputs.white_noise(r, 77)
+    return {"algorithms": ["1 (S)", "2 (S M^-1)", "3 (P S M^-1)"],
+            "h_refinement_n5": {str(m): iters(m, 5, cos) for m in (4, 8, 16, 32)},
+            "p_refinement_m4": {str(n): iters(4, n, cos) for n in (5, 7, 9, 11, 13, 15)},
+            "p_refinement_m4_white_noise": {str(n): iters(4, n, noise) for n in (5, 9, 15)},
+            "paper": {"m32_n5": "Alg. 1 nearly 110, deflated just over 30 (Sec. 3.2)",
+                      "m4_p4_14": "all < 40, preconditioned/deflated < 15 (Sec. 3.3)"}}
 
 
 # ------------------------------------------------------------- batch

@@ -82,6 +82,12 @@ typedef struct {
                                       are owned per CTA (the default from 4 per CTA; for testing) */
 #define SMPM_FLAG_ROBIN_LITERAL 16 /* Robin flux R = I + n.grad with identity weight p_F = 1 on every face
                                       (the literal form of Sec. 1.2); robin_scale is then unused */
+#define SMPM_FLAG_NO_LOCKSTEP 32    /* solve several right-hand sides one after another instead of in
+                                      lockstep (for testing) */
+#define SMPM_FLAG_OPERATOR_ONLY 64  /* schur_factor builds only the element factors T_e of S (no block-
+                                      Jacobi, coarse or null-space factors): smpm_apply_schur and
+                                      smpm_apply_schur32 work, every other call returns ESTATE.  For
+                                      applying S on grids whose dense coarse step would not fit */
 
 /* Per-solve report, written by schur_solve when the pointer is non-null. */
 typedef struct {
@@ -146,8 +152,16 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
  *   tol <= 0 takes opts.tol.  rep (host, nrhs entries) may be null.
  * The right-hand side b = f + tau g is projected out of u_L (Eq.
  * regularize_poisson) and b_S out of u_S (Eq. regularize_schur).
+ * With nrhs > 1, FP64 and block-Jacobi (precond 1 or 2), the right-hand
+ * sides are solved in lockstep, up to 16 at a time: their Arnoldi processes
+ * advance together in one launch, so each step reads the operator matrices
+ * once for all of them (each element product is a small dense GEMM); every
+ * column keeps its own basis, Givens rotations, convergence and restarts,
+ * and its report is its own.  SMPM_FLAG_NO_LOCKSTEP solves them one after
+ * another instead.
  * Errors: EINVAL, ESTATE (no factor), ENOTCONV (u holds the last iterate),
- * ENAN, ECUDA. */
+ * EBREAKDOWN (Arnoldi breakdown before tol; u assembled as for ENOTCONV),
+ * ENAN, ETIMEOUT, ECUDA. */
 smpm_status schur_solve(smpm_handle h, const double* f, const double* g, double tol,
                         int nrhs, double* u, smpm_report* rep, void* stream);
 
@@ -239,6 +253,15 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
  * NaN, so a caller that must detect it checks y.
  * Errors: EINVAL, ESTATE, ECUDA. */
 smpm_status smpm_apply_deflation_noalloc(smpm_handle h, const double* v, double* y, void* stream);
+
+/* Testing hook for the failure path of the device-side waits.  Every grid
+ * or team barrier of the solve kernels polls at most `spins` times (default
+ * 2^28, restored by spins <= 0) before it sets the kernel's error flag and
+ * unwinds; the solve then returns SMPM_ETIMEOUT with no kernel left waiting,
+ * and the context stays usable.  A small value makes real waits run out.
+ * Applies to the current device; call it between solves (it synchronises
+ * with the device like cudaMemcpyToSymbol).  Errors: ECUDA. */
+smpm_status smpm_set_barrier_spin_limit(long long spins);
 
 /* ---- batched solves: many right-hand sides of many independent grids ----
  * One persistent cooperative launch runs every right-hand side of every

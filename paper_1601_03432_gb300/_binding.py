@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmpm.so")
 
 FLAG_NO_SMEM_RESIDENCY, FLAG_STREAM_MATRICES, FLAG_ADJOINT, FLAG_WARP_ELEMS, FLAG_ROBIN_LITERAL = 1, 2, 4, 8, 16
+FLAG_NO_LOCKSTEP, FLAG_OPERATOR_ONLY = 32, 64
 
 SMPM_OK, SMPM_EINVAL, SMPM_ENOINTERFACE, SMPM_ENOMEM, SMPM_ECUDA, SMPM_ENOTCONV, SMPM_EBREAKDOWN, SMPM_ENAN, \
     SMPM_ESTATE, SMPM_ETIMEOUT = range(10)
@@ -29,7 +30,7 @@ EXPORTS = [
     "smpm_apply_deflation_noalloc", "smpm_apply_schur32", "schur_solve_adjoint",
     "smpm_factor_many", "smpm_batch_create", "smpm_batch_info", "smpm_batch_solve", "smpm_batch_autotune", "smpm_batch_destroy",
     "smpm_batch_task_times", "smpm_batch_apply_schur", "smpm_batch_apply_schur32",
-    "smpm_batch_set_apply_kernel",
+    "smpm_batch_set_apply_kernel", "smpm_set_barrier_spin_limit",
 ]
 
 
@@ -98,6 +99,7 @@ def lib():
         L.smpm_batch_apply_schur.argtypes = [P, P, P, P]
         L.smpm_batch_apply_schur32.argtypes = [P, P, P, P]
         L.smpm_batch_set_apply_kernel.argtypes = [P, I]
+        L.smpm_set_barrier_spin_limit.argtypes = [LL]
         L.smpm_batch_destroy.argtypes = [P]
         L.smpm_batch_destroy.restype = None
         L.smpm_last_error.argtypes = []
@@ -224,13 +226,15 @@ class Grid:
         check(lib().smpm_coarse_matrix(self.h, C.ctypes.data))
         return C
 
-    def solve(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
-        """schur_solve on device tensors (float64, contiguous); returns the reports."""
+    def solve(self, f, u, g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False, allow=()):
+        """schur_solve on device tensors (float64, contiguous); returns the
+        reports.  Statuses in `allow` (and ENOTCONV with allow_notconv) are
+        returned in each report's "status" instead of raised."""
         reps = (SmpmReport * nrhs)()
         st = lib().schur_solve(self.h, _dev(f, self.r * nrhs, "f"), _dev(g, self.kp * nrhs, "g", optional=True),
                                float(tol), nrhs, _dev(u, self.r * nrhs, "u"), reps, _stream(stream))
-        check(st, allow=(SMPM_ENOTCONV,) if allow_notconv else ())
-        return [r.as_dict() for r in reps]
+        check(st, allow=tuple(allow) + ((SMPM_ENOTCONV,) if allow_notconv else ()))
+        return [dict(r.as_dict(), status=st) for r in reps]
 
     def solve_adjoint(self, gbar_u, gbar_f, gbar_g=None, tol=0.0, nrhs=1, stream=None, allow_notconv=False):
         """schur_solve_adjoint on device tensors: dl/df (and dl/dg) from dl/du;
@@ -293,6 +297,12 @@ class Grid:
         check(lib().smpm_null_vectors(self.h, _dev(uL, self.r, "uL", optional=True),
                                       _dev(uS, self.kp, "uS", optional=True), _dev(uC, self.d, "uC", optional=True),
                                       _stream(stream)))
+
+
+def set_barrier_spin_limit(spins):
+    """smpm_set_barrier_spin_limit: polls of every device-side barrier wait
+    before it times out (spins <= 0 restores the default); a testing hook."""
+    check(lib().smpm_set_barrier_spin_limit(int(spins)))
 
 
 def factor_many(grids, stream=None, **opts):

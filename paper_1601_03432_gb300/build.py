@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmpm.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["smpm_solver.cu", "smpm_factor_host.cpp"]
-HEADERS = ["smpm_internal.h", "smpm_kernels.cuh"]
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-I", os.path.join(ROOT, "include")]
 

@@ -37,7 +37,7 @@ struct TaskReport {
   double gmres_num, gmres_den;  // relres = num / den
   double res2, bsn2;            // ||b_S - S x_S||^2, ||b_S||^2
   unsigned long long t_begin, t_end;  // global timer (ns) at the task's start and end on its team's first CTA
-  int team, pad;
+  int team, breakdown;  // breakdown: an FP64 solve ended on an Arnoldi breakdown before tol
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
       if (T.precision == 0) {
         r.iterations = gs->j;
         r.restarts = gs->scal[7] > 1 ? (int)gs->scal[7] - 1 : 0;
-        r.converged = (gs->converged || gs->beta0 == 0.0 || gs->breakdown) ? 1 : 0;
+        r.converged = (gs->converged || gs->beta0 == 0.0) ? 1 : 0;
+        r.breakdown = gs->breakdown;
         r.gmres_num = gs->resid;
         r.gmres_den = gs->beta0;
       } else {

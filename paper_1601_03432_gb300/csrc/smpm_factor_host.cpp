@@ -777,7 +777,8 @@ static int coarse_memory_check(const Geometry& g, std::string* err) {
 }
 
 static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
-  {
+  const bool op_only = (o.flags & SMPM_FLAG_OPERATOR_ONLY) != 0;
+  if (!op_only) {
     const int st = coarse_memory_check(g, err);
     if (st != SMPM_OK) return st;
   }
@@ -833,6 +834,10 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
     std::memcpy(f->T.data() + static_cast<size_t>(e) * M * M, T.data(), sizeof(double) * M * M);
   }
   row_sums(g, f->T, &f->Rs);
+  if (op_only) {  // the element factors of S only
+    f->operator_only = true;
+    return SMPM_OK;
+  }
 
   // checkerboard blocks
   f->black.clear();

@@ -108,6 +108,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
+// Polls of a barrier wait before it gives up (default 2^28, about a minute
+// of polling; smpm_set_barrier_spin_limit lowers it to exercise the timeout).
+__device__ long long g_barrier_spin_limit = 1LL << 28;
+
 __device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
   __shared__ int ok;
   __syncthreads();
@@ -116,8 +120,9 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
     epoch += (unsigned)G;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     long long spins = 0;
+    const long long limit = g_barrier_spin_limit;
     while ((int)(ld_acquire(bar) - epoch) < 0) {
-      if (++spins > (1LL << 28)) {  // this CTA's own timeout: code 1 unless a failure is recorded
+      if (++spins > limit) {  // this CTA's own timeout: code 1 unless a failure is recorded
         atomicCAS(err, 0, 1);
         ok = 0;
         break;

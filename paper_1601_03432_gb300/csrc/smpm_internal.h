@@ -77,6 +77,7 @@ struct Factors {
   std::vector<double> c0;    // d : right null vector of C
   std::vector<double> uL, uS, uC, what;  // r, kp, d, r
   std::vector<double> B1;    // kp : B 1 (right null vector of S)
+  bool operator_only = false;  // only T_e and its row sums (SMPM_FLAG_OPERATOR_ONLY)
   int null_iterations = 0;   // GMRES steps of the u_S bordered solve
   double null_relres = 0;
   // Transposed system for the adjoint solve (built with SMPM_FLAG_ADJOINT).

@@ -42,6 +42,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "smpm_internal.h"
@@ -445,6 +446,7 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
 #include "smpm_gmres.cuh"
 #include "smpm_prepost.cuh"
 #include "smpm_refine.cuh"
+#include "smpm_lockstep.cuh"
 #include "smpm_batch.cuh"
 
 // y = S v streamed from HBM: a persistent CTA per SM walks its elements
@@ -899,6 +901,7 @@ struct smpm_handle_s {
   Geometry g;
   smpm_opts opts{};
   bool factored = false;
+  bool op_factored = false;  // operator-only factor step (SMPM_FLAG_OPERATOR_ONLY): S can be applied
   Factors f;
   DevGeo dg{};
   // device factors
@@ -947,6 +950,31 @@ struct smpm_handle_s {
   size_t sf_n = 0;
   std::vector<void*> allocs;
   long long launches = 0;  // kernels launched by this handle (for reports)
+  // lockstep solves of several right-hand sides (allocated on first use, for
+  // up to `cap` columns): per-column pre/post state and GMRES vectors,
+  // basis, w/w2, column reports and the launch shape
+  struct {
+    int cap = 0, RC = 1, mats_smem = 0;
+    size_t smem = 0;
+    double *b = nullptr, *bS = nullptr, *rg = nullptr, *cb = nullptr, *chatb = nullptr, *xs = nullptr;
+    double *x = nullptr, *t = nullptr, *y = nullptr, *vg = nullptr, *c = nullptr, *chat = nullptr;
+    double *V = nullptr, *W = nullptr, *acc = nullptr, *Rh = nullptr, *yv = nullptr;
+    LockColState* cs = nullptr;
+    unsigned char* ctl = nullptr;  // barrier counters | err | per column: acc8, done, nref, rn
+    PrePostArgs* dP = nullptr;     // 2 cap argument blocks (pre, post)
+    // mixed precision: FP32 inner vectors and basis, Z^T r per column,
+    // refinement arguments (kMaxRefine cap)
+    bool has32 = false;
+    float *x32 = nullptr, *t32 = nullptr, *y32 = nullptr, *vg32 = nullptr, *rg32 = nullptr;
+    float *V32 = nullptr, *W32 = nullptr;
+    double* cr = nullptr;
+    RefineArgs* dR = nullptr;
+    std::vector<RefineArgs> hR;
+    std::vector<PrePostArgs> hP;
+    std::vector<LockColState> hcs;
+    std::vector<double> hacc;
+    std::vector<void*> allocs;
+  } lk;
 };
 
 namespace {
@@ -1004,7 +1032,15 @@ smpm_status upload(smpm_handle h, P** p, const std::vector<P>& src, cudaStream_t
   return SMPM_OK;
 }
 
+void free_lock(smpm_handle h) {
+  for (void* p : h->lk.allocs) cudaFree(p);
+  h->lk.allocs.clear();
+  h->lk.cap = 0;
+  h->lk.has32 = false;
+}
+
 void free_all(smpm_handle h) {
+  free_lock(h);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   for (cudaEvent_t* ev : {&h->ev0, &h->ev1, &h->evp, &h->evq}) {
@@ -1444,7 +1480,10 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   if (hs.nan) return fail(SMPM_ENAN, "non-finite value in the right-hand side or the Arnoldi process");
   R.iterations = hs.j;
   R.restarts = scal[7] > 1 ? (int)scal[7] - 1 : 0;
-  const bool conv = hs.converged || hs.beta0 == 0.0 || hs.breakdown;
+  // an Arnoldi breakdown before the estimate reaches tol (the Krylov space
+  // became invariant to round-off, e.g. a tol below round-off on a small
+  // system) is reported as EBREAKDOWN with the iterate assembled as usual
+  const bool conv = hs.converged || hs.beta0 == 0.0;
   R.converged = conv ? 1 : 0;
   R.gmres_relres = hs.beta0 > 0 ? hs.resid / hs.beta0 : 0.0;
   R.schur_relres = acc8[ACC_BSN] > 0 ? std::sqrt(acc8[ACC_RES] / acc8[ACC_BSN]) : 0.0;
@@ -1459,7 +1498,318 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   }
   R.launches = (int)(h->launches - launches0);
   if (rep) *rep = R;
+  if (!conv && hs.breakdown) return fail(SMPM_EBREAKDOWN, "Arnoldi breakdown before GMRES reached tol");
   if (!conv) return fail(SMPM_ENOTCONV, "GMRES did not converge within maxit");
+  return SMPM_OK;
+}
+
+// ---- lockstep solves of several right-hand sides (FP64, Algorithms 2 and 3)
+template <typename P>
+smpm_status lalloc(smpm_handle h, P** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(P) + 16);
+  if (e != cudaSuccess) return fail(SMPM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->lk.allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return SMPM_OK;
+}
+
+// control block of a lockstep solve: 32 barrier counters (pre 0, post 1,
+// inner GMRES 2 + 2 ref, refinement 3 + 2 ref), err at 128; column k's block
+// at kLockCtlBytes + k kLockColBytes: acc8 (8 doubles) | done, nref (ints at
+// +64) | rn[kMaxRefine] at +128
+constexpr size_t kLockCtlBytes = 256;
+constexpr size_t kLockColBytes = 256;
+
+// columns per element work item: the largest of maxrc, ..., 2, 1 that
+// divides R and still gives `warps` warps of a CTA an item (all warps busy:
+// FP64 needs at least 4 per SM for its pipe, FP32 its loads in flight).
+int lock_rc(int R, int nown_b, int maxrc, int warps) {
+  for (int c = maxrc; c >= 2; c /= 2)
+    if (R % c == 0 && (long long)nown_b * (R / c) >= warps) return c;
+  return 1;
+}
+
+// Workspace of the lockstep kernels for up to R columns (FP32 inner buffers
+// too when the handle is factored for mixed precision).
+smpm_status lock_prepare(smpm_handle h, int R) {
+  auto& L = h->lk;
+  const bool mixed = h->opts.precision == 1;
+  if (L.cap >= R && (L.has32 || !mixed)) return SMPM_OK;
+  free_lock(h);
+  int cap = 2;
+  while (cap < R) cap *= 2;
+  const Geometry& g = h->g;
+  const size_t kp = g.kp, r = g.r, d = g.d, m = h->opts.restart, G = h->gm.grid, ES = h->gm.ES;
+  smpm_status s;
+  if ((s = lalloc(h, &L.b, cap * r)) || (s = lalloc(h, &L.bS, cap * kp)) || (s = lalloc(h, &L.rg, cap * kp)) ||
+      (s = lalloc(h, &L.cb, cap * d)) || (s = lalloc(h, &L.chatb, cap * d)) || (s = lalloc(h, &L.xs, cap * kp)) ||
+      (s = lalloc(h, &L.c, cap * d)) || (s = lalloc(h, &L.chat, cap * d)) ||
+      (s = lalloc(h, &L.acc, (2 * m + 1) * cap * (m + 3))) || (s = lalloc(h, &L.Rh, cap * m * (m + 1))) ||
+      (s = lalloc(h, &L.yv, cap * m)) || (s = lalloc(h, &L.cs, (size_t)cap)) ||
+      (s = lalloc(h, &L.ctl, kLockCtlBytes + kLockColBytes * (size_t)cap)) ||
+      (s = lalloc(h, &L.dP, 2 * (size_t)cap)))
+    return s;
+  if (!mixed) {
+    if ((s = lalloc(h, &L.x, cap * kp)) || (s = lalloc(h, &L.t, cap * kp)) || (s = lalloc(h, &L.y, cap * kp)) ||
+        (s = lalloc(h, &L.vg, cap * kp)) || (s = lalloc(h, &L.V, G * (m + 1) * cap * ES)) ||
+        (s = lalloc(h, &L.W, G * 2 * cap * (ES + 1))))
+      return s;
+  } else {
+    if ((s = lalloc(h, &L.x32, cap * kp)) || (s = lalloc(h, &L.t32, cap * kp)) || (s = lalloc(h, &L.y32, cap * kp)) ||
+        (s = lalloc(h, &L.vg32, cap * kp)) || (s = lalloc(h, &L.rg32, cap * kp)) ||
+        (s = lalloc(h, &L.V32, G * (m + 1) * cap * ES)) || (s = lalloc(h, &L.W32, G * 2 * cap * (ES + 1))) ||
+        (s = lalloc(h, &L.cr, cap * d)) || (s = lalloc(h, &L.dR, (size_t)kMaxRefine * cap)))
+      return s;
+    L.has32 = true;
+    L.hR.resize((size_t)kMaxRefine * cap);
+  }
+  L.cap = cap;
+  L.hP.resize(2 * cap);
+  L.hcs.resize(cap);
+  L.hacc.resize(8 * cap);
+  return SMPM_OK;
+}
+
+// Launch shape of the lockstep kernel: resident operator matrices when they fit.
+template <typename S>
+smpm_status lock_shape(smpm_handle h, int R, int optin, int* RC, int* mats, size_t* smem) {
+  const Geometry& g = h->g;
+  const int m = h->opts.restart;
+  *RC = lock_rc(R, h->gm.nown_b, sizeof(S) == 4 ? 8 : 4, kGmresThreads / 32);
+  *mats = 1;
+  *smem = lock_smem_bytes<S>(m, g.M, g.n, R, *RC, h->gm.nown_b, h->gm.nown_w, true);
+  if ((h->opts.flags & SMPM_FLAG_NO_SMEM_RESIDENCY) || *smem > (size_t)optin) {
+    *mats = 0;
+    *smem = lock_smem_bytes<S>(m, g.M, g.n, R, *RC, h->gm.nown_b, h->gm.nown_w, false);
+  }
+  if (*smem > (size_t)optin) return fail(SMPM_EINVAL, "lockstep layout does not fit in shared memory");
+  CU(set_smem_limit(k_gmres_lock<S>, optin));
+  return SMPM_OK;
+}
+
+// R right-hand sides of one grid in lockstep.  FP64: k_pre_cols,
+// k_gmres_lock<double>, k_post_cols.  Mixed precision: k_pre_cols, then
+// kMaxRefine pairs (k_gmres_lock<float>, k_refine_cols) that skip the columns
+// already done, then k_post_cols on the assembled x_S.  One host
+// synchronisation for the reports.
+smpm_status solve_lock(smpm_handle h, const double* f, const double* gn, double* u, double tol, int R,
+                       smpm_report* rep, cudaStream_t st) {
+  smpm_status s;
+  if ((s = lock_prepare(h, R))) return s;
+  auto& L = h->lk;
+  const Geometry& g = h->g;
+  const bool mixed = h->opts.precision == 1;
+  const long long launches0 = h->launches;
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int RC = 1, mats = 0;
+  size_t smem = 0;
+  if ((s = mixed ? lock_shape<float>(h, R, optin, &RC, &mats, &smem) : lock_shape<double>(h, R, optin, &RC, &mats,
+                                                                                          &smem)))
+    return s;
+  CU(set_smem_limit(k_pre_cols, optin));
+  CU(set_smem_limit(k_post_cols, optin));
+  unsigned* bar = reinterpret_cast<unsigned*>(L.ctl);
+  int* err = reinterpret_cast<int*>(L.ctl + 128);
+  auto colblk = [&](int k) { return L.ctl + kLockCtlBytes + kLockColBytes * (size_t)k; };
+  const int m = h->opts.restart;
+  CU(cudaMemsetAsync(L.ctl, 0, kLockCtlBytes + kLockColBytes * (size_t)R, st));
+  CU(cudaMemsetAsync(L.acc, 0, sizeof(double) * (size_t)(2 * m + 1) * R * (m + 3), st));
+  CU(cudaMemsetAsync(L.cs, 0, sizeof(LockColState) * (size_t)R, st));
+  // the work vectors of every column start at zero: slots on physical-boundary
+  // faces are never written by the phases, but the white elements read t there
+  // (times the zero columns of T_e), so they must hold zeros, not stale values
+  {
+    const size_t nv = (size_t)R * g.kp;
+    if (!mixed) {
+      for (double* v : {L.t, L.y, L.vg}) CU(cudaMemsetAsync(v, 0, nv * sizeof(double), st));
+    } else {
+      for (float* v : {L.t32, L.y32, L.vg32}) CU(cudaMemsetAsync(v, 0, nv * sizeof(float), st));
+    }
+  }
+  // per-column arguments of the pre (k < R) and post (R + k) bodies
+  for (int k = 0; k < R; ++k) {
+    PrePostArgs P = prepost_args(h, tol, f + (size_t)k * g.r, gn ? gn + (size_t)k * g.kp : nullptr,
+                                 u + (size_t)k * g.r, mixed);
+    P.b = L.b + (size_t)k * g.r;
+    P.bS = L.bS + (size_t)k * g.kp;
+    P.rg = L.rg + (size_t)k * g.kp;
+    P.cb = L.cb + (size_t)k * g.d;
+    P.chatb = L.chatb + (size_t)k * g.d;
+    P.xs = L.xs + (size_t)k * g.kp;
+    P.acc = reinterpret_cast<double*>(colblk(k));
+    P.ga.err = err;
+    P.gacc = nullptr;
+    P.gacc_n = 0;
+    if (!mixed) {
+      P.ga.x = L.x + (size_t)k * g.kp;
+      double* zs[7] = {P.ga.x, h->wt, h->wy, h->wV, P.bS, P.rg, P.xs};
+      for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+    } else {
+      double* zs[7] = {h->wx, h->wt, h->wy, h->wV, P.bS, P.rg, P.xs};
+      for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+      float* z32[4] = {L.x32 + (size_t)k * g.kp, L.t32, L.y32, L.vg32};
+      for (int i = 0; i < 4; ++i) P.zero32[i] = z32[i];
+      P.cr = L.cr + (size_t)k * g.d;
+      P.rg32 = L.rg32 + (size_t)k * g.kp;
+    }
+    P.ga.bar = bar + 0;
+    L.hP[k] = P;
+    P.ga.bar = bar + 1;
+    P.assembled = mixed ? 1 : 0;
+    L.hP[R + k] = P;
+  }
+  CU(cudaMemcpyAsync(L.dP, L.hP.data(), 2 * R * sizeof(PrePostArgs), cudaMemcpyHostToDevice, st));
+  if (mixed) {
+    for (int ref = 0; ref < kMaxRefine; ++ref)
+      for (int k = 0; k < R; ++k) {
+        GmresArgs<float> a = gmres_args32(h, kInnerTol);
+        a.x = L.x32 + (size_t)k * g.kp;
+        a.t = L.t32;
+        a.y = L.y32;
+        a.vglob = L.vg32;
+        a.rhs = L.rg32 + (size_t)k * g.kp;
+        a.err = err;
+        a.skip = nullptr;
+        RefineArgs RA = refine_args(h, a, tol);
+        RA.ga.bar = bar + 3 + 2 * ref;
+        RA.xS = L.xs + (size_t)k * g.kp;
+        RA.bS = L.bS + (size_t)k * g.kp;
+        RA.cr = L.cr + (size_t)k * g.d;
+        RA.chat_r = L.chatb + (size_t)k * g.d;
+        RA.rgn = reinterpret_cast<double*>(colblk(k)) + ACC_RGN;
+        RA.rn = reinterpret_cast<double*>(colblk(k) + 128) + ref;
+        RA.done = reinterpret_cast<int*>(colblk(k) + 64);
+        RA.nref = reinterpret_cast<int*>(colblk(k) + 68);
+        RA.rhs32 = L.rg32 + (size_t)k * g.kp;
+        L.hR[(size_t)ref * R + k] = RA;
+      }
+    CU(cudaMemcpyAsync(L.dR, L.hR.data(), (size_t)kMaxRefine * R * sizeof(RefineArgs), cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaEventRecord(h->evp, st));
+  {
+    const PrePostArgs* Ps = L.dP;
+    int RR = R;
+    void* args[] = {&Ps, &RR};
+    CU(cudaLaunchCooperativeKernel((const void*)k_pre_cols, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                   h->gm.smem_pp, st));
+    CHECK_LAUNCH();
+  }
+  CU(cudaEventRecord(h->ev0, st));
+  auto lock_fields = [&](auto& A) {
+    A.a.err = err;
+    A.a.mats_smem = mats; A.a.basis_smem = 0; A.a.stream_mats = 0; A.a.warp_elems = 1;
+    A.a.trace = nullptr; A.a.trace_cap = 0; A.a.skip = nullptr; A.a.its_out = nullptr; A.a.wscr = nullptr;
+    A.a.c = L.c; A.a.chat = L.chat; A.a.acc = L.acc;
+    A.R = R; A.RC = RC; A.vs = g.kp; A.ds = g.d;
+    A.cs = L.cs; A.Rh = L.Rh; A.yv = L.yv;
+  };
+  if (!mixed) {
+    LockArgs<double> A{};
+    A.a = gmres_args(h, tol);
+    lock_fields(A);
+    A.a.rhs = L.rg; A.a.x = L.x; A.a.t = L.t; A.a.y = L.y; A.a.vglob = L.vg;
+    A.a.bar = bar + 2;
+    A.V = L.V; A.W = L.W;
+    A.done = nullptr; A.done_stride = 0;
+    if (h->wtrace) {
+      A.a.trace = h->wtrace;
+      A.a.trace_cap = kTraceCap;
+    }
+    void* args[] = {&A};
+    CU(cudaLaunchCooperativeKernel((const void*)k_gmres_lock<double>, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                   smem, st));
+    CHECK_LAUNCH();
+  } else {
+    CU(set_smem_limit(k_refine_cols, optin));
+    for (int ref = 0; ref < kMaxRefine; ++ref) {
+      LockArgs<float> A{};
+      A.a = gmres_args32(h, kInnerTol);
+      lock_fields(A);
+      A.a.rhs = L.rg32; A.a.x = L.x32; A.a.t = L.t32; A.a.y = L.y32; A.a.vglob = L.vg32;
+      A.a.bar = bar + 2 + 2 * ref;
+      A.V = L.V32; A.W = L.W32;
+      A.done = reinterpret_cast<const int*>(colblk(0) + 64);
+      A.done_stride = (int)(kLockColBytes / sizeof(int));
+      if (h->wtrace && ref == 0) {
+        A.a.trace = h->wtrace;
+        A.a.trace_cap = kTraceCap;
+      }
+      {
+        void* args[] = {&A};
+        CU(cudaLaunchCooperativeKernel((const void*)k_gmres_lock<float>, dim3(h->gm.grid), dim3(kGmresThreads),
+                                       args, smem, st));
+        CHECK_LAUNCH();
+      }
+      {
+        const RefineArgs* Rs = L.dR + (size_t)ref * R;
+        int RR = R;
+        void* args[] = {&Rs, &RR};
+        CU(cudaLaunchCooperativeKernel((const void*)k_refine_cols, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                       h->gm32.smem_ref, st));
+        CHECK_LAUNCH();
+      }
+    }
+  }
+  CU(cudaEventRecord(h->ev1, st));
+  {
+    const PrePostArgs* Ps = L.dP + R;
+    int RR = R;
+    void* args[] = {&Ps, &RR};
+    CU(cudaLaunchCooperativeKernel((const void*)k_post_cols, dim3(h->gm.grid), dim3(kGmresThreads), args,
+                                   h->gm.smem_pp, st));
+    CHECK_LAUNCH();
+  }
+  CU(cudaEventRecord(h->evq, st));
+  int herr = 0;
+  std::vector<unsigned char> hcol(kLockColBytes * (size_t)R);
+  CU(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(hcol.data(), colblk(0), hcol.size(), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(L.hcs.data(), L.cs, R * sizeof(LockColState), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (herr) return fail(SMPM_ETIMEOUT, "a grid barrier of the lockstep solve kernels timed out");
+  if (h->wtrace) print_trace(h, st);
+  float gms = 0, pms = 0, qms = 0;
+  CU(cudaEventElapsedTime(&gms, h->ev0, h->ev1));
+  CU(cudaEventElapsedTime(&pms, h->evp, h->ev0));
+  CU(cudaEventElapsedTime(&qms, h->ev1, h->evq));
+  smpm_status worst = SMPM_OK;
+  for (int k = 0; k < R; ++k) {
+    const LockColState& c = L.hcs[k];
+    const unsigned char* blk = hcol.data() + kLockColBytes * (size_t)k;
+    const double* a8 = reinterpret_cast<const double*>(blk);
+    const int done = *reinterpret_cast<const int*>(blk + 64), nref = *reinterpret_cast<const int*>(blk + 68);
+    const double* rn = reinterpret_cast<const double*>(blk + 128);
+    smpm_report Rp{};
+    Rp.iterations = c.its_total;
+    Rp.launches = (int)(h->launches - launches0);
+    Rp.gmres_ms = gms;
+    Rp.pre_ms = pms;
+    Rp.post_ms = qms;
+    Rp.schur_relres = a8[ACC_BSN] > 0 ? std::sqrt(a8[ACC_RES] / a8[ACC_BSN]) : 0.0;
+    bool conv;
+    if (!mixed) {
+      if (c.nan) return fail(SMPM_ENAN, "non-finite value in a right-hand side or its Arnoldi process");
+      Rp.restarts = c.cycles > 1 ? c.cycles - 1 : 0;
+      conv = c.converged != 0;
+      Rp.gmres_relres = c.beta0 > 0 ? c.resid / c.beta0 : 0.0;
+    } else {
+      Rp.refinements = nref;
+      conv = done != 0 || a8[ACC_RGN] == 0.0;
+      const double rho = nref > 0 ? std::sqrt(rn[std::min(nref, kMaxRefine) - 1]) : 0.0;
+      Rp.gmres_relres = a8[ACC_RGN] > 0 ? rho / std::sqrt(a8[ACC_RGN]) : 0.0;
+      if (!std::isfinite(Rp.gmres_relres) || !std::isfinite(Rp.schur_relres))
+        return fail(SMPM_ENAN, "non-finite value in a right-hand side or its refinement");
+    }
+    Rp.converged = conv ? 1 : 0;
+    if (rep) rep[k] = Rp;
+    if (!conv && worst == SMPM_OK) worst = (!mixed && c.breakdown) ? SMPM_EBREAKDOWN : SMPM_ENOTCONV;
+  }
+  if (worst != SMPM_OK)
+    return fail(worst, worst == SMPM_EBREAKDOWN ? "Arnoldi breakdown before tol in a lockstep column"
+                                                : "a lockstep column did not converge");
   return SMPM_OK;
 }
 
@@ -1875,6 +2225,9 @@ smpm_status check_factor_opts(smpm_handle h, const smpm_opts* o, smpm_opts* out)
 // Device half of the factor step: uploads of the host factors in h->f,
 // workspaces and launch shapes.
 smpm_status factor_device(smpm_handle h, cudaStream_t st);
+// The same for an operator-only factor step: T_e (FP64, and FP32 with
+// precision 1) and the element tables of the apply kernels.
+smpm_status factor_device_operator(smpm_handle h, cudaStream_t st);
 
 }  // namespace
 
@@ -1886,11 +2239,13 @@ smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream) try {
   if (cs != SMPM_OK) return cs;
   free_all(h);
   h->factored = false;
+  h->op_factored = false;
   h->opts = opts;
   h->f = Factors();
   std::string err;
   int rc = factor_host(h->g, opts, &h->f, &err);
   if (rc != SMPM_OK) return fail(static_cast<smpm_status>(rc), err);
+  if (h->f.operator_only) return factor_device_operator(h, as_stream(stream));
   return factor_device(h, as_stream(stream));
 } catch (...) {
   return host_exception();
@@ -1923,9 +2278,10 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
     smpm_handle h = hs[i];
     free_all(h);
     h->factored = false;
+    h->op_factored = false;
     h->opts = opts;
     h->f = std::move(fs[i]);
-    smpm_status s = factor_device(h, st);
+    smpm_status s = h->f.operator_only ? factor_device_operator(h, st) : factor_device(h, st);
     if (s != SMPM_OK) return s;
   }
   return SMPM_OK;
@@ -1936,6 +2292,38 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
 }  // extern "C"
 
 namespace {
+
+smpm_status factor_device_operator(smpm_handle h, cudaStream_t st) {
+  const Geometry& g = h->g;
+  DevGeo& dg = h->dg;
+  dg.mx = g.mx; dg.my = g.my; dg.n = g.n; dg.M = g.M;
+  dg.nel = g.nel; dg.kp = g.kp; dg.r = g.r; dg.d = g.d;
+  dg.tau_x = h->f.tau_x; dg.tau_y = h->f.tau_y; dg.p_x = h->f.p_x; dg.p_y = h->f.p_y;
+  dg.sx = 2.0 / g.hx; dg.sy = 2.0 / g.hy;
+  smpm_status s;
+  std::vector<double> Tc = transpose_blocks(h->f.T, g.M, g.nel);
+  if ((s = upload(h, &h->dT, Tc, st))) return s;
+  if (h->opts.precision == 1 && (s = upload(h, &h->dT32, std::vector<float>(Tc.begin(), Tc.end()), st))) return s;
+  std::vector<ElemMeta<double>> t64(g.nel);
+  std::vector<ElemMeta<float>> t32(h->dT32 ? g.nel : 0);
+  for (long long e = 0; e < g.nel; ++e) {
+    ElemMeta<double> a{};
+    a.T = h->dT; a.e = (int)e; a.M = g.M; a.n = g.n; a.mx = g.mx; a.my = g.my;
+    t64[e] = a;
+    if (h->dT32) {
+      ElemMeta<float> c{};
+      c.T = h->dT32; c.e = (int)e; c.M = g.M; c.n = g.n; c.mx = g.mx; c.my = g.my;
+      t32[e] = c;
+    }
+  }
+  if ((s = upload(h, &h->dtab64, t64, st))) return s;
+  if (h->dT32 && (s = upload(h, &h->dtab32, t32, st))) return s;
+  CU(cudaStreamSynchronize(st));
+  h->f.T.clear();
+  h->f.T.shrink_to_fit();
+  h->op_factored = true;
+  return SMPM_OK;
+}
 
 smpm_status factor_device(smpm_handle h, cudaStream_t st) {
   const smpm_opts opts = h->opts;
@@ -2130,11 +2518,30 @@ smpm_status schur_solve(smpm_handle h, const double* f, const double* gn, double
   double t = tol > 0 ? tol : h->opts.tol;
   cudaStream_t st = as_stream(stream);
   smpm_status worst = SMPM_OK;
-  for (int k = 0; k < nrhs; ++k) {
+  // several right-hand sides of an FP64 solve with block-Jacobi: lockstep
+  // groups of up to kLockMaxCols columns
+  const bool lock = nrhs > 1 && h->opts.precond > 0 && !(h->opts.flags & SMPM_FLAG_NO_LOCKSTEP) &&
+                    h->gm.stream_mats == 0 && (h->opts.precision == 0 || h->gm32.stream_mats == 0);
+  for (int k = 0; lock && k < nrhs; k += kLockMaxCols) {
+    const int R = std::min(kLockMaxCols, nrhs - k);
+    smpm_status s = R == 1 ? solve_one(h, f + (size_t)k * h->g.r, gn ? gn + (size_t)k * h->g.kp : nullptr,
+                                       u + (size_t)k * h->g.r, t, rep ? rep + k : nullptr, st)
+                           : solve_lock(h, f + (size_t)k * h->g.r, gn ? gn + (size_t)k * h->g.kp : nullptr,
+                                        u + (size_t)k * h->g.r, t, R, rep ? rep + k : nullptr, st);
+    if (s == SMPM_ENOTCONV || s == SMPM_EBREAKDOWN) {
+      if (worst == SMPM_OK) worst = s;
+    } else if (s != SMPM_OK) {
+      return s;
+    }
+  }
+  for (int k = 0; !lock && k < nrhs; ++k) {
     smpm_status s = solve_one(h, f + (size_t)k * h->g.r, gn ? gn + (size_t)k * h->g.kp : nullptr,
                               u + (size_t)k * h->g.r, t, rep ? rep + k : nullptr, st);
-    if (s == SMPM_ENOTCONV) worst = s;
-    else if (s != SMPM_OK) return s;
+    if (s == SMPM_ENOTCONV || s == SMPM_EBREAKDOWN) {
+      if (worst == SMPM_OK) worst = s;
+    } else if (s != SMPM_OK) {
+      return s;
+    }
   }
   return worst;
 } catch (...) {
@@ -2152,8 +2559,11 @@ smpm_status schur_solve_adjoint(smpm_handle h, const double* gbar_u, double tol,
   for (int k = 0; k < nrhs; ++k) {
     smpm_status s = solve_one(h, gbar_u + (size_t)k * h->g.r, nullptr, gbar_f + (size_t)k * h->g.r, t,
                               rep ? rep + k : nullptr, st, true, gbar_g ? gbar_g + (size_t)k * h->g.kp : nullptr);
-    if (s == SMPM_ENOTCONV) worst = s;
-    else if (s != SMPM_OK) return s;
+    if (s == SMPM_ENOTCONV || s == SMPM_EBREAKDOWN) {
+      if (worst == SMPM_OK) worst = s;
+    } else if (s != SMPM_OK) {
+      return s;
+    }
   }
   return worst;
 } catch (...) {
@@ -2174,7 +2584,7 @@ smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, d
   CU(cudaMemcpyAsync(h->sf, f, rn * sizeof(double), cudaMemcpyHostToDevice, st));
   if (gn) CU(cudaMemcpyAsync(h->sg, gn, gnn * sizeof(double), cudaMemcpyHostToDevice, st));
   smpm_status s = schur_solve(h, h->sf, gn ? h->sg : nullptr, tol, nrhs, h->su, rep, stream);
-  if (s != SMPM_OK && s != SMPM_ENOTCONV) return s;
+  if (s != SMPM_OK && s != SMPM_ENOTCONV && s != SMPM_EBREAKDOWN) return s;
   CU(cudaMemcpyAsync(u, h->su, rn * sizeof(double), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   return s;
@@ -2188,8 +2598,14 @@ smpm_status schur_solve_host(smpm_handle h, const double* f, const double* gn, d
     if (!h->factored) return fail(SMPM_ESTATE, "schur_factor has not been called"); \
   } while (0)
 
+#define NEED_OPERATOR()                                                                          \
+  do {                                                                                           \
+    if (!h) return fail(SMPM_EINVAL, "null handle");                                             \
+    if (!h->factored && !h->op_factored) return fail(SMPM_ESTATE, "schur_factor has not been called"); \
+  } while (0)
+
 smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* stream) try {
-  NEED_FACTOR();
+  NEED_OPERATOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   return launch_schur(h, v, y, as_stream(stream));
 } catch (...) {
@@ -2197,7 +2613,7 @@ smpm_status smpm_apply_schur(smpm_handle h, const double* v, double* y, void* st
 }
 
 smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* stream) try {
-  NEED_FACTOR();
+  NEED_OPERATOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
   if (h->g.M <= 96 && h->dtab32) {
@@ -2546,10 +2962,12 @@ smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, dou
       R.gmres_ms = b->last_ms;
       if (!std::isfinite(R.gmres_relres) || !std::isfinite(R.schur_relres))
         return fail(SMPM_ENAN, "non-finite residual in a batched solve");
-      if (!t.converged) worst = SMPM_ENOTCONV;
+      if (!t.converged && worst == SMPM_OK) worst = t.breakdown ? SMPM_EBREAKDOWN : SMPM_ENOTCONV;
       if (rep) rep[i] = R;
     }
-  if (worst != SMPM_OK) return fail(worst, "a batched solve did not converge");
+  if (worst != SMPM_OK)
+    return fail(worst, worst == SMPM_EBREAKDOWN ? "Arnoldi breakdown before tol in a batched solve"
+                                                : "a batched solve did not converge");
   return SMPM_OK;
 } catch (...) {
   return host_exception();
@@ -2594,6 +3012,14 @@ smpm_status smpm_batch_task_times(smpm_batch b, int* team, double* begin_ms, dou
       if (begin_ms) begin_ms[i] = (double)(t.t_begin - t0) * 1e-6;
       if (end_ms) end_ms[i] = (double)(t.t_end - t0) * 1e-6;
     }
+  return SMPM_OK;
+} catch (...) {
+  return host_exception();
+}
+
+smpm_status smpm_set_barrier_spin_limit(long long spins) try {
+  const long long v = spins > 0 ? spins : (1LL << 28);
+  CU(cudaMemcpyToSymbol(g_barrier_spin_limit, &v, sizeof(v)));
   return SMPM_OK;
 } catch (...) {
   return host_exception();

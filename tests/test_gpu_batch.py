@@ -129,8 +129,10 @@ def test_batch_precision_override(built):
 
 def test_batch_config4_sample(built):
     """The first 12 problems of the seeded uneven config-4 batch (mixed
-    precision, 1e-10): each right-hand side against the single-grid solve of
-    the same handle."""
+    precision, 1e-10): the right-hand sides of the four smallest problems
+    (up to three each) against the oracle's direct bordered solve (1e-9, the
+    bound after refinement), and every right-hand side against the
+    single-grid solve of the same handle."""
     probs = inputs.uneven_batch(512, seed=7)[:12]
     grids = [Grid(mx, my, n) for (mx, my, n, k) in probs]
     factor_many(grids, tol=1e-10, precision=1)
@@ -145,13 +147,20 @@ def test_batch_config4_sample(built):
     reps = b.solve(f, u)
     assert all(r["converged"] == 1 for r in reps)
     uh = u.cpu().numpy()
+    small = sorted(range(len(probs)), key=lambda q: probs[q][0] * probs[q][1] * probs[q][2] ** 2)[:4]
     o, i = 0, 0
-    for gr, p in zip(grids, probs):
+    for q, (gr, p) in enumerate(zip(grids, probs)):
+        og = SMPMGrid(p[0], p[1], p[2]) if q in small else None
+        Lm = og.assemble_L() if og is not None else None
+        uL = SchurSystem(og).u_L if og is not None else None
         for j in range(p[3]):
             fi = torch.as_tensor(fs[i], dtype=torch.float64, device="cuda")
             ui = torch.zeros_like(fi)
             gr.solve(fi, ui)
             assert rel(uh[o:o + gr.r], ui.cpu().numpy()) < 1e-8
+            if og is not None and j < 3:
+                ud = methods.direct_solve(og, Lm, uL, fs[i])
+                assert rel(uh[o:o + gr.r], ud) < 1e-9, (q, j, rel(uh[o:o + gr.r], ud))
             o += gr.r
             i += 1
 
