@@ -69,7 +69,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch", type=int, default=512,
                    help="grids of the uneven batch section (0 skips it; 512 is the full seeded batch)")
-    p.add_argument("--profile", choices=["gmres", "apply", "bapply", "batch"], default=None,
+    p.add_argument("--profile", choices=["gmres", "apply", "apply96", "bapply", "batch"], default=None,
                    help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
 
@@ -330,39 +330,71 @@ def run_ours(args):
              "refinements": mix_rep["refinements"], "schur_relres": mix_rep["schur_relres"],
              "precision": "FP32 inner GMRES (FP32 operator, FP64 coarse/Givens/dot accumulation) + FP64 refinement"}
 
-    # ---- Schur apply y = S v (register-streamed, several warps per element) at a size
-    # whose factor does not stay in L2 between launches: 32x32 elements,
-    # n = 24 (T_e: 75.5 MB FP64, 37.7 MB FP32); L2 flushed before each launch.
-    ga = Grid(32, 32, 24)
-    ga.factor(precision=1, tol=W["tol"], restart=W["restart"])
-    Ma, nela = 4 * 24, 32 * 32
-    apply = {}
-    for name, dt, fn, sz in (("fp64", torch.float64, ga.apply_schur, 8), ("fp32", torch.float32, ga.apply_schur32, 4)):
-        va = torch.randn(ga.kp, dtype=dt, device="cuda")
-        ya = torch.empty_like(va)
-        for _ in range(3):
-            fn(va, ya)
-        times = []
-        for i in range(20):
-            flush.fill_(float(i))
-            flush.sum()    # read pass: the written lines leave L2 clean (no write-back inside the launch)
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record(stream)
-            fn(va, ya)
-            b_.record(stream)
-            torch.cuda.synchronize()
-            times.append(a_.elapsed_time(b_))
-        us = 1e3 * sorted(times)[len(times) // 2]
-        byts = nela * (Ma * Ma + 3 * Ma) * sz
-        flo = 2.0 * nela * Ma * Ma
-        apply[name] = {"us_per_launch": us, "gbs": byts / (us * 1e-6) / 1e9,
-                       "hbm_frac": byts / (us * 1e-6) / 1e9 / hbm_peak, "tflops": flo / (us * 1e-6) / 1e12,
-                       "bytes_per_launch": byts}
-    ga.close()
-    schur_apply = {"workload": "y = S v, 32x32 elements, n=24 (kp = 98304), L2 flushed before each launch "
-                               "(512 MiB write, then a read pass so that no dirty line is written back during the launch)",
-                   "median_of": 20, **apply,
-                   "note": "FP64 is bound by the FP64 ALU (1.26 TFLOP/s) before HBM; FP32 is HBM-bound"}
+    # ---- Schur apply y = S v on single grids of growing size (operator-only
+    # factor step: T_e only), L2 flushed before each launch (write + read
+    # pass, so that no dirty line is written back inside the launch)
+    from paper_1601_03432_gb300 import _binding as _B
+    curve = []
+    for (amx, amy, an) in ((32, 32, 24), (64, 64, 24), (96, 96, 24), (128, 128, 16)):
+        ga = Grid(amx, amy, an)
+        ga.factor(precision=1, flags=_B.FLAG_OPERATOR_ONLY)
+        Ma, nela = 4 * an, amx * amy
+        pt = {"grid": "%dx%d, n=%d" % (amx, amy, an)}
+        for name, dt, fn, sz in (("fp64", torch.float64, ga.apply_schur, 8),
+                                 ("fp32", torch.float32, ga.apply_schur32, 4)):
+            va = torch.randn(ga.kp, dtype=dt, device="cuda")
+            ya = torch.empty_like(va)
+            for _ in range(3):
+                fn(va, ya)
+            times = []
+            for i in range(15):
+                flush.fill_(float(i))
+                flush.sum()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                fn(va, ya)
+                b_.record(stream)
+                torch.cuda.synchronize()
+                times.append(a_.elapsed_time(b_))
+            us = 1e3 * sorted(times)[len(times) // 2]
+            byts = nela * (Ma * Ma + 3 * Ma) * sz
+            pt[name] = {"us": round(us, 2), "MB": round(byts / 1e6, 1), "gbs": round(byts / (us * 1e-6) / 1e9, 1),
+                        "hbm_frac": round(byts / (us * 1e-6) / 1e9 / hbm_peak, 3),
+                        "tflops": round(2.0 * nela * Ma * Ma / (us * 1e-6) / 1e12, 3)}
+        # the element-class-shared path on the same grid: only the vectors
+        # (and the <= 9 class matrices, once) stream from HBM
+        ncls = len({(ix > 0, ix < amx - 1, iy > 0, iy < amy - 1) for ix in range(amx) for iy in range(amy)})
+        for name, dt, fn, sz in (("fp64_class", torch.float64, ga.apply_schur_class, 8),
+                                 ("fp32_class", torch.float32, ga.apply_schur_class32, 4)):
+            va = torch.randn(ga.kp, dtype=dt, device="cuda")
+            ya = torch.empty_like(va)
+            for _ in range(3):
+                fn(va, ya)
+            times = []
+            for i in range(15):
+                flush.fill_(float(i))
+                flush.sum()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                fn(va, ya)
+                b_.record(stream)
+                torch.cuda.synchronize()
+                times.append(a_.elapsed_time(b_))
+            us = 1e3 * sorted(times)[len(times) // 2]
+            byts = (nela * 3 * Ma + ncls * Ma * Ma) * sz
+            pt[name] = {"us": round(us, 2), "MB": round(byts / 1e6, 2), "gbs": round(byts / (us * 1e-6) / 1e9, 1),
+                        "hbm_frac": round(byts / (us * 1e-6) / 1e9 / hbm_peak, 3),
+                        "tflops": round(2.0 * nela * Ma * Ma / (us * 1e-6) / 1e12, 3),
+                        "speedup_vs_per_element": round(pt[name.split("_")[0]]["us"] / us, 2)}
+        curve.append(pt)
+        ga.close()
+    schur_apply = {"workload": "y = S v on one grid, operator-only factor step, L2 flushed before each launch "
+                               "(512 MiB write, then a read pass); median of 15",
+                   "algorithmic_bytes": "per element: nel (M^2 + 3M) s (T_e once, v read twice, y once); class-shared: "
+                                        "3 M nel s + (classes) M^2 s",
+                   "curve": curve,
+                   "note": "FP64 at 0.25 flop/byte is bound by the FP64 pipe (1.26 TFLOP/s) near 5 TB/s; "
+                           "FP32 is HBM-bound; the smallest grids are launch and first-load latency"}
 
     # the batch and precision-config sections run on single-GPU runs only: a
     # multi-GPU run measures the replicated headline solve and holds every GPU
@@ -673,6 +705,21 @@ def run_profile(which):
             b.apply_schur32(v, yv)
         torch.cuda.synchronize()
         b.close()
+        print("ok")
+        return
+    elif which == "apply96":
+        # one grid of 96 x 96 elements, n = 24 (operator-only factor step):
+        # three FP32 and three FP64 y = S v launches (0.35 / 0.70 GB of T_e)
+        from paper_1601_03432_gb300 import _binding as _B
+        g = Grid(96, 96, 24)
+        g.factor(precision=1, flags=_B.FLAG_OPERATOR_ONLY)
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        for dt, fn in ((torch.float32, g.apply_schur32), (torch.float64, g.apply_schur)):
+            v = torch.randn(g.kp, dtype=dt, device="cuda", generator=gen)
+            yv = torch.empty_like(v)
+            for _ in range(3):
+                fn(v, yv)
+        torch.cuda.synchronize()
         print("ok")
         return
     else:

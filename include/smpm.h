@@ -208,6 +208,17 @@ smpm_status smpm_apply_schur_precond(smpm_handle h, const double* v, double* y, 
 smpm_status smpm_apply_deflation(smpm_handle h, const double* v, double* y, void* stream);
 /* y = Q v, Q = I - Z C^-1 Z^T S (Eq. projection2). */
 smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, void* stream);
+/* y = S v as smpm_apply_schur / smpm_apply_schur32, by the element-class-
+ * shared path: on the axis-aligned uniform grids of this library T_e depends
+ * only on which faces of the element are interfaces (at most 9 classes), so
+ * the apply is one dense product T_c X_c per class (X_c: the own slots of the
+ * class's elements side by side) and only the vectors stream from HBM.  The
+ * paper's method keeps per-element factors (mapped elements, Sec. 1.2); this
+ * is a property of uniform grids.  Needs n <= 32.  Errors as
+ * smpm_apply_schur. */
+smpm_status smpm_apply_schur_class(smpm_handle h, const double* v, double* y, void* stream);
+smpm_status smpm_apply_schur_class32(smpm_handle h, const float* v, float* y, void* stream);
+
 /* b_S = B A^-1 b (right-hand side of Eq. schur_complement_system); b: r, bS: kp. */
 smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream);
 /* u = A^-1 (b - E x) (back-substitution of Sec. 1.3); b: r, x: kp, u: r. */

@@ -30,7 +30,8 @@ EXPORTS = [
     "smpm_apply_deflation_noalloc", "smpm_apply_schur32", "schur_solve_adjoint",
     "smpm_factor_many", "smpm_batch_create", "smpm_batch_info", "smpm_batch_solve", "smpm_batch_autotune", "smpm_batch_destroy",
     "smpm_batch_task_times", "smpm_batch_apply_schur", "smpm_batch_apply_schur32",
-    "smpm_batch_set_apply_kernel", "smpm_set_barrier_spin_limit",
+    "smpm_batch_set_apply_kernel", "smpm_set_barrier_spin_limit", "smpm_apply_schur_class",
+    "smpm_apply_schur_class32",
 ]
 
 
@@ -80,7 +81,7 @@ def lib():
         L.schur_solve_adjoint.argtypes = [P, P, D, I, P, P, ctypes.POINTER(SmpmReport), P]
         for name in ["smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond", "smpm_apply_deflation",
                      "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_apply_deflation_noalloc",
-                     "smpm_apply_schur32"]:
+                     "smpm_apply_schur32", "smpm_apply_schur_class", "smpm_apply_schur_class32"]:
             getattr(L, name).argtypes = [P, P, P, P]
         L.smpm_recover.argtypes = [P, P, P, P, P]
         L.smpm_null_vectors.argtypes = [P, P, P, P, P]
@@ -267,6 +268,14 @@ class Grid:
     def apply_schur32(self, v, out, stream=None):
         """y = S v in FP32 (float32 tensors; needs factor(precision=1))."""
         return self._op("smpm_apply_schur32", v, out, stream, dtype="float32")
+
+    def apply_schur_class(self, v, out, stream=None):
+        """y = S v by the element-class-shared path (float64 tensors)."""
+        return self._op("smpm_apply_schur_class", v, out, stream)
+
+    def apply_schur_class32(self, v, out, stream=None):
+        """y = S v in FP32 by the element-class-shared path (needs factor(precision=1))."""
+        return self._op("smpm_apply_schur_class32", v, out, stream, dtype="float32")
 
     def apply_precond(self, v, out, stream=None):
         return self._op("smpm_apply_precond", v, out, stream)

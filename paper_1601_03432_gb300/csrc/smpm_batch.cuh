@@ -24,6 +24,17 @@ struct alignas(16) BatchTask {
   unsigned char* ctl;     // the problem's control block (zeroed per task from byte 256)
   int* its;               // inner iterations per refinement step (in ctl)
   double* rn;             // ||r||^2 per refinement step (in ctl)
+  // lockstep group (ncols >= 2): ncols right-hand sides of the problem in one
+  // lockstep GMRES; per-column arguments live in global memory and are staged
+  // one at a time behind this header
+  int ncols;
+  long long rep0;                // report index of the group's first column
+  long long r_len, kp_len;       // node and slot vector lengths of the problem
+  LockArgs<double> L64;
+  LockArgs<float> L32;
+  const PrePostArgs* Pc;         // 2 R: pre (c), post (R + c)
+  const RefineArgs* Rc;          // kMaxRefine R: refinement step ref of column c at ref R + c
+  unsigned char* lctl;           // column blocks (kLockColBytes each): acc8 | done, nref | rn
 };
 
 struct BatchIO {
@@ -46,7 +57,112 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-constexpr int kBatchHdr = (int)((sizeof(BatchTask) + 127) / 128 * 128);
+constexpr size_t kLockColBytes = 256;  // column block of a lockstep solve's control area
+constexpr int kBatchTaskBytes = (int)((sizeof(BatchTask) + 127) / 128 * 128);
+// header: the task, then staging for one column's pre/post and refinement arguments
+constexpr int kBatchHdr = (int)((kBatchTaskBytes + sizeof(PrePostArgs) + sizeof(RefineArgs) + 127) / 128 * 128);
+
+// copy n bytes (a multiple of 16) from global memory into shared memory, all threads
+__device__ __forceinline__ void stage16(void* dst, const void* src, int n) {
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < n / 16; i += blockDim.x) d[i] = s[i];
+}
+
+// A lockstep group task: pre bodies of the R columns, the lockstep GMRES
+// (FP64, or up to kMaxRefine rounds of FP32 lockstep GMRES and per-column
+// refinement), post bodies, reports.  Returns the failing body (0: none).
+__device__ __noinline__ int batch_group(BatchTask& T, unsigned char* smraw, unsigned char* body, const BatchIO* io,
+                           TaskReport* rep, int team, unsigned& epoch) {
+  PrePostArgs& Pst = *reinterpret_cast<PrePostArgs*>(smraw + kBatchTaskBytes);
+  RefineArgs& Rst = *reinterpret_cast<RefineArgs*>(smraw + kBatchTaskBytes + sizeof(PrePostArgs));
+  const int R = T.ncols;
+  const GmresArgs<double>& ga = T.P.ga;
+  const int rank = team_rank(ga);
+  const unsigned long long t_begin = global_ns();
+  auto stage_p = [&](int i, int c) {
+    __syncthreads();
+    stage16(&Pst, T.Pc + i, (int)sizeof(PrePostArgs));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Pst.f = io->f + T.f_off + (size_t)c * T.r_len;
+      Pst.u = io->u + T.u_off + (size_t)c * T.r_len;
+      Pst.gn = (T.has_g && io->g) ? io->g + T.g_off + (size_t)c * T.kp_len : nullptr;
+    }
+    __syncthreads();
+  };
+  // column blocks, lockstep accumulators and column reports start at zero
+  if (rank == 0) {
+    for (int i = threadIdx.x; i < R * (int)(kLockColBytes / 4); i += blockDim.x) reinterpret_cast<int*>(T.lctl)[i] = 0;
+    for (int i = threadIdx.x; i < R * (int)(sizeof(LockColState) / 4); i += blockDim.x)
+      reinterpret_cast<int*>(T.precision == 0 ? T.L64.cs : T.L32.cs)[i] = 0;
+  }
+  {
+    const GmresArgs<double>& a = T.P.ga;
+    const size_t nacc = (size_t)(2 * a.m + 1) * R * (a.m + 3);
+    double* acc = T.precision == 0 ? T.L64.a.acc : T.L32.a.acc;
+    for (size_t i = (size_t)rank * blockDim.x + threadIdx.x; i < nacc; i += (size_t)a.G * blockDim.x) acc[i] = 0.0;
+  }
+  if (!grid_sync(ga.bar, ga.err, epoch, ga.G)) return 1;
+  for (int c = 0; c < R; ++c) {
+    stage_p(c, c);
+    if (!pre_body(Pst, body, epoch)) return 2;
+  }
+  if (T.precision == 0) {
+    if (!lock_body<double>(T.L64, body, epoch)) return 3;
+  } else {
+    for (int ref = 0; ref < kMaxRefine; ++ref) {
+      // every column's done flag was written before the last barrier
+      bool all = true;
+      for (int c = 0; c < R; ++c)
+        all = all && *((volatile const int*)(T.lctl + (size_t)c * kLockColBytes + 64)) != 0;
+      if (all) break;
+      if (!lock_body<float>(T.L32, body, epoch)) return 3;
+      for (int c = 0; c < R; ++c) {
+        if (*((volatile const int*)(T.lctl + (size_t)c * kLockColBytes + 64))) continue;
+        __syncthreads();
+        stage16(&Rst, T.Rc + (size_t)ref * R + c, (int)sizeof(RefineArgs));
+        __syncthreads();
+        if (refine_body(Rst, body, epoch) < 0) return 4;
+      }
+      if (!grid_sync(ga.bar, ga.err, epoch, ga.G)) return 4;
+    }
+  }
+  for (int c = 0; c < R; ++c) {
+    stage_p(R + c, c);
+    if (!post_body(Pst, body, epoch)) return 5;
+  }
+  if (!grid_sync(ga.bar, ga.err, epoch, ga.G)) return 5;
+  if (rank == 0 && threadIdx.x < R) {
+    const int c = threadIdx.x;
+    const unsigned char* blk = T.lctl + (size_t)c * kLockColBytes;
+    const double* a8 = reinterpret_cast<const double*>(blk);
+    const LockColState& cs = (T.precision == 0 ? T.L64.cs : T.L32.cs)[c];
+    TaskReport r{};
+    r.res2 = __ldcg(a8 + ACC_RES);
+    r.bsn2 = __ldcg(a8 + ACC_BSN);
+    r.iterations = cs.its_total;
+    if (T.precision == 0) {
+      r.restarts = cs.cycles > 1 ? cs.cycles - 1 : 0;
+      r.converged = cs.converged;
+      r.breakdown = cs.breakdown;
+      r.gmres_num = cs.resid;
+      r.gmres_den = cs.beta0;
+    } else {
+      const int nref = *reinterpret_cast<const int*>(blk + 68);
+      const double* rn = reinterpret_cast<const double*>(blk + 128);
+      r.refinements = nref;
+      r.converged = (*reinterpret_cast<const int*>(blk + 64) != 0 || __ldcg(a8 + ACC_RGN) == 0.0) ? 1 : 0;
+      r.gmres_num = nref > 0 ? sqrt(__ldcg(rn + min(nref, kMaxRefine) - 1)) : 0.0;
+      r.gmres_den = sqrt(__ldcg(a8 + ACC_RGN));
+    }
+    r.t_begin = t_begin;
+    r.t_end = global_ns();
+    r.team = team;
+    rep[T.rep0 + c] = r;
+  }
+  return 0;
+}
 
 __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ tasks, const int* __restrict__ begin,
                                                   const int* __restrict__ team_of, const BatchIO* io,
@@ -65,6 +181,14 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
       for (int i = threadIdx.x; i < (int)(sizeof(BatchTask) / 16); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    if (T.ncols >= 2) {  // lockstep group
+      const int where = batch_group(T, smraw, body, io, rep, team, epoch);
+      if (where) {
+        if (threadIdx.x == 0 && atomicCAS(T.P.ga.err + 1, 0, t + 1) == 0) T.P.ga.err[2] = where;
+        return;
+      }
+      continue;
+    }
     if (threadIdx.x == 0) {
       T.P.f = io->f + T.f_off;
       T.P.u = io->u + T.u_off;
@@ -135,7 +259,11 @@ __global__ void __launch_bounds__(256, 1) k_batch(const BatchTask* __restrict__ 
       r.t_begin = t_begin;
       r.t_end = global_ns();
       r.team = team;
-      rep[t] = r;
+      rep[T.rep0] = r;
     }
   }
 }
+// stage16 copies these with 16-byte loads and stores
+static_assert(sizeof(PrePostArgs) % 16 == 0 && alignof(PrePostArgs) >= 16, "PrePostArgs: 16-byte copies");
+static_assert(sizeof(RefineArgs) % 16 == 0 && alignof(RefineArgs) >= 16, "RefineArgs: 16-byte copies");
+static_assert(sizeof(BatchTask) % 16 == 0, "BatchTask: 16-byte copies");

@@ -76,6 +76,12 @@ struct GmresArgs {
   int G;            // CTAs working on this solve (a team; the whole grid for one solve)
   int base;         // first CTA of the team: the CTA's rank is blockIdx.x - base
   S* wscr;          // when non-null: per-CTA global scratch for w, w2 (2 (ES+1) per rank)
+  // fused coarse solve (Algorithm 3 steps only): each white element adds
+  // H[:, j] c_j for its interfaces j into c_hat as soon as c_j is known, so
+  // the separate coarse phase and its grid barrier disappear
+  int fused;           // 1: use HT / chatd in the Arnoldi steps
+  const double* HT;    // d*d, H column-major (HT[j d + r] = H[r][j])
+  double* chatd;       // 2 d: c_hat of even / odd steps (accumulated with atomics)
 };
 
 // rank of this CTA within the team that works on a solve
@@ -158,6 +164,8 @@ struct Smem {
   S *p, *r1, *av, *z, *red;
   S *w, *w2;
   double* cst;  // staged coarse vector c (d)
+  double* cpv;  // fused coarse: c_j of the owned white elements' interfaces (4 per element)
+  int* cpj;     // and their interface indices (-1: none)
   S* V;     // (m+1) * ES when resident
   S* mats;  // resident matrices, or the two stream buffers
   S* wb;    // warp_elems: per-warp element scratch, kWarpScratch(M) entries per warp
@@ -182,6 +190,8 @@ __device__ Smem<S> carve(const GmresArgs<S>& a, unsigned char* raw) {
   s.misc = d; d += 16;
   s.cs = d; d += M;
   s.cst = d; d += a.g.d + 1;
+  s.cpv = d; d += 4 * (size_t)a.nown_w;
+  s.cpj = reinterpret_cast<int*>(d); d += 2 * (size_t)a.nown_w;
   S* q = reinterpret_cast<S*>(d);
   s.p = q; q += M;
   s.r1 = q; q += M;
@@ -213,7 +223,7 @@ template <typename S>
 inline size_t gmres_smem_bytes(int m, int M, int n, int ES, int nown_b, int nown_w, int basis_smem, int mats_smem,
                                long long d, int stream_elems = 0, bool w_global = false, int nbuf = 2,
                                bool warp_elems = false) {
-  size_t dbl = kMaxStreamBufs + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1;
+  size_t dbl = kMaxStreamBufs + 9 * (size_t)(m + 3) + 16 + M + (size_t)d + 1 + 6 * (size_t)nown_w;
   size_t sel = 4 * (size_t)M + 256 + (w_global ? 0 : 2 * (size_t)(ES + 1));
   if (warp_elems) sel += (size_t)(kGmresThreads / 32) * warp_scratch(M) + 16 / sizeof(S);
   if (basis_smem) sel += (size_t)(m + 1) * ES;
@@ -413,7 +423,7 @@ __device__ void block_solve(const GmresArgs<S>& a, const Smem<S>& s, int k, int 
 // c = Z^T y on e's interfaces (with_c).
 template <typename S>
 __device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, const S* Tw, int e, const S* v, double sc,
-                           bool with_c) {
+                           bool with_c, int kstage = -1) {
   const DevGeo& g = a.g;
   const int M = g.M, n = g.n;
   for (int i = threadIdx.x; i < M; i += blockDim.x) s.p[i] = ldcg(a.t + (size_t)e * M + i);
@@ -441,6 +451,10 @@ __device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, const S* Tw,
     sum = warp_sum(sum);
     const int j = dev_iface(g, e, F);
     if (lane == 0 && j >= 0) a.c[j] = sum;
+    if (lane == 0 && kstage >= 0) {
+      s.cpv[kstage * 4 + F] = sum;
+      s.cpj[kstage * 4 + F] = j;
+    }
   }
   __syncthreads();
 }
@@ -695,7 +709,8 @@ __device__ void black_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const
 // White elements with one warp per element: y = S t on the black slots
 // facing e, y = sc*v on e's slots, c = Z^T y on e's interfaces (with_c).
 template <typename S>
-__device__ void white_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const S* v, double sc, bool with_c) {
+__device__ void white_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const S* v, double sc, bool with_c,
+                                  bool stage = false) {
   const DevGeo& g = a.g;
   const int M = g.M, n = g.n, G = a.G, rank = team_rank(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -726,10 +741,14 @@ __device__ void white_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const
     __syncwarp();
     if (with_c && lane < 4) {  // face F summed by lane F
       const int F = lane, j = dev_iface(g, e, F);
+      double sum = 0;
       if (j >= 0) {
-        double sum = 0;
         for (int tt = 0; tt < n; ++tt) sum += ci[F * n + tt];
         a.c[j] = sum;
+      }
+      if (stage) {
+        s.cpv[k * 4 + F] = sum;
+        s.cpj[k * 4 + F] = j;
       }
     }
     __syncwarp();
@@ -777,10 +796,13 @@ __device__ bool black_phase(const GmresArgs<S>& a, const Smem<S>& s, MatStream<S
 }
 
 // op(sc * src) -> y (and c, chat).  With t_done the owners have already
-// written t = M^-1 v for their blocks.
+// written t = M^-1 v for their blocks.  With chat_acc (fused coarse solve,
+// Algorithm 3 only) the white phase also adds H[:, j] c_j for the interfaces
+// of the CTA's white elements into chat_acc (zero on entry), and there is no
+// separate coarse phase: c_hat is complete after the white phase's barrier.
 template <typename S>
 __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, double sc, bool t_done,
-                         int& trace_n, unsigned& epoch, MatStream<S>* ms = nullptr) {
+                         int& trace_n, unsigned& epoch, MatStream<S>* ms = nullptr, double* chat_acc = nullptr) {
   const DevGeo& g = a.g;
   const int G = a.G;
   if (a.precond == 0) {
@@ -791,23 +813,39 @@ __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, 
   GM_TRACE(20);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(21);
-  if (a.warp_elems) white_phase_warps(a, s, src, sc, a.precond == 2);
+  const bool fuse = chat_acc && a.precond == 2;
+  if (fuse)
+    for (int q = threadIdx.x; q < 4 * a.nown_w; q += blockDim.x) s.cpj[q] = -1;
+  __syncthreads();
+  if (a.warp_elems) white_phase_warps(a, s, src, sc, a.precond == 2, fuse);
   for (int k = 0; k < (a.warp_elems ? 0 : a.nown_w); ++k) {
     int iw = team_rank(a) + k * G;
     if (iw >= a.nwhite) break;
     if (ms) {
       const S* T = ms_acquire(a, s, *ms);
       if (!T) return false;
-      white_step(a, s, T, a.white[iw], src, sc, a.precond == 2);
+      white_step(a, s, T, a.white[iw], src, sc, a.precond == 2, fuse ? k : -1);
       ms_release(a, s, *ms);
     } else {
-      white_step(a, s, mat_Tw(a, s, k, a.white[iw]), a.white[iw], src, sc, a.precond == 2);
+      white_step(a, s, mat_Tw(a, s, k, a.white[iw]), a.white[iw], src, sc, a.precond == 2, fuse ? k : -1);
+    }
+  }
+  if (fuse) {  // c_hat += sum over this CTA's interfaces j of H[:, j] c_j
+    __syncthreads();
+    const int d = (int)g.d, nq = 4 * a.nown_w;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) {
+      double acc = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int j = s.cpj[q];
+        if (j >= 0) acc += __ldg(a.HT + (size_t)j * d + r) * s.cpv[q];
+      }
+      if (acc != 0.0) atomicAdd(chat_acc + r, acc);
     }
   }
   GM_TRACE(22);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(23);
-  if (a.precond == 2) {
+  if (a.precond == 2 && !fuse) {
     coarse_rows(a, s);
     GM_TRACE(24);
     if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
@@ -905,6 +943,10 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
       nn = warp_sum(nn);
       if ((threadIdx.x & 31) == 0 && nn != 0.0) atomicAdd(accN, nn);
     }
+    const bool fused = a.fused && a.precond == 2;
+    if (fused)  // both c_hat buffers of the fused coarse solve start at zero
+      for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < 2 * g.d; i += (long long)G * blockDim.x)
+        a.chatd[i] = 0.0;
     if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
     const double beta = sqrt(__ldcg(accN));
     if (cycle == 0) {
@@ -936,18 +978,28 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
         }
         __syncthreads();
       }
+      // fused coarse solve: this step accumulates c_hat into buffer j & 1; the
+      // other buffer was last read in the previous step's phase D (before its
+      // barrier) and is cleared here for the next step
+      double* chat_j = fused ? a.chatd + (size_t)(j & 1) * g.d : nullptr;
+      if (fused) {
+        double* nxt = a.chatd + (size_t)((j + 1) & 1) * g.d;
+        for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < g.d; i += (long long)G * blockDim.x)
+          nxt[i] = 0.0;
+      }
       if (a.precond == 0) {
         if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();  // neighbours read v_j
         if (!apply_op(a, s, a.vglob, ivj, false, trace_n, epoch, ms)) GM_FAIL();
       } else {
         if (!black_phase(a, s, ms, (const S*)nullptr, ivj, vj)) GM_FAIL();
-        if (!apply_op(a, s, a.vglob, ivj, true, trace_n, epoch, ms)) GM_FAIL();
+        if (!apply_op(a, s, a.vglob, ivj, true, trace_n, epoch, ms, chat_j)) GM_FAIL();
       }
       GM_TRACE(4);
       // ---- D: w = y - S Z chat on owned entries; V^T w, ||w||^2
+      const double* chat_d = a.precond == 2 ? (fused ? chat_j : a.chat) : nullptr;
       for (int i = threadIdx.x; i < ES; i += blockDim.x) {
         long long sl = entry_slot(a, i);
-        s.w[i] = sl >= 0 ? (S)deflate_slot_cg(g, a.y, a.precond == 2 ? a.chat : nullptr, a.Rs, sl) : S(0);
+        s.w[i] = sl >= 0 ? (S)deflate_slot_cg(g, a.y, chat_d, a.Rs, sl) : S(0);
       }
       __syncthreads();
       owned_dots(a, s, s.w, j + 2, accD);

@@ -517,7 +517,7 @@ __device__ __forceinline__ double lk_combo(const LockArgs<S>& A, double base, co
 
 // The lockstep GMRES by the CTAs of a team; false when a wait timed out.
 template <typename S>
-__device__ bool lock_body(const LockArgs<S>& A, unsigned char* smraw, unsigned& epoch) {
+__device__ __noinline__ bool lock_body(const LockArgs<S>& A, unsigned char* smraw, unsigned& epoch) {
   const LockSmem<S> s = lock_carve(A, smraw);
   const GmresArgs<S>& a = A.a;
   const DevGeo& g = a.g;
@@ -549,7 +549,9 @@ __device__ bool lock_body(const LockArgs<S>& A, unsigned char* smraw, unsigned& 
   // misc per column: 0 ||w||^2, 1 ||w2||^2, 2 residual estimate, 3 state (0 running,
   // 1 converged, 2 breakdown, 3 NaN), 5 Arnoldi steps (all cycles), 6 beta0, 7 tol * beta0
   for (int c = threadIdx.x; c < R; c += blockDim.x) {
-    s.active[c] = (A.done && A.done[(size_t)c * A.done_stride]) ? 0 : 1;
+    // done flags are written by other CTAs (refinement steps of the same
+    // launch in a batch): read from L2, never a stale L1 line
+    s.active[c] = (A.done && *((volatile const int*)(A.done + (size_t)c * A.done_stride))) ? 0 : 1;
     s.jc[c] = 0;
     for (int k = 0; k < 8; ++k) s.misc[c * 8 + k] = 0;
   }

@@ -39,7 +39,7 @@
 #pragma once
 // Included inside the anonymous namespace of smpm_solver.cu.
 
-struct PrePostArgs {
+struct alignas(16) PrePostArgs {  // 16-byte multiple: staged with 16-byte copies in batched solves
   GmresArgs<double> ga;  // geometry, ownership, operator matrices, t/y/c/chat buffers
   const double* fdx;
   const double* fdy;
@@ -88,6 +88,8 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
   double* B = fd_scratch(s);
   double* U = B + nn;
   double* t1 = U + nn;
+  int trace_n = 0;
+  GM_TRACE(50);
   // ---- P1: zero the work vectors; b = f + tau g; u_L^T b
   for (long long i = (long long)rank * blockDim.x + threadIdx.x; i < g.kp; i += (long long)G * blockDim.x)
     for (int v = 0; v < 7; ++v) P.zero[v][i] = 0.0;
@@ -120,7 +122,9 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
   }
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(P.acc + ACC_ULB, part);
+  GM_TRACE(51);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+  GM_TRACE(52);
   // ---- P2: project b; w = A_e^-1 b_e; push fluxes into b_S; u_S^T b_S; Z^T b_S
   const double alpha = __ldcg(P.acc + ACC_ULB);
   double pus = 0;
@@ -162,15 +166,21 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
   }
   pus = warp_sum(pus);
   if ((threadIdx.x & 31) == 0 && pus != 0.0) atomicAdd(P.acc + ACC_USBS, pus);
+  GM_TRACE(53);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+  GM_TRACE(54);
   // ---- P3: c_hat_b = C^+ Z^T (b_S - beta u_S)
   const double beta = __ldcg(P.acc + ACC_USBS);
   if (a.precond == 2) {
     for (int j = rank * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
       a.c[j] = __ldcg(P.cb + j) - beta * P.ZtuS[j];
+    GM_TRACE(55);
     if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+    GM_TRACE(56);
     coarse_rows(a, s);  // a.c -> a.chat
+    GM_TRACE(57);
     if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+    GM_TRACE(58);
     for (int j = rank * blockDim.x + threadIdx.x; j < (int)g.d; j += G * blockDim.x)
       P.chatb[j] = __ldcg(a.chat + j);
   }
@@ -250,7 +260,9 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
       block_solve(a, s, k, ib, e, s.w);
     }
     if (a.precond == 1) {
+      GM_TRACE(61);
       if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+      GM_TRACE(62);
       for (int i = threadIdx.x; i < a.ES; i += blockDim.x) {
         const long long sl = entry_slot(a, i);
         if (sl >= 0) P.xs[sl] = __ldcg(a.t + sl);
@@ -266,7 +278,9 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
       }
     }
   }
+  GM_TRACE(63);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+  GM_TRACE(64);
   // ---- Q5: recovery u_e = A_e^-1 (b_e - E_e x_S), residual b_S - S x_S, mean
   double pm = 0, pr = 0;
   for (long long e = rank; e < g.nel; e += G) {
@@ -323,7 +337,9 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
     if (pm != 0.0) atomicAdd(P.acc + ACC_MEAN, pm);
     if (pr != 0.0) atomicAdd(P.acc + ACC_RES, pr);
   }
+  GM_TRACE(65);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
+  GM_TRACE(66);
   // ---- Q6: zero GLL-weighted mean (adjoint: projection out of u_L, dl/dg)
   const double mean = __ldcg(P.acc + ACC_MEAN);
   if (!P.adjoint) {

@@ -15,7 +15,7 @@
 #pragma once
 // Included inside the anonymous namespace of smpm_solver.cu.
 
-struct RefineArgs {
+struct alignas(16) RefineArgs {  // 16-byte multiple: staged with 16-byte copies in batched solves
   GmresArgs<float> ga;   // FP32 operator and vectors: x = inner y, t, y, c, chat, rhs (next inner rhs)
   const double* Tc64;    // nel * M*M, FP64 T_e (column-major)
   const double* Rs64;    // FP64 row sums for the deflation of r
@@ -122,7 +122,7 @@ __device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& 
   if ((threadIdx.x & 31) == 0 && pr != 0.0) atomicAdd(R.rn, pr);
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
   // ---- R6: convergence test (uniform), else c_hat_r = C^+ Z^T r
-  const double rho = sqrt(__ldcg(R.rn)), target = R.tol * sqrt(*R.rgn);
+  const double rho = sqrt(__ldcg(R.rn)), target = R.tol * sqrt(__ldcg(R.rgn));
   if (rank == 0 && threadIdx.x == 0) *R.nref += 1;
   if (rho <= target) {
     if (rank == 0 && threadIdx.x == 0) *R.done = 1;

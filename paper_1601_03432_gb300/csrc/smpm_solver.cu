@@ -65,6 +65,9 @@ constexpr int kMaxRefine = 8;        // FP64 refinement steps of the mixed-preci
 constexpr int kMaxStreamBufs = 4;    // shared-memory buffers of the GMRES kernel's matrix stream
 constexpr int kWarpElemsMin = 4;     // owned blocks per CTA from which each warp takes its own element
 constexpr double kInnerTol = 1e-4;   // relative tolerance of each FP32 inner GMRES
+// the coarse solve is fused into the white-element phase when the atomic adds
+// it costs per Arnoldi step (d per CTA) stay below this
+constexpr long long kFusedCoarseMaxAdds = 1LL << 17;
 
 struct GState {
   double tolabs, beta0, beta, wnorm0sq, resid;
@@ -882,6 +885,106 @@ cudaError_t launch_schur_warp(const ElemMeta<S>* tab, long long nelem, const S* 
   return cudaGetLastError();
 }
 
+// Element-class-shared apply y = S v.  On an axis-aligned uniform grid T_e
+// depends only on which of the element's four faces are interfaces (at most
+// 9 classes: interior, 4 edges, 4 corners), so y = v + scatter(T_c X_c) with
+// X_c the M x n_c matrix of the own slots of all elements of class c: a real
+// dense contraction.  One CTA per tile of up to kClassTile elements of one
+// class: thread 0 stages T_c and the tile's element slot vectors in shared
+// memory with 1-D bulk copies (all in flight at once, one mbarrier; plain
+// loads when v is not 16-byte aligned), thread (rg, eg) accumulates rows
+// rg + 16 i (i < ceil(M/16)) of elements eg + 16 j (j < 4) in registers, and
+// the products go straight to the neighbours' facing slots.  HBM traffic is
+// the vectors only (plus the class matrices once).  A copy that does not
+// complete within the bounded wait leaves the tile's outputs NaN.
+constexpr int kClassTile = 64;  // elements per CTA tile
+inline size_t class_smem(int M, size_t elem) {
+  return 16 + ((size_t)M * M + (size_t)(M + 16 / elem) * kClassTile) * elem;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_schur_class(DevGeo g, const S* __restrict__ Tcls, const int* __restrict__ tiles,
+                                                     const int* __restrict__ elems, const S* __restrict__ v, S* y,
+                                                     int bulk) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int M = g.M, n = g.n;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(raw);
+  S* Ts = reinterpret_cast<S*>(raw + 16);  // M x M column-major
+  const int XS = M + 16 / (int)sizeof(S);  // element stride of Xs: 16 bytes of padding (banks, bulk alignment)
+  S* Xs = Ts + (size_t)M * M;              // element-major: Xs[t * XS + k]
+  const int cls = tiles[3 * blockIdx.x], start = tiles[3 * blockIdx.x + 1], cnt = tiles[3 * blockIdx.x + 2];
+  const S* T = Tcls + (size_t)cls * M * M;
+  __shared__ int ok;
+  if (bulk) {
+    // warp 0 issues the copies: lane 0 arms the mbarrier with the tile's
+    // byte count, then every lane copies its own elements (their indices are
+    // loaded in parallel, not one after another)
+    if (threadIdx.x < 32) {
+      const unsigned mm = (unsigned)(M * M * sizeof(S)), col = (unsigned)(M * sizeof(S));
+      if (threadIdx.x == 0) {
+        mbar_init(bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"(mm + (unsigned)cnt * col)
+                     : "memory");
+        bulk_g2s(Ts, T, mm, bar);
+      }
+      __syncwarp();
+      for (int t = threadIdx.x; t < cnt; t += 32)
+        bulk_g2s(Xs + (size_t)t * XS, v + (size_t)__ldg(elems + start + t) * M, col, bar);
+      if (threadIdx.x == 0) ok = mbar_wait(bar, 0) ? 1 : 0;
+    }
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < M * M; i += blockDim.x) Ts[i] = T[i];
+    for (int i = threadIdx.x; i < M * cnt; i += blockDim.x)
+      Xs[(size_t)(i / M) * XS + i % M] = v[(size_t)elems[start + i / M] * M + i % M];
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+  }
+  const int rg = threadIdx.x & 15, eg = threadIdx.x >> 4;  // 16 x 16 thread grid
+  constexpr int RT = 8;                                    // rows per thread (M <= 128)
+  S acc[RT][4];
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = S(0);
+  const int nr = (M - rg + 15) / 16;
+  const S* xb = Xs + (size_t)eg * XS;
+  for (int k = 0; k < M; ++k) {
+    S b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = xb[(size_t)16 * j * XS + k];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      if (i < nr) {
+        const S a = Ts[(size_t)k * M + rg + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a * b[j];
+      }
+    }
+  }
+  const S bad = ok ? S(0) : S(nan(""));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int t = eg + 16 * j;
+    if (t >= cnt) continue;
+    const int e = elems[start + t];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      const int r = rg + 16 * i;
+      if (i >= nr) continue;
+      const int F = r / n, tt = r % n, e2 = dev_neighbour(g, e, F);
+      if (e2 >= 0) {
+        const size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
+        y[sl] = v[sl] + acc[i][j] + bad;
+      } else {
+        y[(size_t)e * M + r] = Xs[(size_t)t * XS + r] + bad;
+      }
+    }
+  }
+}
+
 template <typename S>
 inline size_t schur_stream_batch_smem(unsigned ring, int Mmax) {
   return ring + kRingSlots * (8 + sizeof(ElemMeta<S>)) + (2 * (size_t)Mmax + 256) * sizeof(S) + 64;
@@ -902,6 +1005,14 @@ struct smpm_handle_s {
   smpm_opts opts{};
   bool factored = false;
   bool op_factored = false;  // operator-only factor step (SMPM_FLAG_OPERATOR_ONLY): S can be applied
+  // element classes (face-type masks) for the class-shared apply
+  int ncls = 0, ntiles = 0, cls_ok = 0;  // cls_ok: the kernel's shared-memory limit is set
+  double* dTcls = nullptr;   // ncls * M*M, column-major
+  float* dTcls32 = nullptr;
+  int* dtiles = nullptr;     // ntiles * (class, first, count) into dclsel
+  int* dclsel = nullptr;     // nel: elements sorted by class
+  double* dHT = nullptr;     // H column-major, for the fused coarse solve of the Arnoldi steps
+  double* wchatd = nullptr;  // 2 d: its two c_hat buffers
   Factors f;
   DevGeo dg{};
   // device factors
@@ -1039,6 +1150,10 @@ void free_lock(smpm_handle h) {
   h->lk.has32 = false;
 }
 
+// Frees every device allocation and event of the handle and resets all of
+// its device state (pointers, launch shapes, staging sizes) to the state of
+// a fresh handle, keeping the geometry and the launch count: no pointer of an
+// earlier factor step survives a re-factor with other options.
 void free_all(smpm_handle h) {
   free_lock(h);
   for (void* p : h->allocs) cudaFree(p);
@@ -1047,6 +1162,13 @@ void free_all(smpm_handle h) {
     if (*ev) cudaEventDestroy(*ev);
     *ev = nullptr;
   }
+  const Geometry g = h->g;
+  const smpm_opts opts = h->opts;
+  const long long launches = h->launches;
+  *h = smpm_handle_s();
+  h->g = g;
+  h->opts = opts;
+  h->launches = launches;
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -1161,20 +1283,25 @@ smpm_status launch_defl(smpm_handle h, const double* y, const double* chat, int 
 
 // SMPM_TRACE: per-tag mean SM cycles between consecutive trace points of CTA 0.
 smpm_status print_trace(smpm_handle h, cudaStream_t st) {
-  std::vector<long long> tr(kTraceCap);
+  std::vector<long long> tr(kTraceCap + 4, 0);
   CU(cudaMemcpyAsync(tr.data(), h->wtrace, kTraceCap * sizeof(long long), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  double sum[64] = {0};
-  long long cnt[64] = {0};
-  for (int i = 0; i + 3 < kTraceCap && tr[i + 2] != 0; i += 2) {
-    int tag = (int)tr[i];
-    if (tag >= 0 && tag < 64) {
-      sum[tag] += (double)(tr[i + 3] - tr[i + 1]);
-      cnt[tag] += 1;
+  double sum[80] = {0};
+  long long cnt[80] = {0};
+  // three regions: the GMRES kernel from 0, the pre kernel from cap/2, the
+  // post kernel from 3 cap/4
+  for (int r0 : {0, kTraceCap / 2, 3 * (kTraceCap / 4)}) {
+    const int r1 = r0 == 0 ? kTraceCap / 2 : r0 + kTraceCap / 4;
+    for (int i = r0; i + 3 < r1 && tr[i + 2] != 0; i += 2) {
+      int tag = (int)tr[i];
+      if (tag >= 0 && tag < 80) {
+        sum[tag] += (double)(tr[i + 3] - tr[i + 1]);
+        cnt[tag] += 1;
+      }
     }
   }
   std::fprintf(stderr, "[smpm trace] mean SM cycles from tag to next trace point (CTA 0)\n");
-  for (int t = 0; t < 64; ++t)
+  for (int t = 0; t < 80; ++t)
     if (cnt[t]) std::fprintf(stderr, "  tag %2d  n %5lld  cycles %10.0f\n", t, cnt[t], sum[t] / cnt[t]);
   CU(cudaMemsetAsync(h->wtrace, 0, kTraceCap * sizeof(long long), st));
   return SMPM_OK;
@@ -1242,10 +1369,13 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   a.stream_mats = h->gm.stream_mats; a.buf_elems = h->gm.buf_elems; a.nbuf = h->gm.nbuf;
   a.warp_elems = h->gm.warp_elems;
   a.trace = h->wtrace;
-  a.trace_cap = h->wtrace ? kTraceCap : 0;
+  a.trace_cap = h->wtrace ? kTraceCap / 2 : 0;
   a.skip = nullptr;
   a.G = h->gm.grid;
   a.base = 0;
+  a.fused = (!adj && h->dHT) ? 1 : 0;
+  a.HT = adj ? nullptr : h->dHT;
+  a.chatd = h->wchatd;
   return a;
 }
 
@@ -1270,6 +1400,9 @@ GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
   a.skip = h->wdone;
   a.G = h->gm.grid;
   a.base = 0;
+  a.fused = h->dHT ? 1 : 0;
+  a.HT = h->dHT;
+  a.chatd = h->wchatd;
   return a;
 }
 
@@ -1356,7 +1489,7 @@ smpm_status solve_one_mixed(smpm_handle h, const double* f, const double* gn, do
     a.its_out = reinterpret_cast<int*>(h->wctl + 592) + ref;
     if (ref == 0 && h->wtrace) {
       a.trace = h->wtrace;
-      a.trace_cap = kTraceCap;
+      a.trace_cap = kTraceCap / 2;
     }
     {
       void* args[] = {&a};
@@ -1440,6 +1573,10 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   CU(cudaMemsetAsync(h->wctl, 0, kCtlBytes, st));
   PrePostArgs P = prepost_args(h, tol, f, gn, u, false, adj, gg);
   P.ga.bar = h->wbar + 0;
+  if (h->wtrace) {  // pre and post trace into the upper halves of the buffer
+    P.ga.trace = h->wtrace + kTraceCap / 2;
+    P.ga.trace_cap = kTraceCap / 4;
+  }
   {
     void* args[] = {&P};
     CU(cudaEventRecord(h->evp, st));
@@ -1459,6 +1596,7 @@ smpm_status solve_one(smpm_handle h, const double* f, const double* gn, double* 
   CU(cudaEventRecord(h->ev1, st));
   {
     P.ga.bar = h->wbar + 2;
+    if (h->wtrace) P.ga.trace = h->wtrace + 3 * (kTraceCap / 4);
     void* args[] = {&P};
     CU(cudaLaunchCooperativeKernel((const void*)k_post, dim3(h->gm.grid), dim3(kGmresThreads), args, h->gm.smem_pp,
                                    st));
@@ -1518,8 +1656,7 @@ smpm_status lalloc(smpm_handle h, P** p, size_t count) {
 // inner GMRES 2 + 2 ref, refinement 3 + 2 ref), err at 128; column k's block
 // at kLockCtlBytes + k kLockColBytes: acc8 (8 doubles) | done, nref (ints at
 // +64) | rn[kMaxRefine] at +128
-constexpr size_t kLockCtlBytes = 256;
-constexpr size_t kLockColBytes = 256;
+constexpr size_t kLockCtlBytes = 256;  // (kLockColBytes, the column block size, is shared with the batch)
 
 // columns per element work item: the largest of maxrc, ..., 2, 1 that
 // divides R and still gives `warps` warps of a CTA an item (all warps busy:
@@ -1716,7 +1853,7 @@ smpm_status solve_lock(smpm_handle h, const double* f, const double* gn, double*
     A.done = nullptr; A.done_stride = 0;
     if (h->wtrace) {
       A.a.trace = h->wtrace;
-      A.a.trace_cap = kTraceCap;
+      A.a.trace_cap = kTraceCap / 2;
     }
     void* args[] = {&A};
     CU(cudaLaunchCooperativeKernel((const void*)k_gmres_lock<double>, dim3(h->gm.grid), dim3(kGmresThreads), args,
@@ -1735,7 +1872,7 @@ smpm_status solve_lock(smpm_handle h, const double* f, const double* gn, double*
       A.done_stride = (int)(kLockColBytes / sizeof(int));
       if (h->wtrace && ref == 0) {
         A.a.trace = h->wtrace;
-        A.a.trace_cap = kTraceCap;
+        A.a.trace_cap = kTraceCap / 2;
       }
       {
         void* args[] = {&A};
@@ -1835,6 +1972,7 @@ struct smpm_batch_s {
   int* herr = nullptr;           // pinned
   std::vector<void*> allocs;     // device memory of the current team layout
   std::vector<long long> task_of;  // report index of (problem p, rhs k): task_of[foff-like prefix]
+  std::vector<long long> task_col; // first right-hand side (report index) of each task
   std::vector<long long> rhs_base;
   cudaStream_t bs = nullptr;
   cudaGraph_t graph = nullptr;
@@ -1912,6 +2050,8 @@ smpm_status batch_layout(smpm_batch b, int T) {
     float* vown32;
     double* wscr64;
     float* wscr32;
+    int lock;       // 1: the problem's right-hand sides run as lockstep groups
+    size_t lsmem;   // shared memory of its lockstep body (bound over its groups)
   };
   std::vector<PL> pl(np);
   size_t smem = 0;
@@ -1947,7 +2087,17 @@ smpm_status batch_layout(smpm_batch b, int T) {
     L.lay = lay_for(L.wg);
     if (mixed && warp)  // the refinement body runs the warp phases too
       L.lay.smem = std::max(L.lay.smem, refine_smem_bytes(m, g.M, g.n, L.ES, L.nown_b, L.nown_w, g.d, L.wg, true));
-    const size_t nd = kBatchHdr + std::max(need_fixed(L.wg), L.lay.smem);
+    // several right-hand sides of a block-Jacobi problem: lockstep groups of
+    // up to kLockMaxCols columns when their body fits (bound: the widest tile)
+    L.lock = 0;
+    L.lsmem = 0;
+    if (b->nrhs[p] >= 2 && precond > 0 && !(h->opts.flags & SMPM_FLAG_NO_LOCKSTEP)) {
+      const int Rg = std::min(b->nrhs[p], kLockMaxCols);
+      L.lsmem = mixed ? lock_smem_bytes<float>(m, g.M, g.n, Rg, 8, L.nown_b, L.nown_w, false)
+                      : lock_smem_bytes<double>(m, g.M, g.n, Rg, 4, L.nown_b, L.nown_w, false);
+      if (std::max(need_fixed(L.wg), L.lsmem) <= (size_t)budget) L.lock = 1;
+    }
+    const size_t nd = kBatchHdr + std::max(need_fixed(L.wg), L.lock ? L.lsmem : L.lay.smem);
     if (nd > (size_t)optin - 1024)
       return fail(SMPM_EINVAL, "a problem of the batch is too large for teams of this size");
     smem = std::max(smem, nd);
@@ -1956,25 +2106,127 @@ smpm_status batch_layout(smpm_batch b, int T) {
     L.wscr64 = nullptr;
     L.wscr32 = nullptr;
     const size_t vn = (size_t)T * (m + 1) * L.ES;
-    if (!L.lay.basis_smem && !mixed && (st = balloc(b, &L.vown64, vn))) return st;
-    if (!L.lay.basis_smem && mixed && (st = balloc(b, &L.vown32, vn))) return st;
+    if (!L.lock && !L.lay.basis_smem && !mixed && (st = balloc(b, &L.vown64, vn))) return st;
+    if (!L.lock && !L.lay.basis_smem && mixed && (st = balloc(b, &L.vown32, vn))) return st;
     if (L.wg) {
       if ((st = balloc(b, &L.wscr64, (size_t)T * 2 * (L.ES + 1)))) return st;
       if (mixed && (st = balloc(b, &L.wscr32, (size_t)T * 2 * (L.ES + 1)))) return st;
     }
   }
-  // task table
+  // task table: one task per right-hand side, or one per lockstep group of
+  // up to kLockMaxCols right-hand sides of a problem (per-column arguments in
+  // global memory, work vectors in a workspace of the team sized for the
+  // largest group it runs)
   std::vector<BatchTask> tasks;
   std::vector<int> begin(b->nteams + 1, 0);
   b->task_of.assign(b->ntasks, -1);
+  b->task_col.clear();
+  long long ncol_groups = 0;
+  for (int p = 0; p < np; ++p)
+    if (pl[p].lock)
+      for (int k0 = 0; k0 < b->nrhs[p]; k0 += kLockMaxCols)
+        if (std::min(kLockMaxCols, b->nrhs[p] - k0) >= 2) ncol_groups += std::min(kLockMaxCols, b->nrhs[p] - k0);
+  PrePostArgs* dPc = nullptr;
+  RefineArgs* dRc = nullptr;
+  std::vector<PrePostArgs> hPc;
+  std::vector<RefineArgs> hRc;
+  if (ncol_groups > 0) {
+    if ((st = balloc(b, &dPc, 2 * (size_t)ncol_groups)) || (st = balloc(b, &dRc, (size_t)kMaxRefine * ncol_groups)))
+      return st;
+    hPc.reserve(2 * (size_t)ncol_groups);
+    hRc.reserve((size_t)kMaxRefine * ncol_groups);
+  }
   for (int t = 0; t < b->nteams; ++t) {
     begin[t] = (int)tasks.size();
+    // ---- the team's lockstep workspace: the largest group it runs
+    struct {
+      size_t R = 0, r = 0, kp = 0, d = 0, acc = 0, Rh = 0, yv = 0, V64 = 0, W64 = 0, V32 = 0, W32 = 0;
+      bool f64 = false, f32 = false;
+    } need;
+    for (int p : plist[t]) {
+      if (!pl[p].lock) continue;
+      smpm_handle h = b->hs[p];
+      const Geometry& g = h->g;
+      const size_t R = (size_t)std::min(b->nrhs[p], kLockMaxCols), m = h->opts.restart, ES = pl[p].ES;
+      const bool mixed = (b->precision < 0 ? h->opts.precision : b->precision) == 1;
+      need.R = std::max(need.R, R);
+      need.r = std::max(need.r, (size_t)g.r);
+      need.kp = std::max(need.kp, (size_t)g.kp);
+      need.d = std::max(need.d, (size_t)g.d);
+      need.acc = std::max(need.acc, (2 * m + 1) * R * (m + 3));
+      need.Rh = std::max(need.Rh, R * m * (m + 1));
+      need.yv = std::max(need.yv, R * m);
+      if (mixed) {
+        need.f32 = true;
+        need.V32 = std::max(need.V32, (size_t)T * (m + 1) * R * ES);
+        need.W32 = std::max(need.W32, (size_t)T * 2 * R * (ES + 1));
+      } else {
+        need.f64 = true;
+        need.V64 = std::max(need.V64, (size_t)T * (m + 1) * R * ES);
+        need.W64 = std::max(need.W64, (size_t)T * 2 * R * (ES + 1));
+      }
+    }
+    double *wb = nullptr, *wbS = nullptr, *wrg = nullptr, *wcb = nullptr, *wchatb = nullptr, *wxs = nullptr;
+    double *wc = nullptr, *wchat = nullptr, *wacc = nullptr, *wRh = nullptr, *wyv = nullptr;
+    double *wx = nullptr, *wt = nullptr, *wy = nullptr, *wvg = nullptr, *wV = nullptr, *wW = nullptr, *wcr = nullptr;
+    float *wx32 = nullptr, *wt32 = nullptr, *wy32 = nullptr, *wvg32 = nullptr, *wrg32 = nullptr, *wV32 = nullptr,
+          *wW32 = nullptr;
+    LockColState* wcs = nullptr;
+    unsigned char* wctl = nullptr;
+    if (need.R > 0) {
+      const size_t R = need.R;
+      if ((st = balloc(b, &wb, R * need.r)) || (st = balloc(b, &wbS, R * need.kp)) ||
+          (st = balloc(b, &wrg, R * need.kp)) || (st = balloc(b, &wcb, R * need.d)) ||
+          (st = balloc(b, &wchatb, R * need.d)) || (st = balloc(b, &wxs, R * need.kp)) ||
+          (st = balloc(b, &wc, R * need.d)) || (st = balloc(b, &wchat, R * need.d)) ||
+          (st = balloc(b, &wacc, need.acc)) || (st = balloc(b, &wRh, need.Rh)) || (st = balloc(b, &wyv, need.yv)) ||
+          (st = balloc(b, &wcs, R)) || (st = balloc(b, &wctl, R * kLockColBytes)))
+        return st;
+      if (need.f64 && ((st = balloc(b, &wx, R * need.kp)) || (st = balloc(b, &wt, R * need.kp)) ||
+                       (st = balloc(b, &wy, R * need.kp)) || (st = balloc(b, &wvg, R * need.kp)) ||
+                       (st = balloc(b, &wV, need.V64)) || (st = balloc(b, &wW, need.W64))))
+        return st;
+      if (need.f32 && ((st = balloc(b, &wx32, R * need.kp)) || (st = balloc(b, &wt32, R * need.kp)) ||
+                       (st = balloc(b, &wy32, R * need.kp)) || (st = balloc(b, &wvg32, R * need.kp)) ||
+                       (st = balloc(b, &wrg32, R * need.kp)) || (st = balloc(b, &wcr, R * need.d)) ||
+                       (st = balloc(b, &wV32, need.V32)) || (st = balloc(b, &wW32, need.W32))))
+        return st;
+      // work vectors start at zero (boundary-face slots are never written)
+      for (double* v : {wt, wy, wvg})
+        if (v) CU(cudaMemset(v, 0, R * need.kp * sizeof(double)));
+      for (float* v : {wt32, wy32, wvg32})
+        if (v) CU(cudaMemset(v, 0, R * need.kp * sizeof(float)));
+    }
     for (int p : plist[t]) {
       smpm_handle h = b->hs[p];
       const PL& L = pl[p];
       const bool mixed = (b->precision < 0 ? h->opts.precision : b->precision) == 1;
       const double tol = h->opts.tol;
-      for (int k = 0; k < b->nrhs[p]; ++k) {
+      auto team_fields = [&](auto& a) {
+        a.G = T;
+        a.base = t * T;
+        a.nown_b = L.nown_b;
+        a.nown_w = L.nown_w;
+        a.ES = L.ES;
+        a.mats_smem = 0;
+        a.basis_smem = 0;
+        a.stream_mats = 0;
+        a.bar = b->dbars + t;
+        a.err = b->derr;
+        a.trace = nullptr;
+        a.trace_cap = 0;
+        a.skip = nullptr;
+        a.its_out = nullptr;
+      };
+      auto layout_fields = [&](auto& a) {
+        a.mats_smem = L.lay.mats_smem;
+        a.basis_smem = L.lay.basis_smem;
+        a.stream_mats = L.lay.stream_mats;
+        a.buf_elems = L.lay.buf_elems;
+        a.nbuf = L.lay.nbuf;
+        a.warp_elems = L.lay.warp_elems;
+      };
+      auto single_task = [&](int k) {
         BatchTask bt{};
         bt.P = prepost_args(h, tol, nullptr, nullptr, nullptr, mixed);
         auto team_fields = [&](auto& a) {
@@ -2027,10 +2279,147 @@ smpm_status batch_layout(smpm_batch b, int T) {
         bt.ctl = h->wctl;
         bt.its = reinterpret_cast<int*>(h->wctl + 592);
         bt.rn = h->wrn;
-        b->task_of[b->rhs_base[p] + k] = (long long)tasks.size();
+        bt.rep0 = b->rhs_base[p] + k;
+        b->task_of[b->rhs_base[p] + k] = b->rhs_base[p] + k;
+        b->task_col.push_back(b->rhs_base[p] + k);
+        tasks.push_back(bt);
+      };
+      for (int k0 = 0; k0 < b->nrhs[p]; k0 += (L.lock ? kLockMaxCols : 1)) {
+        const int R = L.lock ? std::min(kLockMaxCols, b->nrhs[p] - k0) : 1;
+        if (R == 1) {
+          single_task(k0);
+          continue;
+        }
+        const Geometry& g = h->g;
+        BatchTask bt{};
+        bt.P = prepost_args(h, tol, nullptr, nullptr, nullptr, mixed);
+        team_fields(bt.P.ga);
+        bt.P.ga.vown = nullptr;
+        bt.P.ga.wscr = L.wscr64;
+        bt.precision = mixed ? 1 : 0;
+        bt.has_g = 1;
+        bt.f_off = b->foff[p] + (long long)k0 * g.r;
+        bt.u_off = bt.f_off;
+        bt.g_off = b->goff[p] + (long long)k0 * g.kp;
+        bt.ncols = R;
+        bt.rep0 = b->rhs_base[p] + k0;
+        bt.r_len = g.r;
+        bt.kp_len = g.kp;
+        bt.lctl = wctl;
+        const size_t c0 = hPc.size() / 2;  // first column slot of this group in the argument arrays
+        bt.Pc = dPc + 2 * c0;
+        bt.Rc = dRc + (size_t)kMaxRefine * c0;
+        std::vector<PrePostArgs> pre(R), post(R);
+        for (int c = 0; c < R; ++c) {
+          PrePostArgs P = bt.P;
+          P.b = wb + (size_t)c * g.r;
+          P.bS = wbS + (size_t)c * g.kp;
+          P.rg = wrg + (size_t)c * g.kp;
+          P.cb = wcb + (size_t)c * g.d;
+          P.chatb = wchatb + (size_t)c * g.d;
+          P.xs = wxs + (size_t)c * g.kp;
+          P.acc = reinterpret_cast<double*>(wctl + (size_t)c * kLockColBytes);
+          P.gacc = nullptr;
+          P.gacc_n = 0;
+          if (!mixed) {
+            P.ga.x = wx + (size_t)c * g.kp;
+            double* zs[7] = {P.ga.x, h->wt, h->wy, h->wV, P.bS, P.rg, P.xs};
+            for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+          } else {
+            double* zs[7] = {h->wx, h->wt, h->wy, h->wV, P.bS, P.rg, P.xs};
+            for (int i = 0; i < 7; ++i) P.zero[i] = zs[i];
+            float* z32[4] = {wx32 + (size_t)c * g.kp, wt32, wy32, wvg32};
+            for (int i = 0; i < 4; ++i) P.zero32[i] = z32[i];
+            P.cr = wcr + (size_t)c * g.d;
+            P.rg32 = wrg32 + (size_t)c * g.kp;
+          }
+          P.assembled = 0;
+          pre[c] = P;
+          P.assembled = mixed ? 1 : 0;
+          post[c] = P;
+        }
+        hPc.insert(hPc.end(), pre.begin(), pre.end());
+        hPc.insert(hPc.end(), post.begin(), post.end());
+        hRc.resize(hRc.size() + (size_t)kMaxRefine * R);
+        auto lock_fields = [&](auto& A, int maxrc) {
+          team_fields(A.a);
+          A.a.mats_smem = 0;
+          A.a.basis_smem = 0;
+          A.a.stream_mats = 0;
+          A.a.warp_elems = 1;
+          A.a.wscr = nullptr;
+          A.a.vown = nullptr;
+          A.a.fused = 0;
+          A.a.c = wc;
+          A.a.chat = wchat;
+          A.a.acc = wacc;
+          A.R = R;
+          A.RC = lock_rc(R, L.nown_b, maxrc, kGmresThreads / 32);
+          A.vs = g.kp;
+          A.ds = g.d;
+          A.cs = wcs;
+          A.Rh = wRh;
+          A.yv = wyv;
+        };
+        if (!mixed) {
+          bt.L64.a = gmres_args(h, tol);
+          lock_fields(bt.L64, 4);
+          bt.L64.a.rhs = wrg;
+          bt.L64.a.x = wx;
+          bt.L64.a.t = wt;
+          bt.L64.a.y = wy;
+          bt.L64.a.vglob = wvg;
+          bt.L64.V = wV;
+          bt.L64.W = wW;
+          bt.L64.done = nullptr;
+          bt.L64.done_stride = 0;
+        } else {
+          bt.L32.a = gmres_args32(h, kInnerTol);
+          lock_fields(bt.L32, 8);
+          bt.L32.a.rhs = wrg32;
+          bt.L32.a.x = wx32;
+          bt.L32.a.t = wt32;
+          bt.L32.a.y = wy32;
+          bt.L32.a.vglob = wvg32;
+          bt.L32.V = wV32;
+          bt.L32.W = wW32;
+          bt.L32.done = reinterpret_cast<const int*>(wctl + 64);
+          bt.L32.done_stride = (int)(kLockColBytes / sizeof(int));
+          for (int ref = 0; ref < kMaxRefine; ++ref)
+            for (int c = 0; c < R; ++c) {
+              GmresArgs<float> a = gmres_args32(h, kInnerTol);
+              team_fields(a);
+              a.warp_elems = L.lay.warp_elems;
+              a.wscr = L.wscr32;
+              a.x = wx32 + (size_t)c * g.kp;
+              a.t = wt32;
+              a.y = wy32;
+              a.vglob = wvg32;
+              a.rhs = wrg32 + (size_t)c * g.kp;
+              RefineArgs RA = refine_args(h, a, tol);
+              RA.ga.warp_elems = L.lay.warp_elems;
+              RA.xS = wxs + (size_t)c * g.kp;
+              RA.bS = wbS + (size_t)c * g.kp;
+              RA.cr = wcr + (size_t)c * g.d;
+              RA.chat_r = wchatb + (size_t)c * g.d;
+              unsigned char* blk = wctl + (size_t)c * kLockColBytes;
+              RA.rgn = reinterpret_cast<double*>(blk) + ACC_RGN;
+              RA.rn = reinterpret_cast<double*>(blk + 128) + ref;
+              RA.done = reinterpret_cast<int*>(blk + 64);
+              RA.nref = reinterpret_cast<int*>(blk + 68);
+              RA.rhs32 = wrg32 + (size_t)c * g.kp;
+              hRc[(size_t)kMaxRefine * c0 + (size_t)ref * R + c] = RA;
+            }
+        }
+        for (int c = 0; c < R; ++c) b->task_of[b->rhs_base[p] + k0 + c] = b->rhs_base[p] + k0 + c;
+        b->task_col.push_back(b->rhs_base[p] + k0);
         tasks.push_back(bt);
       }
     }
+  }
+  if (!hPc.empty()) {
+    CU(cudaMemcpy(dPc, hPc.data(), hPc.size() * sizeof(PrePostArgs), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dRc, hRc.data(), hRc.size() * sizeof(RefineArgs), cudaMemcpyHostToDevice));
   }
   begin[b->nteams] = (int)tasks.size();
   std::vector<int> team_of(sms, -1);
@@ -2293,6 +2682,54 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
 
 namespace {
 
+// Class tables of the class-shared apply: one T per face-type mask (the
+// copies of T_e within a class are identical), tiles of kClassTile elements.
+smpm_status upload_classes(smpm_handle h, const std::vector<double>& Tc, cudaStream_t st) {
+  const Geometry& g = h->g;
+  const size_t MM = (size_t)g.M * g.M;
+  std::vector<int> cls_of_mask(16, -1), first;
+  std::vector<std::vector<int>> members;
+  for (long long e = 0; e < g.nel; ++e) {
+    const int key = g.mask((int)e);
+    if (cls_of_mask[key] < 0) {
+      cls_of_mask[key] = (int)members.size();
+      members.emplace_back();
+      first.push_back((int)e);
+    }
+    members[cls_of_mask[key]].push_back((int)e);
+  }
+  std::vector<double> Tcls(members.size() * MM);
+  for (size_t c = 0; c < members.size(); ++c)
+    std::copy(Tc.begin() + (size_t)first[c] * MM, Tc.begin() + (size_t)(first[c] + 1) * MM, Tcls.begin() + c * MM);
+  std::vector<int> sel, tiles;
+  for (size_t c = 0; c < members.size(); ++c) {
+    const int base = (int)sel.size();
+    sel.insert(sel.end(), members[c].begin(), members[c].end());
+    for (int i = 0; i < (int)members[c].size(); i += kClassTile) {
+      tiles.push_back((int)c);
+      tiles.push_back(base + i);
+      tiles.push_back(std::min(kClassTile, (int)members[c].size() - i));
+    }
+  }
+  smpm_status s;
+  if ((s = upload(h, &h->dTcls, Tcls, st)) || (s = upload(h, &h->dtiles, tiles, st)) ||
+      (s = upload(h, &h->dclsel, sel, st)))
+    return s;
+  if (h->opts.precision == 1 && (s = upload(h, &h->dTcls32, std::vector<float>(Tcls.begin(), Tcls.end()), st)))
+    return s;
+  h->ncls = (int)members.size();
+  h->ntiles = (int)(tiles.size() / 3);
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (g.M <= 128 && class_smem(g.M, sizeof(double)) <= (size_t)optin) {
+    CU(set_smem_limit(k_schur_class<double>, optin));
+    CU(set_smem_limit(k_schur_class<float>, optin));
+    h->cls_ok = 1;
+  }
+  return SMPM_OK;
+}
+
 smpm_status factor_device_operator(smpm_handle h, cudaStream_t st) {
   const Geometry& g = h->g;
   DevGeo& dg = h->dg;
@@ -2318,6 +2755,7 @@ smpm_status factor_device_operator(smpm_handle h, cudaStream_t st) {
   }
   if ((s = upload(h, &h->dtab64, t64, st))) return s;
   if (h->dT32 && (s = upload(h, &h->dtab32, t32, st))) return s;
+  if ((s = upload_classes(h, Tc, st))) return s;
   CU(cudaStreamSynchronize(st));
   h->f.T.clear();
   h->f.T.shrink_to_fit();
@@ -2473,6 +2911,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       }
       if ((s = upload(h, &h->dtab64, t64, st))) return s;
       if (h->dT32 && (s = upload(h, &h->dtab32, t32, st))) return s;
+      if ((s = upload_classes(h, Tc, st))) return s;
     }
     if (h->f.has_adjoint) {
       // T~_e = T_e^T: its column-major device copy is T_e row-major
@@ -2501,6 +2940,12 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
     h->wrn = reinterpret_cast<double*>(h->wctl + 336);
     if ((s = dalloc(h, &h->wacc, (size_t)(2 * m + 1) * (m + 3)))) return s;
     if (!gm.basis_smem && (s = dalloc(h, &h->wvown, (size_t)gm.grid * (m + 1) * gm.ES))) return s;
+    if (opts.precond == 2 && g.d * (long long)gm.grid <= kFusedCoarseMaxAdds) {
+      std::vector<double> HT((size_t)g.d * g.d);
+      for (long long r = 0; r < g.d; ++r)
+        for (long long j = 0; j < g.d; ++j) HT[(size_t)j * g.d + r] = h->f.H[(size_t)r * g.d + j];
+      if ((s = upload(h, &h->dHT, HT, st)) || (s = dalloc(h, &h->wchatd, 2 * (size_t)g.d))) return s;
+    }
   }
   CU(cudaStreamSynchronize(st));
   h->factored = true;
@@ -2625,6 +3070,41 @@ smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* st
     return SMPM_OK;
   }
   return launch_schur_stream<float>(h, h->dT32, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename S>
+smpm_status launch_schur_class(smpm_handle h, const S* T, const S* v, S* y, cudaStream_t st) {
+  if (!h->cls_ok) return fail(SMPM_EINVAL, "the class-shared apply needs n <= 32 and its tile in shared memory");
+  const int bulk = (reinterpret_cast<uintptr_t>(v) % 16 == 0) ? 1 : 0;  // bulk copies need 16-byte alignment
+  k_schur_class<S><<<(unsigned)h->ntiles, 256, class_smem(h->g.M, sizeof(S)), st>>>(h->dg, T, h->dtiles, h->dclsel,
+                                                                                      v, y, bulk);
+  CHECK_LAUNCH();
+  return SMPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+smpm_status smpm_apply_schur_class(smpm_handle h, const double* v, double* y, void* stream) try {
+  NEED_OPERATOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  return launch_schur_class<double>(h, h->dTcls, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
+}
+
+smpm_status smpm_apply_schur_class32(smpm_handle h, const float* v, float* y, void* stream) try {
+  NEED_OPERATOR();
+  if (!v || !y) return fail(SMPM_EINVAL, "null vector");
+  if (!h->dTcls32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
+  return launch_schur_class<float>(h, h->dTcls32, v, y, as_stream(stream));
 } catch (...) {
   return host_exception();
 }
@@ -2938,9 +3418,10 @@ smpm_status smpm_batch_solve(smpm_batch b, const double* f, const double* g, dou
   if (b->herr[0]) {  // code, first failing task + 1, body (see k_batch)
     std::string where = "unknown";
     const long long t = (long long)b->herr[1] - 1;
-    for (size_t p = 0; p < b->hs.size() && t >= 0; ++p)
+    const long long col = (t >= 0 && t < (long long)b->task_col.size()) ? b->task_col[t] : -1;
+    for (size_t p = 0; p < b->hs.size() && col >= 0; ++p)
       for (int k = 0; k < b->nrhs[p]; ++k)
-        if (b->task_of[b->rhs_base[p] + k] == t) where = "problem " + std::to_string(p) + " rhs " + std::to_string(k);
+        if (b->rhs_base[p] + k == col) where = "problem " + std::to_string(p) + " rhs " + std::to_string(k);
     static const char* what[] = {"?", "start barrier", "pre", "GMRES", "refinement", "post"};
     const int w = (b->herr[2] >= 0 && b->herr[2] <= 5) ? b->herr[2] : 0;
     return fail(SMPM_ETIMEOUT, std::string(b->herr[0] == 2 ? "a matrix copy wait" : "a team barrier") +

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1601_03432_gb300 import Batch, Grid, factor_many, inputs
+from paper_1601_03432_gb300 import _binding as B
 from oracle.smpm import SMPMGrid
 from oracle.schur import SchurSystem
 from oracle import methods
@@ -195,3 +196,31 @@ def test_batched_apply_matches_single_grid_apply(built, kind):
         pad = np.setdiff1d(np.arange(og.kp), og.padded_index)
         assert np.all(h64[o + pad] == 0) and np.all(h32[o + pad] == 0)
         o += og.kp
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 1e-10), (1, 1e-9)], ids=["fp64", "mixed"])
+def test_batch_lockstep_groups_match_one_at_a_time(built, precision, bound):
+    """Problems with several right-hand sides run as lockstep groups inside
+    the batched launch (up to 16 columns per group; 19 right-hand sides make
+    a group of 16 and a group of 3; 1 stays a single task).  Every column
+    matches the oracle's direct solve and the batch whose handles ask for one
+    right-hand side at a time (SMPM_FLAG_NO_LOCKSTEP)."""
+    probs = [(4, 3, 6, 5), (5, 4, 7, 19), (3, 3, 8, 1), (6, 5, 5, 2)]
+    fs, gs, refs = make_inputs(probs, 31)
+    f, g = packed(fs), packed(gs)
+    sols = []
+    for flags in (0, B.FLAG_NO_LOCKSTEP):
+        grids = [Grid(mx, my, n) for (mx, my, n, _) in probs]
+        factor_many(grids, tol=1e-12 if precision == 0 else 1e-11, precision=precision, flags=flags)
+        b = Batch(grids, [k for *_, k in probs], team_size=8)
+        u = torch.zeros_like(f)
+        reps = b.solve(f, u, g=g)
+        assert all(r["converged"] == 1 for r in reps), reps
+        uh = u.cpu().numpy()
+        o = 0
+        for ref in refs:
+            assert rel(uh[o:o + ref.size], ref) < bound
+            o += ref.size
+        sols.append(uh)
+        b.close()
+    assert rel(sols[0], sols[1]) < bound

@@ -389,3 +389,83 @@ def test_literal_robin_reading(built, mx, my, n, Lx, Ly):
     assert rep["converged"] == 1
     assert rel(host(u), ud) < 1e-10
     assert abs(rep["iterations"] - info["iterations"]) <= 1, (rep, info["iterations"])
+
+
+def test_operator_only_factor(built):
+    """SMPM_FLAG_OPERATOR_ONLY builds only T_e: the FP64 and FP32 applies
+    equal those of a full factor step (and the oracle's S); every other
+    call is refused with ESTATE."""
+    og = SMPMGrid(5, 4, 7)
+    osys = SchurSystem(og)
+    full, op = Grid(5, 4, 7), Grid(5, 4, 7)
+    full.factor(precision=1)
+    op.factor(precision=1, flags=B.FLAG_OPERATOR_ONLY)
+    v = np.random.default_rng(43).standard_normal(og.k)
+    vp = dev(og.to_padded(v))
+    a, b = torch.zeros_like(vp), torch.zeros_like(vp)
+    full.apply_schur(vp, a)
+    op.apply_schur(vp, b)
+    assert torch.equal(a, b)
+    assert rel(og.from_padded(host(b)), osys.apply_S(v)) < 1e-12
+    a32, b32 = torch.zeros_like(vp, dtype=torch.float32), torch.zeros_like(vp, dtype=torch.float32)
+    full.apply_schur32(vp.float(), a32)
+    op.apply_schur32(vp.float(), b32)
+    assert torch.equal(a32, b32)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    for call in (lambda: op.solve(torch.ones_like(u), u), lambda: op.apply_precond(vp, a),
+                 lambda: op.apply_deflation(vp, a), lambda: op.apply_deflation_noalloc(vp, a)):
+        with pytest.raises(B.SmpmError) as ei:
+            call()
+        assert ei.value.status == B.SMPM_ESTATE
+
+
+def test_refactor_with_other_options(built):
+    """A handle factored again with other options keeps no device state of
+    the earlier factor step: FP32 factors are gone after an FP64 factor
+    step, the fused coarse solve of Algorithm 3 is not used by Algorithm 2,
+    and the host-pointer entry re-stages its buffers."""
+    og = SMPMGrid(6, 5, 6)
+    osys = SchurSystem(og)
+    lg = Grid(6, 5, 6)
+    f = inputs.white_noise(og.r, 44)
+    ud = methods.direct_solve(og, og.assemble_L(), osys.u_L, f)
+    u = torch.zeros(og.r, dtype=torch.float64, device="cuda")
+    lg.factor(precision=1, tol=1e-12)
+    uh = np.zeros(og.r)
+    lg.solve_host(f, uh)
+    assert rel(uh, ud) < 1e-9
+    lg.factor(tol=1e-12)
+    with pytest.raises(B.SmpmError) as ei:
+        lg.apply_schur32(torch.zeros(og.kp, dtype=torch.float32, device="cuda"),
+                         torch.zeros(og.kp, dtype=torch.float32, device="cuda"))
+    assert ei.value.status == B.SMPM_ESTATE
+    for precond in (2, 1, 2):
+        lg.factor(tol=1e-12, precond=precond)
+        lg.solve(dev(f), u)
+        assert rel(host(u), ud) < 1e-10, precond
+        uh[:] = 0
+        lg.solve_host(f, uh)
+        assert rel(uh, ud) < 1e-10, precond
+
+
+@pytest.mark.parametrize("mx,my,n", [(5, 4, 8), (9, 7, 5), (70, 3, 4), (2, 3, 32), (12, 10, 9)])
+def test_class_shared_apply(built, mx, my, n):
+    """y = S v by the element-class-shared path (one dense product per
+    face-type class) against the oracle's S and the per-element apply, FP64
+    and FP32; boundary-face slots of y stay zero."""
+    og = SMPMGrid(mx, my, n)
+    osys = SchurSystem(og)
+    lg = Grid(mx, my, n)
+    lg.factor(precision=1)
+    v = np.random.default_rng(45).standard_normal(og.k)
+    vp = dev(og.to_padded(v))
+    a, b = torch.zeros_like(vp), torch.full_like(vp, 7.0)
+    lg.apply_schur(vp, a)
+    lg.apply_schur_class(vp, b)
+    hb = host(b)
+    assert rel(og.from_padded(hb), osys.apply_S(v)) < 1e-12
+    assert rel(hb, host(a)) < 1e-13
+    assert np.all(hb[np.setdiff1d(np.arange(og.kp), og.padded_index)] == 0)
+    b32 = torch.full_like(vp, 7.0, dtype=torch.float32)
+    lg.apply_schur_class32(vp.float(), b32)
+    assert rel(og.from_padded(b32.double().cpu().numpy()), osys.apply_S(v)) < 1e-5
