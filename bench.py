@@ -401,6 +401,7 @@ def run_ours(args):
     # for as short a time as that takes
     batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and world == 1 else None
     config3 = run_config3(args, stream) if world == 1 else None
+    config5 = run_config5(stream) if world == 1 else None
     sweeps = run_sweeps() if world == 1 else None
 
     traffic, traffic_src = kernel_traffic()
@@ -429,6 +430,7 @@ def run_ours(args):
             "schur_apply": schur_apply,
             "batch": batch,
             "config3": config3,
+            "config5": config5,
             "paper_sweeps": sweeps,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
@@ -510,6 +512,46 @@ def run_config3(args, stream):
     out["mixed_over_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     for g in grids.values():
         g.close()
+    return out
+
+
+# ------------------------------------------------- differentiation config
+def run_config5(stream):
+    """48x48 elements, n = 16, FP64, tol 1e-11: the forward solve of a seeded
+    Fourier right-hand side and the adjoint solve (S^T, dl/df and dl/dg) of
+    the loss ||u - u_t||^2, each timed with CUDA events (median of 5)."""
+    import torch
+    from paper_1601_03432_gb300 import Grid, inputs
+    from paper_1601_03432_gb300 import _binding as _B
+    g = Grid(48, 48, 16)
+    t0 = time.perf_counter()
+    g.factor(tol=1e-11, flags=_B.FLAG_ADJOINT)
+    factor_s = time.perf_counter() - t0
+    x, y = g.node_coords()
+    f = torch.as_tensor(inputs.fourier_rhs(x, y, seed=6)[0], dtype=torch.float64, device="cuda")
+    ut = torch.as_tensor(inputs.fourier_rhs(x, y, seed=5)[0], dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    gf = torch.zeros_like(f)
+    gg = torch.zeros(g.kp, dtype=torch.float64, device="cuda")
+    out = {"workload": "48x48 elements, n=16 (r=589824, d=4512), FP64, tol 1e-11, Fourier f (seed 6), "
+                       "u_t Fourier (seed 5)", "factor_s": round(factor_s, 2)}
+    for name, call in (("forward", lambda: g.solve(f, u)[0]),
+                       ("adjoint", lambda: g.solve_adjoint(2.0 * (u - ut), gf, gg)[0])):
+        rep = call()
+        ts = []
+        for _ in range(5):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            rep = call()
+            b_.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a_.elapsed_time(b_))
+        ms = sorted(ts)[len(ts) // 2]
+        out[name] = {"solves_per_s": 1e3 / ms, "ms": round(ms, 3), "iterations": rep["iterations"],
+                     "gmres_us_per_step": round(1e3 * rep["gmres_ms"] / max(rep["iterations"], 1), 1),
+                     "converged": rep["converged"]}
+    out["coarse_bytes_per_step"] = 8 * g.d * g.d
+    g.close()
     return out
 
 
