@@ -46,7 +46,7 @@ def grad_f_g(grid, db):
                 continue
             for t in range(grid.n):
                 a, b = grid.face_node(F, t)
-                dg[e * 4 * grid.n + F * grid.n + t] = grid.tau(F) * db[grid.node(e, a, b)]
+                dg[e * 4 * grid.n + F * grid.n + t] = grid.tau(F, e) * db[grid.node(e, a, b)]
     return db.copy(), dg
 
 
@@ -68,6 +68,9 @@ class AdjointDeflation:
     def __init__(self, sysm):
         self.sysm = sysm
         d = sysm.grid.d
+        if not sysm.coarse_singular:   # graded grid: C^T is nonsingular
+            self.C_lu = sla.lu_factor(sysm.C.T)
+            return
         self.c0hat = sysm.c0 / np.linalg.norm(sysm.c0)
         K = np.zeros((d + 1, d + 1))
         K[:d, :d] = sysm.C.T
@@ -76,6 +79,8 @@ class AdjointDeflation:
         self.K_lu = sla.lu_factor(K)
 
     def coarse_solve(self, r):
+        if not self.sysm.coarse_singular:
+            return sla.lu_solve(self.C_lu, r)
         d = self.sysm.grid.d
         rr = r - self.c0hat * (self.c0hat @ r)
         return sla.lu_solve(self.K_lu, np.concatenate([rr, [0.0]]))[:d]

@@ -15,11 +15,15 @@ of C^-1 is regularised with the left null vector u_C of C.
 Readings of passages the paper leaves open:
 * The right null vector of L is the constant vector (Sec. 1.4), so B 1 is a
   right null vector of S (A 1 + E B 1 = L 1 = 0 gives B A^-1 E (B 1) = -B 1).
-  B 1 = -tau_F p_F is constant on each interface, B 1 = Z c0, so C c0 = 0.
+  B 1 = -tau_F p_F of the receiving face.  Where both sides of every interface
+  carry the same tau_F p_F (uniform grids), B 1 = Z c0 and C c0 = 0.
 * "C \\ r" for the singular C is read as: project r out of u_C, then take the
   solution y of C y = r' with c0^T y = 0 (a bordered solve).  Any other choice
   changes the Schur solution only by a multiple of B 1, i.e. u only by a
   constant, which the zero-mean normalisation removes.
+* On a graded grid where some interface has different h_perp on its two sides,
+  B 1 is not in the range of Z; C is then nonsingular and C \\ r is the plain
+  solve (no u_C, no border).
 * The black checkerboard colour is i_x + i_y even.
 """
 import numpy as np
@@ -45,7 +49,7 @@ class SchurSystem:
         self._lu_cache = {}
         self.A_lu = []
         for e in range(g.nel):
-            key = tuple(g.neighbour(e, F) >= 0 for F in (W, E, S, N))
+            key = tuple(g.neighbour(e, F) >= 0 for F in (W, E, S, N)) + tuple(g.h_of(e))
             if key not in self._lu_cache:
                 self._lu_cache[key] = sla.lu_factor(g.element_A(e))
             self.A_lu.append(self._lu_cache[key])
@@ -187,12 +191,17 @@ class SchurSystem:
         cols = np.array([g.iface_of[(e, F)] for (e, F, t) in g.slots])
         self.Z = sp.csr_matrix((np.ones(g.k), (np.arange(g.k), cols)), shape=(g.k, g.d))
         self.C = (self.Z.T @ (self.S @ self.Z)).toarray()
-        # right null vector of C: B 1 = Z c0
+        # right null vector of C: B 1 = Z c0 when B 1 is constant on each interface
         zb = self.Z.T @ self.B1
-        self.c0 = zb / (2 * g.n)
-        if not np.allclose(self.Z @ self.c0, self.B1, rtol=1e-12, atol=1e-12 * np.abs(self.B1).max()):
-            raise AssertionError("B 1 is not constant on each interface")
+        c0 = zb / (2 * g.n)
+        self.coarse_singular = bool(np.allclose(self.Z @ c0, self.B1, rtol=1e-12,
+                                                atol=1e-12 * np.abs(self.B1).max()))
         d = g.d
+        if not self.coarse_singular:
+            self.c0, self.u_C = None, None
+            self.C_lu = sla.lu_factor(self.C)
+            return
+        self.c0 = c0
         K = np.zeros((d + 1, d + 1))
         K[:d, :d] = self.C
         K[:d, d] = self.c0
@@ -206,7 +215,10 @@ class SchurSystem:
         self.u_C = _fix_sign(y)
 
     def coarse_solve(self, r):
-        """C\\ r regularised (Sec. 2): y with C y = r - u_C (u_C^T r), c0^T y = 0."""
+        """C\\ r regularised (Sec. 2): y with C y = r - u_C (u_C^T r), c0^T y = 0
+        (a plain solve when C is nonsingular)."""
+        if not self.coarse_singular:
+            return sla.lu_solve(self.C_lu, r)
         d = self.grid.d
         rr = r - self.u_C * (self.u_C @ r)
         return sla.lu_solve(self.K_lu, np.concatenate([rr, [0.0]]))[:d]

@@ -5,6 +5,16 @@ passage cited):
 
 * Elements: an m_y x m_x Cartesian grid on [0, L_x] x [0, L_y] (Sec. 1.2, Sec. 3),
   element e = i_y * m_x + i_x covering [i_x h_x, (i_x+1) h_x] x [i_y h_y, (i_y+1) h_y].
+  Graded grids (Sec. 1.2 allows any smooth invertible element map; the
+  axis-aligned case is taken): column edges x_0 < ... < x_mx and row edges
+  y_0 < ... < y_my, element (i_x, i_y) covering [x_ix, x_ix+1] x [y_iy, y_iy+1],
+  so h_x varies by column and h_y by row and neighbours stay conforming.
+* Graded readings of Eq. smpm_poisson: tau_F and p_F of a face use the h_perp of
+  the element that owns the face (the element whose residual row it is), so the
+  two sides of an interface may carry different values; in element e's
+  residual the neighbour's trace enters through the same R (e's p_F), and the
+  neighbour's gradient is taken with the neighbour's own map.  The jump of R u
+  then vanishes for any smooth u, as on a uniform grid.
 * Nodes: n x n GLL points per element, node (a, b) at local index b * n + a (the
   x index a runs fastest), global index e * n^2 + b * n + a; r = n^2 m_x m_y.
 * Faces: W, E, S, N = 0, 1, 2, 3 with outward normals (-1,0), (1,0), (0,-1),
@@ -44,22 +54,46 @@ OPPOSITE = {W: E, E: W, S: N, N: S}
 class SMPMGrid:
     """Geometry, indexing and operators of one SMPM grid."""
 
-    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0, tau_scale=1.0, robin_scale=0.25, robin_literal=False):
+    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0, tau_scale=1.0, robin_scale=0.25, robin_literal=False,
+                 xs=None, ys=None):
+        """Uniform grid of m_x x m_y elements on [0, L_x] x [0, L_y], or, with the
+        column edges xs (m_x + 1 increasing values) and row edges ys (m_y + 1),
+        the graded grid on [xs[0], xs[-1]] x [ys[0], ys[-1]]."""
         if mx < 1 or my < 1 or n < 2:
             raise ValueError("bad grid")
         self.mx, self.my, self.n = int(mx), int(my), int(n)
-        self.Lx, self.Ly = float(Lx), float(Ly)
         self.tau_scale = float(tau_scale)
         self.robin_scale = float(robin_scale)
         self.robin_literal = bool(robin_literal)
         self.x1d, self.w1d = gll_nodes_weights(self.n)
         self.D = diff_matrix(self.x1d)
-        self.hx, self.hy = self.Lx / self.mx, self.Ly / self.my
+        self.graded = xs is not None or ys is not None
+        self.xe = self._edges(xs, self.mx, float(Lx))
+        self.ye = self._edges(ys, self.my, float(Ly))
+        self.Lx = float(Lx) if xs is None else self.xe[-1] - self.xe[0]
+        self.Ly = float(Ly) if ys is None else self.ye[-1] - self.ye[0]
+        self.hxe, self.hye = np.diff(self.xe), np.diff(self.ye)
+        if xs is None:
+            self.hxe[:] = self.Lx / self.mx
+        if ys is None:
+            self.hye[:] = self.Ly / self.my
+        # uniform spacing (None on a graded grid: every use goes through h_of)
+        self.hx = None if xs is not None else self.Lx / self.mx
+        self.hy = None if ys is not None else self.Ly / self.my
         self.nel = self.mx * self.my
         self.nn = self.n * self.n
         self.r = self.nn * self.nel
         self.kp = 4 * self.n * self.nel
         self._build_slots()
+
+    @staticmethod
+    def _edges(edges, m, L):
+        if edges is None:
+            return np.arange(m + 1) * (L / m)
+        e = np.asarray(edges, dtype=np.float64)
+        if e.shape != (m + 1,) or not np.all(np.diff(e) > 0):
+            raise ValueError("element edges must be m + 1 increasing values")
+        return e.copy()
 
     # ---------------------------------------------------------------- indexing
     def element(self, ix, iy):
@@ -84,18 +118,28 @@ class SMPMGrid:
     def node(self, e, a, b):
         return e * self.nn + b * self.n + a
 
-    def tau(self, F):
-        """Penalty tau_F of Eq. (smpm_poisson) (reading: -alpha n(n-1)/h_perp)."""
-        h = self.hx if F in (W, E) else self.hy
-        return -self.tau_scale * self.n * (self.n - 1) / h
+    def h_of(self, e):
+        """(h_x, h_y) of element e."""
+        ix, iy = self.element_ij(e)
+        return self.hxe[ix], self.hye[iy]
 
-    def robin_weight(self, F):
-        """Weight p_F of the identity in the Robin flux R of Sec. 1.2 (reading:
-        beta n(n-1)/h_perp; 1 under the literal reading R = I + n.grad)."""
+    def h_perp(self, F, e):
+        """Size of element e across face F: h_x for W/E faces, h_y for S/N."""
+        hx, hy = self.h_of(e)
+        return hx if F in (W, E) else hy
+
+    def tau(self, F, e):
+        """Penalty tau_F of face F of element e, Eq. (smpm_poisson) (reading:
+        -alpha n(n-1)/h_perp)."""
+        return -self.tau_scale * self.n * (self.n - 1) / self.h_perp(F, e)
+
+    def robin_weight(self, F, e):
+        """Weight p_F of the identity in the Robin flux R of face F of element e
+        (Sec. 1.2) (reading: beta n(n-1)/h_perp; 1 under the literal reading
+        R = I + n.grad)."""
         if self.robin_literal:
             return 1.0
-        h = self.hx if F in (W, E) else self.hy
-        return self.robin_scale * self.n * (self.n - 1) / h
+        return self.robin_scale * self.n * (self.n - 1) / self.h_perp(F, e)
 
     def _build_slots(self):
         n = self.n
@@ -138,34 +182,38 @@ class SMPMGrid:
         y = np.empty(self.r)
         for e in range(self.nel):
             ix, iy = self.element_ij(e)
+            hx, hy = self.h_of(e)
             for b in range(self.n):
                 for a in range(self.n):
                     q = self.node(e, a, b)
-                    x[q] = ix * self.hx + (self.x1d[a] + 1.0) * self.hx / 2.0
-                    y[q] = iy * self.hy + (self.x1d[b] + 1.0) * self.hy / 2.0
+                    x[q] = self.xe[ix] + (self.x1d[a] + 1.0) * hx / 2.0
+                    y[q] = self.ye[iy] + (self.x1d[b] + 1.0) * hy / 2.0
         return x, y
 
     def mass(self):
         """GLL quadrature weight W_q = w_a w_b h_x h_y / 4 of every node."""
         m = np.empty(self.r)
         for e in range(self.nel):
+            hx, hy = self.h_of(e)
             for b in range(self.n):
                 for a in range(self.n):
-                    m[self.node(e, a, b)] = self.w1d[a] * self.w1d[b] * self.hx * self.hy / 4.0
+                    m[self.node(e, a, b)] = self.w1d[a] * self.w1d[b] * hx * hy / 4.0
         return m
 
     # ---------------------------------------------------- element operators
-    def laplacian_block(self):
-        """n^2 x n^2 element Laplacian: (2/h_x)^2 D^2 along a plus (2/h_y)^2 D^2 along b."""
+    def laplacian_block(self, e):
+        """n^2 x n^2 Laplacian of element e: (2/h_x)^2 D^2 along a plus (2/h_y)^2 D^2 along b."""
         I = np.eye(self.n)
         D2 = self.D @ self.D
-        return (2.0 / self.hx) ** 2 * np.kron(I, D2) + (2.0 / self.hy) ** 2 * np.kron(D2, I)
+        hx, hy = self.h_of(e)
+        return (2.0 / hx) ** 2 * np.kron(I, D2) + (2.0 / hy) ** 2 * np.kron(D2, I)
 
-    def normal_derivative_row(self, F, t):
-        """Row vector (over one element's n^2 nodes) of n_F . grad u at face node t of F."""
+    def normal_derivative_row(self, F, t, e):
+        """Row vector (over element e's n^2 nodes) of n_F . grad u at face node t of F."""
         n = self.n
         row = np.zeros(self.nn)
-        sx, sy = 2.0 / self.hx, 2.0 / self.hy
+        hx, hy = self.h_of(e)
+        sx, sy = 2.0 / hx, 2.0 / hy
         if F == W:
             row[t * n + np.arange(n)] = -sx * self.D[0]
         elif F == E:
@@ -176,23 +224,24 @@ class SMPMGrid:
             row[np.arange(n) * n + t] = sy * self.D[n - 1]
         return row
 
-    def robin_row(self, F, t):
-        """R u = p_F u + n_F . grad u at face node t of face F, as a row over
-        one element (R_ii of Sec. 1.2)."""
-        row = self.normal_derivative_row(F, t)
+    def robin_row(self, F, t, e):
+        """R u = p_F u + n_F . grad u at face node t of face F of element e, as a
+        row over e's nodes (R_ii of Sec. 1.2)."""
+        row = self.normal_derivative_row(F, t, e)
         a, b = self.face_node(F, t)
-        row[b * self.n + a] += self.robin_weight(F)
+        row[b * self.n + a] += self.robin_weight(F, e)
         return row
 
-    def neighbour_robin_row(self, F, t):
-        """(p_F u' + n_F . grad u') at the node of the neighbour across face F that
-        coincides with face node t of F, as a row over the neighbour's nodes.
-        n_F is the receiving element's outward normal, i.e. minus the
-        neighbour's own normal on its face opposite(F)."""
+    def neighbour_robin_row(self, F, t, e):
+        """(p_F u' + n_F . grad u') at the node of the neighbour e' across face F
+        of e that coincides with face node t of F, as a row over e''s nodes.
+        p_F is e's (the same R acts on both traces); n_F is e's outward
+        normal, i.e. minus e''s own normal on its face opposite(F), and the
+        gradient is taken with e''s own map."""
         G = OPPOSITE[F]
-        row = -self.normal_derivative_row(G, t)
+        row = -self.normal_derivative_row(G, t, self.neighbour(e, F))
         a, b = self.face_node(G, t)
-        row[b * self.n + a] += self.robin_weight(F)
+        row[b * self.n + a] += self.robin_weight(F, e)
         return row
 
     # ------------------------------------------------------ global operators
@@ -201,26 +250,26 @@ class SMPMGrid:
         L_i u_i = lap u_i + tau_i (R_ii u_i - sum_j R_ij u_j) on interface faces
                   + tau_i n.grad u_i on boundary faces."""
         rows, cols, vals = [], [], []
-        lap = self.laplacian_block()
         nn = self.nn
         loc = np.arange(nn)
         for e in range(self.nel):
             o = e * nn
+            lap = self.laplacian_block(e)
             rr, cc = np.nonzero(lap)
             rows.append(o + rr); cols.append(o + cc); vals.append(lap[rr, cc])
             for F in (W, E, S, N):
                 e2 = self.neighbour(e, F)
-                tau = self.tau(F)
+                tau = self.tau(F, e)
                 for t in range(self.n):
                     a, b = self.face_node(F, t)
                     q = self.node(e, a, b)
                     if e2 >= 0:
-                        own = tau * self.robin_row(F, t)
-                        nb = -tau * self.neighbour_robin_row(F, t)
+                        own = tau * self.robin_row(F, t, e)
+                        nb = -tau * self.neighbour_robin_row(F, t, e)
                         rows.append(np.full(nn, q)); cols.append(o + loc); vals.append(own)
                         rows.append(np.full(nn, q)); cols.append(e2 * nn + loc); vals.append(nb)
                     else:
-                        own = tau * self.normal_derivative_row(F, t)
+                        own = tau * self.normal_derivative_row(F, t, e)
                         rows.append(np.full(nn, q)); cols.append(o + loc); vals.append(own)
         Lm = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                            shape=(self.r, self.r)).tocsr()
@@ -229,25 +278,26 @@ class SMPMGrid:
 
     def element_A(self, e):
         """Local block A_e (Sec. 1.3): Laplacian, boundary term and R_ii terms of element e."""
-        A = self.laplacian_block().copy()
+        A = self.laplacian_block(e).copy()
         for F in (W, E, S, N):
-            tau = self.tau(F)
+            tau = self.tau(F, e)
             interface = self.neighbour(e, F) >= 0
             for t in range(self.n):
                 a, b = self.face_node(F, t)
                 q = b * self.n + a
-                A[q] += tau * (self.robin_row(F, t) if interface else self.normal_derivative_row(F, t))
+                A[q] += tau * (self.robin_row(F, t, e) if interface else self.normal_derivative_row(F, t, e))
         return A
 
     def assemble_B(self):
         """Flux operator B: Omega -> Gamma (k x r, Sec. 1.3):
-        (B u)_(e,F,t) = -tau_F (p_F u' + n_F.grad u')(q'), u' the neighbour across F."""
+        (B u)_(e,F,t) = -tau_F (p_F u' + n_F.grad u')(q'), u' the neighbour across F
+        and tau_F, p_F those of e's face F."""
         rows, cols, vals = [], [], []
         loc = np.arange(self.nn)
         for i, (e, F, t) in enumerate(self.slots):
             e2 = self.neighbour(e, F)
             rows.append(np.full(self.nn, i)); cols.append(e2 * self.nn + loc)
-            vals.append(-self.tau(F) * self.neighbour_robin_row(F, t))
+            vals.append(-self.tau(F, e) * self.neighbour_robin_row(F, t, e))
         Bm = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                            shape=(self.k, self.r)).tocsr()
         Bm.eliminate_zeros()
@@ -276,7 +326,7 @@ class SMPMGrid:
                     continue
                 for t in range(self.n):
                     a, b_ = self.face_node(F, t)
-                    b[self.node(e, a, b_)] += self.tau(F) * g[e * 4 * self.n + F * self.n + t]
+                    b[self.node(e, a, b_)] += self.tau(F, e) * g[e * 4 * self.n + F * self.n + t]
         return b
 
     def boundary_g(self, gfun):

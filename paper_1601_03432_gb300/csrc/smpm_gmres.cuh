@@ -482,7 +482,15 @@ __device__ void push_step(const GmresArgs<S>& a, const Smem<S>& s, int e, const 
 
 // c_hat = H c: CTA c takes a contiguous range of rows; c is staged in shared
 // memory and P lanes split each row (H row-major: lanes read consecutive
-// columns), partial sums meet in warp shuffles.
+// columns), partial sums meet in warp shuffles.  Each lane keeps eight loads
+// in flight (16-byte loads when rows start 16-byte aligned, i.e. d even), so
+// that a matrix larger than L2 streams at HBM rate; such a matrix is read
+// with the evict-first hint, which keeps the Krylov basis resident in L2.
+__device__ __forceinline__ double2 ld_h2(const double* p, bool stream) {
+  return stream ? __ldcs(reinterpret_cast<const double2*>(p)) : __ldg(reinterpret_cast<const double2*>(p));
+}
+__device__ __forceinline__ double ld_h1(const double* p, bool stream) { return stream ? __ldcs(p) : __ldg(p); }
+
 template <typename S>
 __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
   const int d = (int)a.g.d;
@@ -491,23 +499,47 @@ __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
   if (r0 >= r1) return;
   for (int j = threadIdx.x; j < d; j += blockDim.x) s.cst[j] = __ldcg(a.c + j);
   __syncthreads();
+  const bool stream = (size_t)d * d * sizeof(double) > ((size_t)48 << 20);
+  const bool vec = (d & 1) == 0;
   const int rows = r1 - r0;
   int P = 32;
   while (P > 1 && P * rows > 2 * (int)blockDim.x) P >>= 1;
   const int lane = threadIdx.x % P, grp = threadIdx.x / P, ngrp = blockDim.x / P;
+  const double* cs = s.cst;
   for (int rb = 0; rb < rows; rb += ngrp) {  // uniform trip count per warp
     const int r = r0 + rb + grp;
     double sum = 0;
     if (r < r1) {
       const double* hr = a.H + (size_t)r * d;
-      double s0 = 0, s1 = 0;
-      int j = lane;
-      for (; j + P < d; j += 2 * P) {
-        s0 += __ldg(hr + j) * s.cst[j];
-        s1 += __ldg(hr + j + P) * s.cst[j + P];
+      double acc[4] = {0, 0, 0, 0};
+      if (vec) {
+        int j = 2 * lane;
+        for (; j + 14 * P < d; j += 16 * P) {
+          double2 h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = ld_h2(hr + j + 2 * u * P, stream);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jj = j + 2 * u * P;
+            acc[u & 3] += h[u].x * cs[jj] + h[u].y * cs[jj + 1];
+          }
+        }
+        for (; j < d; j += 2 * P) {
+          const double2 h = ld_h2(hr + j, stream);
+          acc[0] += h.x * cs[j] + h.y * cs[j + 1];
+        }
+      } else {
+        int j = lane;
+        for (; j + 7 * P < d; j += 8 * P) {
+          double h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = ld_h1(hr + j + u * P, stream);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u & 3] += h[u] * cs[j + u * P];
+        }
+        for (; j < d; j += P) acc[0] += ld_h1(hr + j, stream) * cs[j];
       }
-      if (j < d) s0 += __ldg(hr + j) * s.cst[j];
-      sum = s0 + s1;
+      sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
     if (lane == 0 && r < r1) a.chat[r] = sum;

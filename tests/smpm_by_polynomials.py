@@ -11,7 +11,8 @@ The face terms follow Eq. smpm_poisson with R = p_F I + n.grad and the
 readings of the penalty and the Robin weight:
     tau_F = -tau_scale n(n-1)/h_perp,
     p_F   = robin_scale n(n-1)/h_perp   (or 1 under the literal R = I + n.grad),
-h_perp = h_x on W/E faces, h_y on S/N faces.
+h_perp = h_x on W/E faces, h_y on S/N faces, of the element whose residual row
+it is (graded grids: column edges xs, row edges ys).
 """
 import numpy as np
 from numpy.polynomial import Polynomial
@@ -29,17 +30,25 @@ def _lagrange(nodes, a):
     return Polynomial.fromroots(others) / np.prod([nodes[a] - c for c in others])
 
 
-def operator_by_polynomials(mx, my, n, Lx, Ly, tau_scale=1.0, robin_scale=0.25, literal=False):
-    """Dense r x r L, node (a, b) of element e = iy*mx + ix at e*n*n + b*n + a."""
+def operator_by_polynomials(mx, my, n, Lx, Ly, tau_scale=1.0, robin_scale=0.25, literal=False,
+                            xs=None, ys=None):
+    """Dense r x r L, node (a, b) of element e = iy*mx + ix at e*n*n + b*n + a.
+    xs / ys: column / row edges of a graded grid (else uniform on [0,Lx]x[0,Ly])."""
     xi = np.array(GLL_CLOSED_FORM[n])
-    hx, hy = Lx / mx, Ly / my
+    xe = np.linspace(0.0, Lx, mx + 1) if xs is None else np.asarray(xs, float)
+    ye = np.linspace(0.0, Ly, my + 1) if ys is None else np.asarray(ys, float)
     nel, nn = mx * my, n * n
     r = nel * nn
+
+    def sizes(e):
+        ix, iy = e % mx, e // mx
+        return xe[ix + 1] - xe[ix], ye[iy + 1] - ye[iy]
 
     # physical node coordinates and the 1-D Lagrange bases of every element
     def elem_nodes(e):
         ix, iy = e % mx, e // mx
-        return ix * hx + (xi + 1) * hx / 2, iy * hy + (xi + 1) * hy / 2
+        hx, hy = sizes(e)
+        return xe[ix] + (xi + 1) * hx / 2, ye[iy] + (xi + 1) * hy / 2
 
     bases = []
     for e in range(nel):
@@ -82,7 +91,7 @@ def operator_by_polynomials(mx, my, n, Lx, Ly, tau_scale=1.0, robin_scale=0.25, 
                             own = ec == e
                             val = lap if own else 0.0
                             for F in faces:
-                                hp = hx if F in (0, 1) else hy
+                                hp = sizes(e)[0] if F in (0, 1) else sizes(e)[1]
                                 tau = -tau_scale * n * (n - 1) / hp
                                 p = 1.0 if literal else robin_scale * n * (n - 1) / hp
                                 nx, ny = normal[F]

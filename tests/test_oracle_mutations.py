@@ -36,10 +36,11 @@ def pins_hold(mx=3, my=2, n=5, Lx=1.5, Ly=0.75):
     return True
 
 
-def _swap_h(self, F, t):
+def _swap_h(self, F, t, e):
     n = self.n
     row = np.zeros(self.nn)
-    sx, sy = 2.0 / self.hy, 2.0 / self.hx           # mistake: h_x and h_y swapped
+    hx, hy = self.h_of(e)
+    sx, sy = 2.0 / hy, 2.0 / hx                     # mistake: h_x and h_y swapped
     if F == sm.W:
         row[t * n + np.arange(n)] = -sx * self.D[0]
     elif F == sm.E:
@@ -51,37 +52,35 @@ def _swap_h(self, F, t):
     return row
 
 
-def _neighbour_sign(self, F, t):
+def _neighbour_sign(self, F, t, e):
     G = sm.OPPOSITE[F]
-    row = self.normal_derivative_row(G, t)          # mistake: neighbour normal not negated
+    row = self.normal_derivative_row(G, t, self.neighbour(e, F))  # mistake: neighbour normal not negated
     a, b = self.face_node(G, t)
-    row[b * self.n + a] += self.robin_weight(F)
+    row[b * self.n + a] += self.robin_weight(F, e)
     return row
 
 
-def _neighbour_reversed(self, F, t):
+def _neighbour_reversed(self, F, t, e):
     G = sm.OPPOSITE[F]
     t2 = self.n - 1 - t                             # mistake: face nodes matched in reverse
-    row = -self.normal_derivative_row(G, t2)
+    row = -self.normal_derivative_row(G, t2, self.neighbour(e, F))
     a, b = self.face_node(G, t2)
-    row[b * self.n + a] += self.robin_weight(F)
+    row[b * self.n + a] += self.robin_weight(F, e)
     return row
 
 
-def _tau_sign(self, F):
-    h = self.hx if F in (sm.W, sm.E) else self.hy
-    return self.tau_scale * self.n * (self.n - 1) / h  # mistake: wrong sign
+def _tau_sign(self, F, e):
+    return self.tau_scale * self.n * (self.n - 1) / self.h_perp(F, e)  # mistake: wrong sign
 
 
-def _tau_scale2(self, F):
-    h = self.hx if F in (sm.W, sm.E) else self.hy
-    return -2.0 * self.n * (self.n - 1) / h          # mistake: factor 2
+def _tau_scale2(self, F, e):
+    return -2.0 * self.n * (self.n - 1) / self.h_perp(F, e)          # mistake: factor 2
 
 
-def _laplacian_dropped(self):
+def _laplacian_dropped(self, e):
     I = np.eye(self.n)
     D2 = self.D @ self.D
-    return (2.0 / self.hx) ** 2 * np.kron(I, D2)     # mistake: y term dropped
+    return (2.0 / self.h_of(e)[0]) ** 2 * np.kron(I, D2)     # mistake: y term dropped
 
 
 def _face_node_swapped(self, F, t):
@@ -136,41 +135,39 @@ def robin_pins_hold():
     return True
 
 
-def _robin_h_swapped(self, F):
+def _robin_h_swapped(self, F, e):
     if self.robin_literal:
         return 1.0
-    h = self.hy if F in (sm.W, sm.E) else self.hx     # mistake: h_perp taken along the face
+    hx, hy = self.h_of(e)
+    h = hy if F in (sm.W, sm.E) else hx               # mistake: h_perp taken along the face
     return self.robin_scale * self.n * (self.n - 1) / h
 
 
-def _robin_hx_everywhere(self, F):
+def _robin_hx_everywhere(self, F, e):
     if self.robin_literal:
         return 1.0
-    return self.robin_scale * self.n * (self.n - 1) / self.hx   # mistake: h_x on S/N faces too
+    return self.robin_scale * self.n * (self.n - 1) / self.h_of(e)[0]   # mistake: h_x on S/N faces too
 
 
-def _robin_no_quarter(self, F):
+def _robin_no_quarter(self, F, e):
     if self.robin_literal:
         return 1.0
-    h = self.hx if F in (sm.W, sm.E) else self.hy
-    return self.n * (self.n - 1) / h                  # mistake: the factor 1/4 dropped
+    return self.n * (self.n - 1) / self.h_perp(F, e)  # mistake: the factor 1/4 dropped
 
 
-def _robin_master_gradient(self, F):
+def _robin_master_gradient(self, F, e):
     if self.robin_literal:
         return 1.0
-    h = self.hx if F in (sm.W, sm.E) else self.hy
-    return 2.0 / h                                    # mistake: 2/h (master-element scale) for n(n-1)/(4h)
+    return 2.0 / self.h_perp(F, e)                    # mistake: 2/h (master-element scale) for n(n-1)/(4h)
 
 
-def _robin_literal_ignored(self, F):
-    h = self.hx if F in (sm.W, sm.E) else self.hy
-    return self.robin_scale * self.n * (self.n - 1) / h   # mistake: the literal reading not honoured
+def _robin_literal_ignored(self, F, e):
+    return self.robin_scale * self.n * (self.n - 1) / self.h_perp(F, e)   # mistake: the literal reading not honoured
 
 
-def _robin_identity_on_own_side_only(self, F, t):
+def _robin_identity_on_own_side_only(self, F, t, e):
     G = sm.OPPOSITE[F]
-    return -self.normal_derivative_row(G, t)          # mistake: neighbour's p_F u' term dropped
+    return -self.normal_derivative_row(G, t, self.neighbour(e, F))  # mistake: neighbour's p_F u' term dropped
 
 
 ROBIN_MUTATIONS = [
