@@ -111,6 +111,20 @@ void smpm_default_opts(smpm_opts* o);
  * 1 <= mx, my <= 4096).  No device work.  Errors: EINVAL, ENOMEM. */
 smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* h);
 
+/* Graded grid (Sec. 1.2 admits any smooth invertible element map; this is
+ * the axis-aligned case with sizes of their own): element (ix, iy) covers
+ * [xs[ix], xs[ix+1]] x [ys[iy], ys[iy+1]].  xs: host, mx+1 finite, strictly
+ * increasing column edges; ys: host, my+1 row edges; both copied.  The
+ * penalty tau_F and the Robin weight p_F of every face use the size of the
+ * element that owns the face; the neighbour's gradient uses the neighbour's
+ * size.  B 1, the right null vector of S, then differs between the two sides
+ * of an interface, and the deflation vectors z_j of Sec. 2 are its
+ * restrictions to interface j divided by the mean of the two sides (the
+ * 0/1 indicators of the paper on a uniform grid; indicators alone leave B 1
+ * outside the coarse space and GMRES stagnates on strongly graded grids).
+ * Other limits and errors as smpm_setup. */
+smpm_status smpm_setup_graded(int mx, int my, int n, const double* xs, const double* ys, smpm_handle* h);
+
 /* Sizes: r = n^2 mx my nodes, kp = 4 n mx my slots, d interfaces, k = 2 n d
  * real interface slots, nblack checkerboard blocks.  Any pointer may be null. */
 smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d,

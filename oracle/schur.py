@@ -37,7 +37,13 @@ from .smpm import W, E, S, N, OPPOSITE
 class SchurSystem:
     """All operators of Algorithms 1-3 for one grid (FP64, plain)."""
 
-    def __init__(self, grid, seed=12345):
+    def __init__(self, grid, seed=12345, deflation="weighted"):
+        """deflation: "weighted" (z_j = B 1 on interface j's slots over the mean
+        of its two sides, the indicator on a uniform grid) or "indicator" (the
+        0/1 vectors of Sec. 2 on any grid)."""
+        if deflation not in ("weighted", "indicator"):
+            raise ValueError("deflation must be 'weighted' or 'indicator'")
+        self.deflation = deflation
         if grid.nel < 2:
             raise ValueError("the Schur method needs at least one interface (m_x m_y >= 2)")
         self.grid = grid
@@ -186,14 +192,25 @@ class SchurSystem:
     # -------------------------------------------------------------- deflation
     def _build_deflation(self):
         """Z (k x d): z_j is 1 on the 2n slots of interface j (both sides) and 0
-        elsewhere; C = Z^T S Z (Sec. 2)."""
+        elsewhere; C = Z^T S Z (Sec. 2).  Graded-grid reading: B 1 takes the
+        value -tau_F p_F of each side, which differs across an interface of
+        unequal sizes, so with 0/1 vectors B 1 leaves the coarse space (C is
+        then nonsingular) and deflated GMRES stagnates on strongly graded grids.
+        The weighted z_j is B 1 restricted to interface j divided by beta_j, the
+        mean of its two sides; B 1 = Z beta again, and on a uniform grid every
+        weight is exactly 1."""
         g = self.grid
         cols = np.array([g.iface_of[(e, F)] for (e, F, t) in g.slots])
-        self.Z = sp.csr_matrix((np.ones(g.k), (np.arange(g.k), cols)), shape=(g.k, g.d))
+        beta = np.empty(g.d)                     # mean of the two sides' values
+        for j, (e, F) in enumerate(g.interfaces):
+            e2 = g.neighbour(e, F)
+            beta[j] = 0.5 * (self.B1[g.slot_of[(e, F, 0)]] + self.B1[g.slot_of[(e2, OPPOSITE[F], 0)]])
+        w = self.B1 / beta[cols] if self.deflation == "weighted" else np.ones(g.k)
+        self.zweights = w
+        self.Z = sp.csr_matrix((w, (np.arange(g.k), cols)), shape=(g.k, g.d))
         self.C = (self.Z.T @ (self.S @ self.Z)).toarray()
-        # right null vector of C: B 1 = Z c0 when B 1 is constant on each interface
-        zb = self.Z.T @ self.B1
-        c0 = zb / (2 * g.n)
+        # right null vector of C: B 1 = Z c0 when B 1 is in the range of Z
+        c0 = beta
         self.coarse_singular = bool(np.allclose(self.Z @ c0, self.B1, rtol=1e-12,
                                                 atol=1e-12 * np.abs(self.B1).max()))
         d = g.d

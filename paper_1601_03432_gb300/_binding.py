@@ -23,7 +23,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "
 
 # every symbol include/smpm.h declares
 EXPORTS = [
-    "smpm_default_opts", "smpm_setup", "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
+    "smpm_default_opts", "smpm_setup", "smpm_setup_graded", "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
@@ -72,6 +72,7 @@ def lib():
         L.smpm_default_opts.argtypes = [ctypes.POINTER(SmpmOpts)]
         L.smpm_default_opts.restype = None
         L.smpm_setup.argtypes = [I, I, I, D, D, ctypes.POINTER(P)]
+        L.smpm_setup_graded.argtypes = [I, I, I, P, P, ctypes.POINTER(P)]
         L.smpm_sizes.argtypes = [P] + [ctypes.POINTER(LL)] * 5
         L.smpm_node_coords.argtypes = [P, P, P]
         L.smpm_node_mass.argtypes = [P, P]
@@ -173,9 +174,19 @@ def _stream(stream):
 class Grid:
     """One SMPM grid and its factors, owned through an smpm_handle."""
 
-    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0):
+    def __init__(self, mx, my, n, Lx=1.0, Ly=1.0, xs=None, ys=None):
+        """Uniform grid on [0,Lx]x[0,Ly], or with column edges xs (mx+1) and/or
+        row edges ys (my+1) the graded grid (smpm_setup_graded)."""
         h = ctypes.c_void_p()
-        check(lib().smpm_setup(mx, my, n, float(Lx), float(Ly), ctypes.byref(h)))
+        if xs is None and ys is None:
+            check(lib().smpm_setup(mx, my, n, float(Lx), float(Ly), ctypes.byref(h)))
+        else:
+            ex = np.ascontiguousarray(np.arange(mx + 1) * (Lx / mx) if xs is None else xs, dtype=np.float64)
+            ey = np.ascontiguousarray(np.arange(my + 1) * (Ly / my) if ys is None else ys, dtype=np.float64)
+            if ex.shape != (mx + 1,) or ey.shape != (my + 1,):
+                raise ValueError("xs needs mx + 1 and ys my + 1 edges")
+            check(lib().smpm_setup_graded(mx, my, n, ex.ctypes.data, ey.ctypes.data, ctypes.byref(h)))
+            Lx, Ly = float(ex[-1] - ex[0]), float(ey[-1] - ey[0])
         self.h = h
         self.mx, self.my, self.n, self.Lx, self.Ly = mx, my, n, Lx, Ly
         vals = [ctypes.c_longlong() for _ in range(5)]

@@ -22,11 +22,19 @@
 //     right-preconditioned GMRES with iterative refinement,
 //     and u_L = -A^-T B^T u_S normalised (u_L^T L = -u_S^T S B = 0), Sec. 1.4.
 //
-// Identical element matrices (same face types; h is uniform per direction)
-// are computed once and copied: the stored factors are per element.
+// Graded grids (column widths and row heights of their own): tau_F, p_F and
+// the derivative scale of every face come from the element that owns the face,
+// so T_e depends on e's size and on its neighbours' facing faces.  B 1 then
+// differs between the two sides of an interface, and the deflation vectors
+// z_j are its restrictions to interface j (scaled by the mean of the two
+// sides) instead of 0/1 indicators; on a uniform grid both are the same.  C =
+// Z^T S Z stays singular with right null vector c0 = the per-interface means.
+// Identical element matrices (same face types and sizes) are computed once
+// and copied: the stored factors are per element.
 #include <unistd.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -316,32 +324,35 @@ void elem_solve_T(int n, const double* fx, const double* fy, const double* B, do
     }
 }
 
-// n_F . grad U at face node t of face F of one element (U[b][a]).
-double normal_derivative(const Geometry& g, const std::vector<double>& D, const double* U, int F, int t) {
+// n_F . grad U at face node t of face F of one element (U[b][a]); sc = 2/h
+// of the element along the face normal.
+double normal_derivative(const Geometry& g, const std::vector<double>& D, const double* U, int F, int t, double sc) {
   const int n = g.n;
-  const double sx = 2.0 / g.hx, sy = 2.0 / g.hy;
   double acc = 0;
   switch (F) {
-    case FACE_W: for (int c = 0; c < n; ++c) acc += D[c] * U[t * n + c]; return -sx * acc;
-    case FACE_E: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[t * n + c]; return sx * acc;
-    case FACE_S: for (int c = 0; c < n; ++c) acc += D[c] * U[c * n + t]; return -sy * acc;
-    default: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[c * n + t]; return sy * acc;
+    case FACE_W: for (int c = 0; c < n; ++c) acc += D[c] * U[t * n + c]; return -sc * acc;
+    case FACE_E: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[t * n + c]; return sc * acc;
+    case FACE_S: for (int c = 0; c < n; ++c) acc += D[c] * U[c * n + t]; return -sc * acc;
+    default: for (int c = 0; c < n; ++c) acc += D[(n - 1) * n + c] * U[c * n + t]; return sc * acc;
   }
 }
 
 struct Ctx {
   const Geometry& g;
   Factors* f;
-  double tau(int F) const { return F < 2 ? f->tau_x : f->tau_y; }
-  double pw(int F) const { return F < 2 ? f->p_x : f->p_y; }
+  // [tau, p, 2/h] of face F of element e (from e's column for W/E, row for S/N)
+  const double* face(int e, int F) const {
+    return F < 2 ? f->colg.data() + 3 * (e % g.mx) : f->rowg.data() + 3 * (e / g.mx);
+  }
   const double* fx(int e) const { return f->fdx.data() + static_cast<size_t>(xclass(g, e)) * (2 * g.n * g.n + g.n); }
   const double* fy(int e) const { return f->fdy.data() + static_cast<size_t>(yclass(g, e)) * (2 * g.n * g.n + g.n); }
 };
 
 // T_e for element e (M x M, row (F,t) = the flux into the neighbour across F,
 // column (G,s) = e's own slot).  Row (F,t) equals the B row of slot
-// (nbr(e,F), opp F, t): -tau_F (p_F w - n_F.grad w) at e's face node (F,t),
-// with w = A_e^-1 E_e (unit value at the face node of slot (G,s)).
+// (e' = nbr(e,F), opp F, t): -tau' (p' w - n_F.grad w) at e's face node (F,t),
+// with tau', p' those of e''s face opp F, the gradient taken with e's own
+// size, and w = A_e^-1 E_e (unit value at the face node of slot (G,s)).
 void element_T(const Ctx& c, int e, double* T) {
   const Geometry& g = c.g;
   const int n = g.n, M = g.M;
@@ -356,12 +367,15 @@ void element_T(const Ctx& c, int e, double* T) {
       B[b * n + a] = 1.0;
       elem_solve(n, c.fx(e), c.fy(e), B.data(), U.data());
       for (int F = 0; F < 4; ++F) {
-        if (g.neighbour(e, F) < 0) continue;
+        const int e2 = g.neighbour(e, F);
+        if (e2 < 0) continue;
+        const double* fn = c.face(e2, opposite(F));
+        const double se = c.face(e, F)[2];
         for (int t = 0; t < n; ++t) {
           int aa, bb;
           g.face_node(F, t, &aa, &bb);
-          double val = c.pw(F) * U[bb * n + aa] - normal_derivative(g, c.f->D, U.data(), F, t);
-          T[(F * n + t) * M + G * n + s] = -c.tau(F) * val;
+          double val = fn[1] * U[bb * n + aa] - normal_derivative(g, c.f->D, U.data(), F, t, se);
+          T[(F * n + t) * M + G * n + s] = -fn[0] * val;
         }
       }
     }
@@ -369,33 +383,37 @@ void element_T(const Ctx& c, int e, double* T) {
 }
 
 // ----------------------------------------------------- slot operators (host)
-// Class representatives.  Elements with the same face-type mask hold
-// identical T_e, and black blocks with the same key (own mask, then the four
-// neighbours' masks) identical G_b and X_b: the factor step computes T_e and
-// G_b once per class and copies them, and gathers X_b from the neighbours'
-// identical T.  The host operators below read the representative's copy,
-// which gives the same arithmetic from a cache-resident working set.
+// Class representatives.  Elements of one T class (same face types and, on a
+// graded grid, the same own and facing sizes) hold identical T_e, and black
+// blocks with the same key (own T class, then the four neighbours' classes)
+// identical G_b and X_b: the factor step computes T_e and G_b once per class
+// and copies them, and gathers X_b from the neighbours' identical T.  The
+// host operators below read the representative's copy, which gives the same
+// arithmetic from a cache-resident working set.
 struct ClassReps {
   std::vector<long long> t;  // per element: element whose T_e it reads
   std::vector<long long> b;  // per black block: block whose G_b, X_b it reads
 };
 
-ClassReps class_reps(const Geometry& g, const std::vector<int>& black) {
+using BlockKey = std::array<int, 5>;
+BlockKey block_key(const Geometry& g, const std::vector<int>& tcls, int e) {
+  BlockKey k{tcls[e], -1, -1, -1, -1};
+  for (int F = 0; F < 4; ++F) {
+    const int e2 = g.neighbour(e, F);
+    k[F + 1] = e2 >= 0 ? tcls[e2] : -1;
+  }
+  return k;
+}
+
+ClassReps class_reps(const Geometry& g, const std::vector<int>& black, const std::vector<int>& tcls) {
   ClassReps c;
   c.t.resize(g.nel);
   std::map<int, long long> first_t;
-  for (long long e = 0; e < g.nel; ++e) c.t[e] = first_t.emplace(g.mask(static_cast<int>(e)), e).first->second;
+  for (long long e = 0; e < g.nel; ++e) c.t[e] = first_t.emplace(tcls[e], e).first->second;
   c.b.resize(black.size());
-  std::map<long long, long long> first_b;
-  for (size_t ib = 0; ib < black.size(); ++ib) {
-    const int e = black[ib];
-    long long key = g.mask(e);
-    for (int F = 0; F < 4; ++F) {
-      const int e2 = g.neighbour(e, F);
-      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
-    }
-    c.b[ib] = first_b.emplace(key, static_cast<long long>(ib)).first->second;
-  }
+  std::map<BlockKey, long long> first_b;
+  for (size_t ib = 0; ib < black.size(); ++ib)
+    c.b[ib] = first_b.emplace(block_key(g, tcls, black[ib]), static_cast<long long>(ib)).first->second;
   return c;
 }
 
@@ -485,7 +503,7 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   double an = std::sqrt(dot(a, a));
   for (auto& v : a) v /= an;
   std::vector<double> tmp(kp), tmp2(kp);
-  const ClassReps cr = class_reps(g, f->black);
+  const ClassReps cr = class_reps(g, f->black, f->tcls);
   auto op = [&](const std::vector<double>& z, std::vector<double>& out) {
     apply_MinvT(g, *f, cr, z.data(), tmp.data());
     apply_ST(g, *f, cr, tmp.data(), tmp2.data());
@@ -613,9 +631,11 @@ int left_null_S(const Geometry& g, Factors* f, std::string* err) {
   return SMPM_OK;
 }
 
-// Row sums of T_e over each input face: Rs[row * 4 + G] = sum_q T_e[row, G n + q]
-// (the pushed part of S Z, one column per face of e).
-void row_sums(const Geometry& g, const std::vector<double>& T, std::vector<double>* Rs) {
+// Weighted row sums of T_e over each input face:
+// Rs[row * 4 + G] = zw[4e + G] sum_q T_e[row, G n + q] (the pushed part of S Z,
+// one column per face of e).
+void row_sums(const Geometry& g, const std::vector<double>& T, const std::vector<double>& zw,
+              std::vector<double>* Rs) {
   const int n = g.n, M = g.M;
   Rs->assign(static_cast<size_t>(g.nel) * M * 4, 0.0);
 #pragma omp parallel for schedule(static)
@@ -626,7 +646,7 @@ void row_sums(const Geometry& g, const std::vector<double>& T, std::vector<doubl
       for (int G = 0; G < 4; ++G) {
         double acc = 0;
         for (int q = 0; q < n; ++q) acc += Te[row * M + G * n + q];
-        R[row * 4 + G] = acc;
+        R[row * 4 + G] = zw[4 * e + G] * acc;
       }
   }
 }
@@ -634,28 +654,43 @@ void row_sums(const Geometry& g, const std::vector<double>& T, std::vector<doubl
 // Block-Jacobi factors of the checkerboard blocks of I + (push form of T)
 // (Sec. 2, Fig. 2): per black element the X_F blocks (the neighbours' T rows
 // facing e, restricted to their slots facing e) and G = (I - X Y)^-1 with
-// Y = T_e; identical blocks (same face-type masks) share one inversion.
+// Y = T_e; identical blocks (same own and neighbour T classes) share one
+// inversion.
 int block_factors(const Geometry& g, const std::vector<int>& black, const std::vector<double>& T,
-                  std::vector<double>* Gout, std::vector<double>* Xout, std::string* err) {
+                  const std::vector<int>& tcls, std::vector<double>* Gout, std::vector<double>* Xout,
+                  std::string* err) {
   const int n = g.n, M = g.M;
   const size_t nb = black.size();
   Gout->assign(nb * M * M, 0.0);
   Xout->assign(nb * 4 * n * n, 0.0);
-  std::map<long long, std::vector<double>> gcache;
-  for (size_t ib = 0; ib < nb; ++ib) {
-    int e = black[ib];
+#pragma omp parallel for schedule(static)
+  for (long long ib = 0; ib < static_cast<long long>(nb); ++ib) {
+    const int e = black[ib];
     double* X = Xout->data() + ib * 4 * n * n;
-    long long key = g.mask(e);
     for (int F = 0; F < 4; ++F) {
       int e2 = g.neighbour(e, F);
-      key = key * 16 + (e2 >= 0 ? g.mask(e2) : 0);
       if (e2 < 0) continue;
       const double* T2 = T.data() + static_cast<size_t>(e2) * M * M;
       int Fo = opposite(F);
       for (int t = 0; t < n; ++t)
         for (int q = 0; q < n; ++q) X[(F * n + t) * n + q] = T2[(Fo * n + t) * M + Fo * n + q];
     }
-    if (!gcache.count(key)) {
+  }
+  // one representative block per key, inverted in parallel, then copied
+  std::map<BlockKey, int> first;
+  std::vector<int> rep(nb), reps;
+  for (size_t ib = 0; ib < nb; ++ib) {
+    auto it = first.emplace(block_key(g, tcls, black[ib]), static_cast<int>(reps.size()));
+    if (it.second) reps.push_back(static_cast<int>(ib));
+    rep[ib] = it.first->second;
+  }
+  std::vector<std::vector<double>> ginv(reps.size());
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+  for (long long ir = 0; ir < static_cast<long long>(reps.size()); ++ir) {
+    const int ib = reps[ir], e = black[ib];
+    const double* X = Xout->data() + static_cast<size_t>(ib) * 4 * n * n;
+    {
       const double* Y = T.data() + static_cast<size_t>(e) * M * M;
       std::vector<double> A(static_cast<size_t>(M) * M, 0.0);
       for (int F = 0; F < 4; ++F)
@@ -666,7 +701,7 @@ int block_factors(const Geometry& g, const std::vector<int>& black, const std::v
             A[(F * n + t) * M + col] = (F * n + t == col ? 1.0 : 0.0) - acc;
           }
       DenseLU lu = lu_factor(A.data(), M);
-      if (!lu.ok) { *err = "singular block-Jacobi block"; return SMPM_EINVAL; }
+      if (!lu.ok) { bad += 1; continue; }
       std::vector<double> Gi(static_cast<size_t>(M) * M), col(M);
       for (int j = 0; j < M; ++j) {
         std::fill(col.begin(), col.end(), 0.0);
@@ -674,11 +709,13 @@ int block_factors(const Geometry& g, const std::vector<int>& black, const std::v
         lu_solve(lu, col.data());
         for (int i = 0; i < M; ++i) Gi[i * M + j] = col[i];
       }
-      gcache[key] = Gi;
+      ginv[ir] = std::move(Gi);
     }
-    const std::vector<double>& Gi = gcache.at(key);
-    std::memcpy(Gout->data() + ib * M * M, Gi.data(), sizeof(double) * M * M);
   }
+  if (bad) { *err = "singular block-Jacobi block"; return SMPM_EINVAL; }
+#pragma omp parallel for schedule(static)
+  for (long long ib = 0; ib < static_cast<long long>(nb); ++ib)
+    std::memcpy(Gout->data() + ib * M * M, ginv[rep[ib]].data(), sizeof(double) * M * M);
   return SMPM_OK;
 }
 
@@ -784,56 +821,105 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
   }
   const int n = g.n, M = g.M;
   const double nn1 = n * (n - 1.0);
-  f->tau_x = -o.tau_scale * nn1 / g.hx;
-  f->tau_y = -o.tau_scale * nn1 / g.hy;
-  // identity weight of the Robin flux R = p_F I + n.grad: scaled by the
-  // element's own length, or 1 under the literal reading R = I + n.grad
+  // per column (W/E faces) and row (S/N faces): tau = -alpha n(n-1)/h, the
+  // identity weight of the Robin flux R = p I + n.grad (scaled by the
+  // element's own length, or 1 under the literal reading R = I + n.grad) and
+  // the derivative scale 2/h
   const bool literal = (o.flags & SMPM_FLAG_ROBIN_LITERAL) != 0;
-  f->p_x = literal ? 1.0 : o.robin_scale * nn1 / g.hx;
-  f->p_y = literal ? 1.0 : o.robin_scale * nn1 / g.hy;
+  auto face_data = [&](double h, double* out) {
+    out[0] = -o.tau_scale * nn1 / h;
+    out[1] = literal ? 1.0 : o.robin_scale * nn1 / h;
+    out[2] = 2.0 / h;
+  };
+  f->colg.assign(3 * static_cast<size_t>(g.mx), 0.0);
+  f->rowg.assign(3 * static_cast<size_t>(g.my), 0.0);
+  for (int ix = 0; ix < g.mx; ++ix) face_data(g.col_h(ix), f->colg.data() + 3 * ix);
+  for (int iy = 0; iy < g.my; ++iy) face_data(g.row_h(iy), f->rowg.data() + 3 * iy);
   gll(n, &f->x1d, &f->w1d);
   diff_matrix(f->x1d, &f->D);
 
-  // 1-D operators and their fast diagonalisation, 4 classes per direction
+  // 1-D operators and their fast diagonalisation: 4 classes per direction
+  // (face types) on a uniform grid, one per column / row on a graded one
   const int fds = 2 * n * n + n;
-  f->fdx.assign(4 * fds, 0.0);
-  f->fdy.assign(4 * fds, 0.0);
-  std::vector<double> K;
-  for (int cls = 0; cls < 4; ++cls) {
-    build_K(g, f->D, 2.0 / g.hx, f->tau_x, f->p_x, cls & 1, cls & 2, &K);
-    fast_diag(n, f->w1d, K, f->fdx.data() + cls * fds);
-    build_K(g, f->D, 2.0 / g.hy, f->tau_y, f->p_y, cls & 1, cls & 2, &K);
-    fast_diag(n, f->w1d, K, f->fdy.data() + cls * fds);
+  const int nfx = g.graded ? g.mx : 4, nfy = g.graded ? g.my : 4;
+  f->fdx.assign(static_cast<size_t>(nfx) * fds, 0.0);
+  f->fdy.assign(static_cast<size_t>(nfy) * fds, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < nfx + nfy; ++i) {
+    std::vector<double> K;
+    const bool xdir = i < nfx;
+    const int c = xdir ? i : i - nfx, m = xdir ? g.mx : g.my;
+    // face types of the entry: bit 0 = low-side interface, bit 1 = high side
+    const int cls = g.graded ? ((c > 0 ? 1 : 0) | (c < m - 1 ? 2 : 0)) : c;
+    const double* fd = (xdir ? f->colg.data() : f->rowg.data()) + 3 * (g.graded ? c : 0);
+    build_K(g, f->D, fd[2], fd[0], fd[1], cls & 1, cls & 2, &K);
+    fast_diag(n, f->w1d, K, (xdir ? f->fdx.data() : f->fdy.data()) + static_cast<size_t>(c) * fds);
   }
-  for (int cls = 0; cls < 4; ++cls)
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        const double* lx = f->fdx.data() + cls * fds + 2 * n * n;
-        const double* ly = f->fdy.data() + cls * fds + 2 * n * n;
-        if (!(std::fabs(lx[i] + ly[j]) > 0)) {
-          // only the element without interfaces (mx = my = 1) is singular
-          if ((cls & 3) != 0) { *err = "singular element operator"; return SMPM_EINVAL; }
-        }
-      }
+  // the element operator I (x) K_x + K_y (x) I is singular only for the
+  // element without interfaces (mx = my = 1)
+  for (int cx = 0; cx < nfx; ++cx)
+    for (int cy = 0; cy < nfy; ++cy) {
+      const int clsx = g.graded ? ((cx > 0 ? 1 : 0) | (cx < g.mx - 1 ? 2 : 0)) : cx;
+      const int clsy = g.graded ? ((cy > 0 ? 1 : 0) | (cy < g.my - 1 ? 2 : 0)) : cy;
+      if ((clsx | clsy) == 0) continue;
+      const double* lx = f->fdx.data() + static_cast<size_t>(cx) * fds + 2 * n * n;
+      const double* ly = f->fdy.data() + static_cast<size_t>(cy) * fds + 2 * n * n;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          if (!(std::fabs(lx[i] + ly[j]) > 0)) { *err = "singular element operator"; return SMPM_EINVAL; }
+    }
   Ctx c{g, f};
 
-  // T_e, computed once per face-type mask
+  // T_e, computed once per class: elements with the same face types, the same
+  // size and the same facing sizes of their neighbours hold identical T_e
   f->T.assign(static_cast<size_t>(g.nel) * M * M, 0.0);
-  std::map<int, std::vector<double>> tcache;
-  for (long long e = 0; e < g.nel; ++e) {
-    int key = g.mask(static_cast<int>(e));
-    if (!tcache.count(key)) {
-      std::vector<double> T(static_cast<size_t>(M) * M);
-      element_T(c, static_cast<int>(e), T.data());
-      tcache[key] = T;
+  f->tcls.assign(g.nel, 0);
+  std::vector<int> trep;
+  {
+    std::map<std::vector<double>, int> tkeys;
+    for (long long e = 0; e < g.nel; ++e) {
+      const int ei = static_cast<int>(e);
+      std::vector<double> key{static_cast<double>(g.mask(ei)), g.hx_of(ei), g.hy_of(ei)};
+      for (int F = 0; F < 4; ++F) {
+        const int e2 = g.neighbour(ei, F);
+        key.push_back(e2 >= 0 ? g.hperp(e2, opposite(F)) : 0.0);
+      }
+      auto it = tkeys.emplace(std::move(key), static_cast<int>(trep.size()));
+      if (it.second) trep.push_back(ei);
+      f->tcls[e] = it.first->second;
     }
   }
-#pragma omp parallel for schedule(static)
-  for (long long e = 0; e < g.nel; ++e) {
-    const std::vector<double>& T = tcache.at(g.mask(static_cast<int>(e)));
-    std::memcpy(f->T.data() + static_cast<size_t>(e) * M * M, T.data(), sizeof(double) * M * M);
+  std::vector<std::vector<double>> tcache(trep.size());
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long long i = 0; i < static_cast<long long>(trep.size()); ++i) {
+    tcache[i].assign(static_cast<size_t>(M) * M, 0.0);
+    element_T(c, trep[i], tcache[i].data());
   }
-  row_sums(g, f->T, &f->Rs);
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < g.nel; ++e)
+    std::memcpy(f->T.data() + static_cast<size_t>(e) * M * M, tcache[f->tcls[e]].data(), sizeof(double) * M * M);
+
+  // B 1 (slot (e, F, t): -tau p of e's face F), the per-interface means c0 of
+  // its two sides, and the deflation weights zw = B1 / c0 (Sec. 2's z_j on a
+  // uniform grid, where both sides agree and every weight is 1)
+  auto tau_p = [&](int e, int F) { const double* fc = c.face(e, F); return -fc[0] * fc[1]; };
+  const int d = static_cast<int>(g.d);
+  f->B1.assign(g.kp, 0.0);
+  f->c0.assign(d, 0.0);
+  f->zw.assign(4 * static_cast<size_t>(g.nel), 0.0);
+  f->zwa.assign(4 * static_cast<size_t>(g.nel), 0.0);
+  for (long long e = 0; e < g.nel; ++e)
+    for (int F = 0; F < 4; ++F) {
+      const int ei = static_cast<int>(e), e2 = g.neighbour(ei, F);
+      if (e2 < 0) continue;
+      const double here = tau_p(ei, F), there = tau_p(e2, opposite(F));
+      const double beta = 0.5 * (here + there);
+      f->c0[g.iface(ei, F)] = beta;
+      f->zw[4 * e + F] = here / beta;
+      f->zwa[4 * e + F] = there / beta;
+      for (int t = 0; t < n; ++t) f->B1[e * M + F * n + t] = here;
+    }
+  row_sums(g, f->T, f->zw, &f->Rs);
   if (op_only) {  // the element factors of S only
     f->operator_only = true;
     return SMPM_OK;
@@ -844,32 +930,31 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
   f->white.clear();
   for (long long e = 0; e < g.nel; ++e) (g.black(static_cast<int>(e)) ? f->black : f->white).push_back(static_cast<int>(e));
   {
-    int st = block_factors(g, f->black, f->T, &f->G, &f->X, err);
+    int st = block_factors(g, f->black, f->T, f->tcls, &f->G, &f->X, err);
     if (st != SMPM_OK) return st;
   }
 
-  // B 1 and the coarse matrix C = Z^T S Z
-  f->B1.assign(g.kp, 0.0);
-  for (long long e = 0; e < g.nel; ++e)
-    for (int F = 0; F < 4; ++F)
-      if (g.neighbour(static_cast<int>(e), F) >= 0)
-        for (int t = 0; t < n; ++t) f->B1[e * M + F * n + t] = -(F < 2 ? f->tau_x * f->p_x : f->tau_y * f->p_y);
-  const int d = static_cast<int>(g.d);
+  // the coarse matrix C = Z^T S Z: the identity part sum_slots w^2 = n (w^2 of
+  // both sides) on the diagonal (2n on a uniform grid); row (Fp, t) of T_e
+  // feeds the slot (nbr, opp Fp, t) of interface i, weighted by its zw
   f->C.assign(static_cast<size_t>(d) * d, 0.0);
-  f->c0.assign(d, 0.0);
-  for (int j = 0; j < d; ++j) f->C[static_cast<size_t>(j) * d + j] = 2.0 * n;
+  for (long long e = 0; e < g.nel; ++e)
+    for (int F = 0; F < 4; ++F) {
+      const int j = g.iface(static_cast<int>(e), F);
+      if (j >= 0) f->C[static_cast<size_t>(j) * d + j] += n * f->zw[4 * e + F] * f->zw[4 * e + F];
+    }
   for (long long e = 0; e < g.nel; ++e) {
     const double* R = f->Rs.data() + static_cast<size_t>(e) * M * 4;
     for (int Fp = 0; Fp < 4; ++Fp) {
       int i = g.iface(static_cast<int>(e), Fp);
       if (i < 0) continue;
-      f->c0[i] = -(Fp < 2 ? f->tau_x * f->p_x : f->tau_y * f->p_y);
+      const double wout = f->zwa[4 * e + Fp];  // weight of the slot (nbr, opp Fp, t)
       for (int F = 0; F < 4; ++F) {
         int j = g.iface(static_cast<int>(e), F);
         if (j < 0) continue;
         double s = 0;
         for (int t = 0; t < n; ++t) s += R[(Fp * n + t) * 4 + F];
-        f->C[static_cast<size_t>(i) * d + j] += s;
+        f->C[static_cast<size_t>(i) * d + j] += wout * s;
       }
     }
   }
@@ -938,8 +1023,9 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
     for (int G = 0; G < 4; ++G) {
       int e2 = g.neighbour(static_cast<int>(e), G);
       if (e2 < 0) continue;
-      const double tg = G < 2 ? f->tau_x : f->tau_y, pg = G < 2 ? f->p_x : f->p_y;
-      const double sx = 2.0 / g.hx, sy = 2.0 / g.hy;
+      // the slot (e2, opp G, t) is written with e2's tau, p and e's own gradient
+      const double* fn = c.face(e2, opposite(G));
+      const double tg = fn[0], pg = fn[1], sc = c.face(static_cast<int>(e), G)[2];
       for (int t = 0; t < n; ++t) {
         double v = -tg * f->uS[e2 * M + opposite(G) * n + t];
         int a, b;
@@ -947,10 +1033,10 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
         bt[b * n + a] += pg * v;
         for (int q = 0; q < n; ++q) {  // minus the transposed normal-derivative row
           switch (G) {
-            case FACE_W: bt[t * n + q] -= -sx * f->D[q] * v; break;
-            case FACE_E: bt[t * n + q] -= sx * f->D[(n - 1) * n + q] * v; break;
-            case FACE_S: bt[q * n + t] -= -sy * f->D[q] * v; break;
-            default: bt[q * n + t] -= sy * f->D[(n - 1) * n + q] * v; break;
+            case FACE_W: bt[t * n + q] -= -sc * f->D[q] * v; break;
+            case FACE_E: bt[t * n + q] -= sc * f->D[(n - 1) * n + q] * v; break;
+            case FACE_S: bt[q * n + t] -= -sc * f->D[q] * v; break;
+            default: bt[q * n + t] -= sc * f->D[(n - 1) * n + q] * v; break;
           }
         }
       }
@@ -974,7 +1060,7 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
   for (long long e = 0; e < g.nel; ++e)
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
-        double w = f->w1d[a] * f->w1d[b] * g.hx * g.hy / 4.0;
+        double w = f->w1d[a] * f->w1d[b] * g.hx_of(static_cast<int>(e)) * g.hy_of(static_cast<int>(e)) / 4.0;
         f->what[e * n * n + b * n + a] = w;
         tot += w;
       }
@@ -992,8 +1078,8 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < M; ++j) Ae[i * M + j] = Te[j * M + i];
     }
-    row_sums(g, f->Ta, &f->Rsa);
-    int sta = block_factors(g, f->black, f->Ta, &f->Ga, &f->Xa, err);
+    row_sums(g, f->Ta, f->zwa, &f->Rsa);
+    int sta = block_factors(g, f->black, f->Ta, f->tcls, &f->Ga, &f->Xa, err);
     if (sta != SMPM_OK) return sta;
     transpose_fd(n, f->fdx, &f->fdxT);
     transpose_fd(n, f->fdy, &f->fdyT);
@@ -1027,13 +1113,20 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
       for (int j = 0; j < d; ++j)
         f->Ha[static_cast<size_t>(i) * d + j] =
             Kinv[static_cast<size_t>(j) * d + i] - v[i] * ch[j] - f->uC[i] * w[j];
-    // left null vector of the permuted S^T: Phi B1 = B1 (B1 is constant on
-    // each interface), normalised
+    // left null vector of the permuted S^T: Phi B1 (Phi swaps the two slots
+    // facing each other across an interface; Phi B1 = B1 where B1 is constant
+    // on each interface), normalised
     double bn = 0;
     for (double b : f->B1) bn += b * b;
     bn = std::sqrt(bn);
-    f->uSa.resize(g.kp);
-    for (long long i = 0; i < g.kp; ++i) f->uSa[i] = f->B1[i] / bn;
+    f->uSa.assign(g.kp, 0.0);
+    for (long long e = 0; e < g.nel; ++e)
+      for (int F = 0; F < 4; ++F) {
+        const int e2 = g.neighbour(static_cast<int>(e), F);
+        if (e2 < 0) continue;
+        for (int t = 0; t < n; ++t)
+          f->uSa[e * M + F * n + t] = f->B1[static_cast<size_t>(e2) * M + opposite(F) * n + t] / bn;
+      }
     f->has_adjoint = true;
   }
   return SMPM_OK;

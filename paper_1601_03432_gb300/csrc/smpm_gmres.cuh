@@ -439,7 +439,7 @@ __device__ void white_step(const GmresArgs<S>& a, const Smem<S>& s, const S* Tw,
       size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
       S ys = ldcg(a.t + sl) + s.z[i];
       a.y[sl] = ys;
-      ci = (double)vo + (double)ys;
+      ci = g.zw ? dev_zw(g, e, F) * (double)vo + dev_zw(g, e2, F ^ 1) * (double)ys : (double)vo + (double)ys;
     }
     s.cs[i] = ci;
   }
@@ -556,7 +556,7 @@ __device__ __forceinline__ double deflate_slot_cg(const DevGeo& g, const S* y, c
   if (e2 < 0) return 0.0;
   double ys = (double)ldcg(y + sl);
   if (!chat) return ys;
-  double acc = __ldcg(chat + dev_iface(g, e, F));
+  double acc = dev_zw(g, e, F) * __ldcg(chat + dev_iface(g, e, F));
   const S* R = Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
 #pragma unroll
   for (int G = 0; G < 4; ++G) {
@@ -766,7 +766,7 @@ __device__ void white_phase_warps(const GmresArgs<S>& a, const Smem<S>& s, const
         const size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
         const S ys = ldcg(a.t + sl) + z[i];
         a.y[sl] = ys;
-        c1 = (double)vo + (double)ys;
+        c1 = g.zw ? dev_zw(g, e, F) * (double)vo + dev_zw(g, e2, F ^ 1) * (double)ys : (double)vo + (double)ys;
       }
       ci[i] = c1;
     }

@@ -18,11 +18,24 @@ inline int opposite(int F) { return F ^ 1; }
 // slot (e, F, t) at e*M + F*n + t with M = 4n; interfaces numbered row by
 // row: in element row iy, the mx-1 vertical interfaces (ix | ix+1) at
 // iy*(2mx-1) + ix, then the mx horizontal ones (row iy | iy+1) at
-// iy*(2mx-1) + mx-1 + ix.
+// iy*(2mx-1) + mx-1 + ix.  A graded grid has column edges xe (mx+1) and row
+// edges ye (my+1): element (ix, iy) covers [xe[ix], xe[ix+1]] x
+// [ye[iy], ye[iy+1]]; a uniform grid covers [0,Lx]x[0,Ly] with spacing hx, hy.
 struct Geometry {
   int mx = 0, my = 0, n = 0, M = 0;
   double Lx = 1, Ly = 1, hx = 1, hy = 1;
   long long nel = 0, nn = 0, r = 0, kp = 0, d = 0, k = 0;
+  bool graded = false;
+  std::vector<double> xe, ye;
+
+  double col_h(int ix) const { return graded ? xe[ix + 1] - xe[ix] : hx; }
+  double row_h(int iy) const { return graded ? ye[iy + 1] - ye[iy] : hy; }
+  double col_x0(int ix) const { return graded ? xe[ix] : ix * hx; }
+  double row_y0(int iy) const { return graded ? ye[iy] : iy * hy; }
+  double hx_of(int e) const { return col_h(e % mx); }
+  double hy_of(int e) const { return row_h(e / mx); }
+  // element size across face F: h_x for W/E faces, h_y for S/N faces
+  double hperp(int e, int F) const { return F < 2 ? hx_of(e) : hy_of(e); }
 
   int neighbour(int e, int F) const {
     int ix = e % mx, iy = e / mx;
@@ -62,12 +75,16 @@ struct Geometry {
 
 // Everything the factor step produces, in host memory (FP64).
 struct Factors {
-  double tau_x = 0, tau_y = 0, p_x = 0, p_y = 0;  // per face direction
+  // face data per element column (W/E faces) and row (S/N faces), three
+  // values each: penalty tau, Robin identity weight p, derivative scale 2/h
+  std::vector<double> colg, rowg;
   std::vector<double> x1d, w1d, D;                  // GLL nodes, weights, D (n*n)
-  // fast diagonalisation of the 1-D operators K_x (4 classes by the W/E face
-  // types) and K_y (4 classes by S/N): per class V (n*n), Vinv (n*n), lam (n)
+  // fast diagonalisation of the 1-D operators K_x (uniform grids: 4 classes
+  // by the W/E face types; graded: one per column) and K_y (by S/N types, or
+  // one per row): per entry V (n*n), Vinv (n*n), lam (n)
   std::vector<double> fdx, fdy;
   std::vector<double> T;     // nel * M*M : T_e[(F,t),(G,s)] row-major
+  std::vector<int> tcls;     // nel : class of T_e (elements of one class hold identical T_e)
   std::vector<double> Rs;    // nel * M*4 : row sums of T_e per input face
   std::vector<int> black, white;
   std::vector<double> G;     // nblack * M*M : (I - X Y)^-1
@@ -77,6 +94,12 @@ struct Factors {
   std::vector<double> c0;    // d : right null vector of C
   std::vector<double> uL, uS, uC, what;  // r, kp, d, r
   std::vector<double> B1;    // kp : B 1 (right null vector of S)
+  // deflation weights, 4 per element (0 on boundary faces): z_j takes the
+  // value zw[4e + F] on the n slots of face F of e, with zw = B1 / beta_j and
+  // beta_j the mean of B1 over interface j's two sides (all 1 on a uniform
+  // grid, where z_j is the indicator of Sec. 2); zwa: the adjoint system's
+  // weights, zwa[4e + F] = zw[4 nbr(e,F) + opp F]
+  std::vector<double> zw, zwa;
   bool operator_only = false;  // only T_e and its row sums (SMPM_FLAG_OPERATOR_ONLY)
   int null_iterations = 0;   // GMRES steps of the u_S bordered solve
   double null_relres = 0;
@@ -95,14 +118,15 @@ struct Factors {
 
 // Host factor step (smpm_factor_host.cpp).
 int factor_host(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err);
-// Fast-diagonalisation class of element e in x and y.
+// Fast-diagonalisation entry of element e in x and y: the face-type class
+// on a uniform grid, the column / row on a graded one.
 inline int xclass(const Geometry& g, int e) {
   int ix = e % g.mx;
-  return (ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0);
+  return g.graded ? ix : ((ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0));
 }
 inline int yclass(const Geometry& g, int e) {
   int iy = e / g.mx;
-  return (iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0);
+  return g.graded ? iy : ((iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0));
 }
 // GLL nodes and weights, differentiation matrix (host).
 void gll(int n, std::vector<double>* x, std::vector<double>* w);

@@ -17,8 +17,26 @@ namespace smpm {
 struct DevGeo {
   int mx, my, n, M;
   long long nel, kp, r, d;
-  double tau_x, tau_y, p_x, p_y, sx, sy;
+  // [tau, p, 2/h] of the W/E faces of every element column (cgeo, 3 mx) and
+  // of the S/N faces of every row (rgeo, 3 my); device memory
+  const double* cgeo;
+  const double* rgeo;
+  // weight of face F of element e in the deflation vectors z_j (zw[4e + F]):
+  // z_j is the restriction of B 1 to interface j's slots, scaled by the mean
+  // of its two sides; null on uniform grids, where every weight is 1
+  const double* zw;
+  int graded;  // fast-diagonalisation factors per column / row (else per face-type class)
+  int pad_;
 };
+
+__device__ __forceinline__ double dev_zw(const DevGeo& g, int e, int F) {
+  return g.zw ? __ldg(g.zw + 4 * (size_t)e + F) : 1.0;
+}
+
+// [tau, p, 2/h] of face F of element e
+__device__ __forceinline__ const double* face_geo(const DevGeo& g, int e, int F) {
+  return F < 2 ? g.cgeo + 3 * (e % g.mx) : g.rgeo + 3 * (e / g.mx);
+}
 
 __device__ __forceinline__ int dev_neighbour(const DevGeo& g, int e, int F) {
   int ix = e % g.mx, iy = e / g.mx;

@@ -280,7 +280,7 @@ __device__ void lk_white(const LockArgs<S>& A, const LockSmem<S>& s, const S* v,
         const size_t sl = (size_t)e2 * M + (F ^ 1) * n + tt;
         const S ys = ldcg(a.t + rho * A.vs + sl) + Z[i * RC + c];
         a.y[rho * A.vs + sl] = ys;
-        c1 = (double)vo + (double)ys;
+        c1 = g.zw ? dev_zw(g, e, F) * (double)vo + dev_zw(g, e2, F ^ 1) * (double)ys : (double)vo + (double)ys;
       }
       ci[c * M + i] = c1;
     }

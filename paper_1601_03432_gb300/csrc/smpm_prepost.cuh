@@ -111,10 +111,11 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
       double v = P.f[gq];
       if (P.gn) {
         const long long s0 = e * M;
-        if (aa == 0 && dev_neighbour(g, (int)e, 0) < 0) v += g.tau_x * P.gn[s0 + bb];
-        if (aa == n - 1 && dev_neighbour(g, (int)e, 1) < 0) v += g.tau_x * P.gn[s0 + n + bb];
-        if (bb == 0 && dev_neighbour(g, (int)e, 2) < 0) v += g.tau_y * P.gn[s0 + 2 * n + aa];
-        if (bb == n - 1 && dev_neighbour(g, (int)e, 3) < 0) v += g.tau_y * P.gn[s0 + 3 * n + aa];
+        const double tx = face_geo(g, (int)e, 0)[0], ty = face_geo(g, (int)e, 2)[0];
+        if (aa == 0 && dev_neighbour(g, (int)e, 0) < 0) v += tx * P.gn[s0 + bb];
+        if (aa == n - 1 && dev_neighbour(g, (int)e, 1) < 0) v += tx * P.gn[s0 + n + bb];
+        if (bb == 0 && dev_neighbour(g, (int)e, 2) < 0) v += ty * P.gn[s0 + 2 * n + aa];
+        if (bb == n - 1 && dev_neighbour(g, (int)e, 3) < 0) v += ty * P.gn[s0 + 3 * n + aa];
       }
       P.b[gq] = v;
       part += P.adjoint ? v : P.uL[gq] * v;
@@ -137,7 +138,8 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
     }
     __syncthreads();
     elem_fd(P, (int)e, B, U, t1);
-    // flux of w into the slot (nbr, opp F, t): -tau_F (p_F w - n_F . grad w)
+    // flux of w into the slot (nbr, opp F, t): -tau' (p' w - n_F . grad w) with
+    // tau', p' of the neighbour's face opp F and the gradient in e's own size
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
       const int F = i / n, t = i % n;
       const int e2 = dev_neighbour(g, (int)e, F);
@@ -145,11 +147,13 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
       if (e2 >= 0) {
         int aa, bb;
         face_node(n, F, t, &aa, &bb);
-        const double tau = F < 2 ? g.tau_x : g.tau_y, pw = F < 2 ? g.p_x : g.p_y;
-        val = P.adjoint ? U[bb * n + aa] : -tau * (pw * U[bb * n + aa] - normal_deriv(g, P.D, U, F, t));
+        const double* fn = face_geo(g, e2, F ^ 1);
+        val = P.adjoint ? U[bb * n + aa]
+                        : -fn[0] * (fn[1] * U[bb * n + aa] - normal_deriv(g, P.D, U, F, t, face_geo(g, (int)e, F)[2]));
         const size_t sl = (size_t)e2 * M + (F ^ 1) * n + t;
         P.bS[sl] = val;
         pus += P.uS[sl] * val;
+        val *= dev_zw(g, e2, F ^ 1);  // its weight in Z^T b_S
       }
       s.cs[i] = val;
     }
@@ -203,7 +207,7 @@ __device__ bool pre_body(const PrePostArgs& P, unsigned char* smraw, unsigned& e
     if (a.precond == 2) {
       // - (S Z c_hat_b) at the slot (pull form), as in the GMRES deflation
       const int ii = (int)(sl % M), t = ii % n, e2 = dev_neighbour(g, e, F);
-      double acc = __ldcg(a.chat + dev_iface(g, e, F));
+      double acc = dev_zw(g, e, F) * __ldcg(a.chat + dev_iface(g, e, F));
       const double* R = a.Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
       for (int G2 = 0; G2 < 4; ++G2) {
         const int jj = dev_iface(g, e2, G2);
@@ -274,7 +278,7 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
         const long long sl = entry_slot(a, i);
         if (sl < 0) continue;
         const int e = (int)(sl / M), F = (int)(sl % M) / n, j = dev_iface(g, e, F);
-        P.xs[sl] = j < 0 ? 0.0 : __ldcg(a.t + sl) - (__ldcg(a.chat + j) - P.chatb[j]);
+        P.xs[sl] = j < 0 ? 0.0 : __ldcg(a.t + sl) - dev_zw(g, e, F) * (__ldcg(a.chat + j) - P.chatb[j]);
       }
     }
   }
@@ -297,10 +301,12 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
           }
         } else {
           // - B_e^T mu: the slot (F, t) feeds, through B, the flux
-          // -tau_F (p_F u(q) - n_F.grad u(q)) at face node q = (F, t); its
-          // transpose touches the n nodes on the normal line through q
-          const double tau = F < 2 ? g.tau_x : g.tau_y, pw = F < 2 ? g.p_x : g.p_y;
-          const double sc = F < 2 ? g.sx : g.sy;
+          // -tau' (p' u(q) - n_F.grad u(q)) at face node q = (F, t), tau' and p'
+          // of the neighbour's face opp F; its transpose touches the n nodes
+          // on the normal line through q
+          const double* fn = face_geo(g, dev_neighbour(g, (int)e, F), F ^ 1);
+          const double tau = fn[0], pw = fn[1];
+          const double sc = face_geo(g, (int)e, F)[2];
           const int drow = (F & 1) ? n - 1 : 0;   // D row of the face end
           const double sgn = (F & 1) ? 1.0 : -1.0;  // outward normal along the axis
           for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
@@ -356,7 +362,7 @@ __device__ bool post_body(const PrePostArgs& P, unsigned char* smraw, unsigned& 
           int aa, bb;
           face_node(n, F, t, &aa, &bb);
           const long long q = e * nn + bb * n + aa;
-          v = (F < 2 ? g.tau_x : g.tau_y) * (__ldcg(P.u + q) - mean * P.uL[q]);
+          v = face_geo(g, (int)e, F)[0] * (__ldcg(P.u + q) - mean * P.uL[q]);
         }
         P.gg[e * M + i] = v;
       }

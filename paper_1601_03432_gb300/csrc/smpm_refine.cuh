@@ -57,7 +57,7 @@ __device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& 
     const long long sl = entry_slot(a, i);
     if (sl < 0) continue;
     const int e = (int)(sl / M), F = (int)(sl % M) / n, j = dev_iface(g, e, F);
-    if (j >= 0) R.xS[sl] += (double)__ldcg(a.t + sl) - (__ldcg(a.chat + j) - R.chat_r[j]);
+    if (j >= 0) R.xS[sl] += (double)__ldcg(a.t + sl) - dev_zw(g, e, F) * (__ldcg(a.chat + j) - R.chat_r[j]);
     a.x[sl] = 0.f;
   }
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return -1;
@@ -79,6 +79,7 @@ __device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& 
           rr = R.bS[sl] - (__ldcg(R.xS + sl) + zw[i]);
           R.r[sl] = rr;
           pr += rr * rr;
+          rr *= dev_zw(g, e2, F ^ 1);  // its weight in Z^T r
         }
         pw[i] = rr;
       }
@@ -104,6 +105,7 @@ __device__ int refine_body(const RefineArgs& R, unsigned char* smraw, unsigned& 
         rr = R.bS[sl] - (__ldcg(R.xS + sl) + z64[i]);
         R.r[sl] = rr;
         pr += rr * rr;
+        rr *= dev_zw(g, e2, F ^ 1);  // its weight in Z^T r
       }
       red64[i] = rr;
     }

@@ -175,30 +175,34 @@ __device__ __forceinline__ void face_node(int n, int F, int t, int* a, int* b) {
 }
 
 // n_F . grad U at face node t (U in shared memory, D in global).
-__device__ double normal_deriv(const DevGeo& g, const double* __restrict__ D, const double* U, int F, int t) {
+// n_F . grad U at face node t of face F (sc = 2/h of the element across F).
+__device__ double normal_deriv(const DevGeo& g, const double* __restrict__ D, const double* U, int F, int t,
+                               double sc) {
   const int n = g.n;
   double acc = 0;
   switch (F) {
-    case 0: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[t * n + c]; return -g.sx * acc;
-    case 1: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[t * n + c]; return g.sx * acc;
-    case 2: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[c * n + t]; return -g.sy * acc;
-    default: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[c * n + t]; return g.sy * acc;
+    case 0: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[t * n + c]; return -sc * acc;
+    case 1: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[t * n + c]; return sc * acc;
+    case 2: for (int c = 0; c < n; ++c) acc += __ldg(D + c) * U[c * n + t]; return -sc * acc;
+    default: for (int c = 0; c < n; ++c) acc += __ldg(D + (n - 1) * n + c) * U[c * n + t]; return sc * acc;
   }
 }
 
+// fast-diagonalisation entry: face-type class, or the column / row on a graded grid
 __device__ __forceinline__ const double* fd_x(const DevGeo& g, const double* fdx, int e) {
   int ix = e % g.mx;
-  int cls = (ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0);
+  int cls = g.graded ? ix : ((ix > 0 ? 1 : 0) | (ix < g.mx - 1 ? 2 : 0));
   return fdx + (size_t)cls * (2 * g.n * g.n + g.n);
 }
 __device__ __forceinline__ const double* fd_y(const DevGeo& g, const double* fdy, int e) {
   int iy = e / g.mx;
-  int cls = (iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0);
+  int cls = g.graded ? iy : ((iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0));
   return fdy + (size_t)cls * (2 * g.n * g.n + g.n);
 }
 
 // b_S = B A^-1 b (Eq. schur_complement_system): one CTA per element; the flux of
-// w = A_e^-1 b_e into the slot (nbr, opp F, t) is -tau_F (p_F w - n_F.grad w).
+// w = A_e^-1 b_e into the slot (nbr, opp F, t) is -tau' (p' w - n_F.grad w),
+// tau' and p' those of the neighbour's face opp F.
 // Slots on boundary faces are not written (the caller zeroes b_S).
 __global__ void k_schur_rhs(DevGeo g, const double* __restrict__ fdx, const double* __restrict__ fdy,
                             const double* __restrict__ D, const double* __restrict__ b, double* bS) {
@@ -214,9 +218,9 @@ __global__ void k_schur_rhs(DevGeo g, const double* __restrict__ fdx, const doub
     if (e2 < 0) continue;
     int a, bb;
     face_node(n, F, t, &a, &bb);
-    double tau = F < 2 ? g.tau_x : g.tau_y, p = F < 2 ? g.p_x : g.p_y;
-    double val = p * U[bb * n + a] - normal_deriv(g, D, U, F, t);
-    bS[(size_t)e2 * g.M + (F ^ 1) * n + t] = -tau * val;
+    const double* fn = face_geo(g, e2, F ^ 1);
+    double val = fn[1] * U[bb * n + a] - normal_deriv(g, D, U, F, t, face_geo(g, e, F)[2]);
+    bS[(size_t)e2 * g.M + (F ^ 1) * n + t] = -fn[0] * val;
   }
 }
 
@@ -333,7 +337,7 @@ __global__ void k_white(DevGeo g, const int* __restrict__ white, const S* __rest
       size_t s = (size_t)e2 * M + (F ^ 1) * n + tt;
       S ys = t[s] + z[i];
       y[s] = ys;
-      ci = (double)vo + (double)ys;
+      ci = g.zw ? dev_zw(g, e, F) * (double)vo + dev_zw(g, e2, F ^ 1) * (double)ys : (double)vo + (double)ys;
     }
     cs[i] = ci;
   }
@@ -349,7 +353,7 @@ __global__ void k_white(DevGeo g, const int* __restrict__ white, const S* __rest
   }
 }
 
-// c = Z^T v: one thread per interface, summing its 2n slots.
+// c = Z^T v: one thread per interface, summing its 2n slots (weighted).
 template <typename S>
 __global__ void k_zt(DevGeo g, const S* __restrict__ v, double* c) {
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -360,9 +364,10 @@ __global__ void k_zt(DevGeo g, const S* __restrict__ v, double* c) {
   if (rem < g.mx - 1) { e1 = iy * g.mx + rem; F1 = 1; }
   else { e1 = iy * g.mx + rem - (g.mx - 1); F1 = 3; }
   int e2 = dev_neighbour(g, e1, F1);
+  const double w1 = dev_zw(g, e1, F1), w2 = dev_zw(g, e2, F1 ^ 1);
   double s = 0;
   for (int t = 0; t < n; ++t)
-    s += (double)v[(size_t)e1 * M + F1 * n + t] + (double)v[(size_t)e2 * M + (F1 ^ 1) * n + t];
+    s += w1 * (double)v[(size_t)e1 * M + F1 * n + t] + w2 * (double)v[(size_t)e2 * M + (F1 ^ 1) * n + t];
   c[j] = s;
 }
 
@@ -388,7 +393,7 @@ __device__ __forceinline__ double deflate_slot(const DevGeo& g, const S* __restr
   if (e2 < 0) return 0.0;
   double ys = (double)y[s];
   if (!chat) return ys;
-  double acc = chat[dev_iface(g, e, F)];
+  double acc = dev_zw(g, e, F) * chat[dev_iface(g, e, F)];
   const S* R = Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
 #pragma unroll
   for (int G = 0; G < 4; ++G) {
@@ -443,7 +448,7 @@ __global__ void k_assemble(DevGeo g, const double* __restrict__ t, const double*
   int j = dev_iface(g, e, F);
   if (j < 0) { x[s] = 0.0; return; }
   double cb = chat_b ? chat_b[j] : 0.0;
-  x[s] = t[s] - (chat ? chat[j] : 0.0) + cb;
+  x[s] = t[s] - dev_zw(g, e, F) * ((chat ? chat[j] : 0.0) - cb);
 }
 
 #include "smpm_gmres.cuh"
@@ -1018,6 +1023,8 @@ struct smpm_handle_s {
   // device factors
   double *dT = nullptr, *dRs = nullptr, *dG = nullptr, *dX = nullptr, *dH = nullptr;
   double *dfdx = nullptr, *dfdy = nullptr, *dD = nullptr;
+  double *dcgeo = nullptr, *drgeo = nullptr;  // per column / row: tau, p, 2/h
+  double *dzw = nullptr, *dzwa = nullptr;      // deflation weights (graded grids), forward / adjoint
   double *duL = nullptr, *duS = nullptr, *duC = nullptr, *dwhat = nullptr;
   int *dblack = nullptr, *dwhite = nullptr;
   // workspace
@@ -1359,7 +1366,7 @@ GmresArgs<double> gmres_args(smpm_handle h, double tol, bool adj = false) {
   a.nblack = (int)h->f.black.size();
   a.nwhite = (int)h->f.white.size();
   a.Tc = h->dT; a.Gc = h->dG; a.Xc = h->dX; a.Rs = h->dRs; a.H = h->dH;
-  if (adj) { a.Tc = h->dTa; a.Gc = h->dGa; a.Xc = h->dXa; a.Rs = h->dRsa; a.H = h->dHa; }
+  if (adj) { a.Tc = h->dTa; a.Gc = h->dGa; a.Xc = h->dXa; a.Rs = h->dRsa; a.H = h->dHa; a.g.zw = h->dzwa; }
   a.vglob = h->wV; a.vown = h->wvown; a.t = h->wt; a.y = h->wy;
   a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg; a.x = h->wx;
   a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
@@ -2516,6 +2523,32 @@ void smpm_default_opts(smpm_opts* o) {
 
 const char* smpm_last_error(void) { return g_last_error.c_str(); }
 
+smpm_status smpm_setup_graded(int mx, int my, int n, const double* xs, const double* ys, smpm_handle* out) try {
+  if (!out) return fail(SMPM_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (!xs || !ys) return fail(SMPM_EINVAL, "null element edges");
+  if (mx < 1 || my < 1 || mx > 4096 || my > 4096) return fail(SMPM_EINVAL, "grid sizes out of range");
+  for (int i = 0; i <= mx; ++i)
+    if (!std::isfinite(xs[i]) || (i > 0 && !(xs[i] > xs[i - 1])))
+      return fail(SMPM_EINVAL, "column edges must be finite and strictly increasing");
+  for (int i = 0; i <= my; ++i)
+    if (!std::isfinite(ys[i]) || (i > 0 && !(ys[i] > ys[i - 1])))
+      return fail(SMPM_EINVAL, "row edges must be finite and strictly increasing");
+  smpm_status s = smpm_setup(mx, my, n, xs[mx] - xs[0], ys[my] - ys[0], out);
+  if (s != SMPM_OK) return s;
+  Geometry& g = (*out)->g;
+  g.graded = true;
+  g.xe.assign(xs, xs + mx + 1);
+  g.ye.assign(ys, ys + my + 1);
+  return SMPM_OK;
+} catch (...) {
+  if (out && *out) {
+    smpm_destroy(*out);
+    *out = nullptr;
+  }
+  return host_exception();
+}
+
 smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle* out) try {
   if (!out) return fail(SMPM_EINVAL, "null handle pointer");
   *out = nullptr;
@@ -2564,11 +2597,12 @@ smpm_status smpm_node_coords(smpm_handle h, double* x, double* y) try {
   gll(g.n, &xi, &w);
   for (long long e = 0; e < g.nel; ++e) {
     int ix = (int)(e % g.mx), iy = (int)(e / g.mx);
+    const double x0 = g.col_x0(ix), y0 = g.row_y0(iy), hx = g.col_h(ix), hy = g.row_h(iy);
     for (int b = 0; b < g.n; ++b)
       for (int a = 0; a < g.n; ++a) {
         long long q = e * g.nn + b * g.n + a;
-        x[q] = ix * g.hx + (xi[a] + 1.0) * g.hx / 2.0;
-        y[q] = iy * g.hy + (xi[b] + 1.0) * g.hy / 2.0;
+        x[q] = x0 + (xi[a] + 1.0) * hx / 2.0;
+        y[q] = y0 + (xi[b] + 1.0) * hy / 2.0;
       }
   }
   return SMPM_OK;
@@ -2583,7 +2617,8 @@ smpm_status smpm_node_mass(smpm_handle h, double* wq) try {
   gll(g.n, &xi, &w);
   for (long long e = 0; e < g.nel; ++e)
     for (int b = 0; b < g.n; ++b)
-      for (int a = 0; a < g.n; ++a) wq[e * g.nn + b * g.n + a] = w[a] * w[b] * g.hx * g.hy / 4.0;
+      for (int a = 0; a < g.n; ++a)
+        wq[e * g.nn + b * g.n + a] = w[a] * w[b] * g.hx_of((int)e) * g.hy_of((int)e) / 4.0;
   return SMPM_OK;
 } catch (...) {
   return host_exception();
@@ -2682,21 +2717,22 @@ smpm_status smpm_factor_many(const smpm_handle* hs, int count, const smpm_opts* 
 
 namespace {
 
-// Class tables of the class-shared apply: one T per face-type mask (the
-// copies of T_e within a class are identical), tiles of kClassTile elements.
+// Class tables of the class-shared apply: one T per T class of the factor
+// step (face types, and on a graded grid the sizes; the copies of T_e within
+// a class are identical), tiles of kClassTile elements.
 smpm_status upload_classes(smpm_handle h, const std::vector<double>& Tc, cudaStream_t st) {
   const Geometry& g = h->g;
   const size_t MM = (size_t)g.M * g.M;
-  std::vector<int> cls_of_mask(16, -1), first;
+  std::vector<int> cls_of(g.nel, -1), first;
   std::vector<std::vector<int>> members;
   for (long long e = 0; e < g.nel; ++e) {
-    const int key = g.mask((int)e);
-    if (cls_of_mask[key] < 0) {
-      cls_of_mask[key] = (int)members.size();
+    const int key = h->f.tcls[e];
+    if (cls_of[key] < 0) {
+      cls_of[key] = (int)members.size();
       members.emplace_back();
       first.push_back((int)e);
     }
-    members[cls_of_mask[key]].push_back((int)e);
+    members[cls_of[key]].push_back((int)e);
   }
   std::vector<double> Tcls(members.size() * MM);
   for (size_t c = 0; c < members.size(); ++c)
@@ -2735,11 +2771,14 @@ smpm_status factor_device_operator(smpm_handle h, cudaStream_t st) {
   DevGeo& dg = h->dg;
   dg.mx = g.mx; dg.my = g.my; dg.n = g.n; dg.M = g.M;
   dg.nel = g.nel; dg.kp = g.kp; dg.r = g.r; dg.d = g.d;
-  dg.tau_x = h->f.tau_x; dg.tau_y = h->f.tau_y; dg.p_x = h->f.p_x; dg.p_y = h->f.p_y;
-  dg.sx = 2.0 / g.hx; dg.sy = 2.0 / g.hy;
+  dg.graded = g.graded ? 1 : 0;
   smpm_status s;
   std::vector<double> Tc = transpose_blocks(h->f.T, g.M, g.nel);
-  if ((s = upload(h, &h->dT, Tc, st))) return s;
+  if ((s = upload(h, &h->dT, Tc, st)) || (s = upload(h, &h->dcgeo, h->f.colg, st)) ||
+      (s = upload(h, &h->drgeo, h->f.rowg, st)))
+    return s;
+  dg.cgeo = h->dcgeo;
+  dg.rgeo = h->drgeo;
   if (h->opts.precision == 1 && (s = upload(h, &h->dT32, std::vector<float>(Tc.begin(), Tc.end()), st))) return s;
   std::vector<ElemMeta<double>> t64(g.nel);
   std::vector<ElemMeta<float>> t32(h->dT32 ? g.nel : 0);
@@ -2769,8 +2808,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
   DevGeo& dg = h->dg;
   dg.mx = g.mx; dg.my = g.my; dg.n = g.n; dg.M = g.M;
   dg.nel = g.nel; dg.kp = g.kp; dg.r = g.r; dg.d = g.d;
-  dg.tau_x = h->f.tau_x; dg.tau_y = h->f.tau_y; dg.p_x = h->f.p_x; dg.p_y = h->f.p_y;
-  dg.sx = 2.0 / g.hx; dg.sy = 2.0 / g.hy;
+  dg.graded = g.graded ? 1 : 0;
   smpm_status s;
   // device copies of T_e, G_b and the X_F blocks are column-major
   std::vector<double> Tc = transpose_blocks(h->f.T, g.M, g.nel), Gc = transpose_blocks(h->f.G, g.M, h->f.black.size()),
@@ -2781,8 +2819,16 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       (s = upload(h, &h->dfdy, h->f.fdy, st)) || (s = upload(h, &h->dD, h->f.D, st)) ||
       (s = upload(h, &h->duL, h->f.uL, st)) || (s = upload(h, &h->duS, h->f.uS, st)) ||
       (s = upload(h, &h->duC, h->f.uC, st)) || (s = upload(h, &h->dwhat, h->f.what, st)) ||
-      (s = upload(h, &h->dblack, h->f.black, st)) || (s = upload(h, &h->dwhite, h->f.white, st)))
+      (s = upload(h, &h->dblack, h->f.black, st)) || (s = upload(h, &h->dwhite, h->f.white, st)) ||
+      (s = upload(h, &h->dcgeo, h->f.colg, st)) || (s = upload(h, &h->drgeo, h->f.rowg, st)))
     return s;
+  dg.cgeo = h->dcgeo;
+  dg.rgeo = h->drgeo;
+  if (g.graded) {  // uniform grids: every deflation weight is 1 (no table)
+    if ((s = upload(h, &h->dzw, h->f.zw, st))) return s;
+    if (h->f.has_adjoint && (s = upload(h, &h->dzwa, h->f.zwa, st))) return s;
+  }
+  dg.zw = h->dzw;
   const size_t kp = g.kp, r = g.r, d = g.d, m = opts.restart;
   const size_t nbs = blocks_for(g.kp, kSlotsPerBlock);
   if ((s = dalloc(h, &h->wb, r)) || (s = dalloc(h, &h->wbS, kp)) || (s = dalloc(h, &h->wV, (m + 1) * kp)) ||
@@ -2883,7 +2929,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       for (int F = 0; F < 4; ++F) {
         int j = h->g.iface((int)e, F);
         if (j < 0) continue;
-        for (int t = 0; t < g.n; ++t) ztus[j] += h->f.uS[e * g.M + F * g.n + t];
+        for (int t = 0; t < g.n; ++t) ztus[j] += h->f.zw[4 * e + F] * h->f.uS[e * g.M + F * g.n + t];
       }
     if ((s = upload(h, &h->dZtuS, ztus, st))) return s;
     {
@@ -2922,7 +2968,7 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
         for (int F = 0; F < 4; ++F) {
           int j = h->g.iface((int)e, F);
           if (j < 0) continue;
-          for (int t = 0; t < g.n; ++t) ztusa[j] += h->f.uSa[e * g.M + F * g.n + t];
+          for (int t = 0; t < g.n; ++t) ztusa[j] += h->f.zwa[4 * e + F] * h->f.uSa[e * g.M + F * g.n + t];
         }
       if ((s = upload(h, &h->dTa, h->f.T, st)) || (s = upload(h, &h->dRsa, h->f.Rsa, st)) ||
           (s = upload(h, &h->dGa, Gca, st)) || (s = upload(h, &h->dXa, Xca, st)) ||
@@ -3238,6 +3284,8 @@ smpm_status smpm_host_factor(smpm_handle h, const char* name, double* out, long 
   else if (nm == "Xa") src = &f.Xa;
   else if (nm == "Ha") src = &f.Ha;
   else if (nm == "Rsa") src = &f.Rsa;
+  else if (nm == "zw") src = &f.zw;
+  else if (nm == "zwa") src = &f.zwa;
   else if (nm == "Rs") src = &f.Rs;
   else if (nm == "uSa") src = &f.uSa;
   else if (nm == "fdx") src = &f.fdx;
@@ -3586,8 +3634,9 @@ __global__ void __launch_bounds__(256) k_deflate_noalloc(DevGeo g, const double*
     if (rem < g.mx - 1) { e1 = iy * g.mx + rem; F1 = 1; }
     else { e1 = iy * g.mx + rem - (g.mx - 1); F1 = 3; }
     int e2 = dev_neighbour(g, e1, F1);
+    const double w1 = dev_zw(g, e1, F1), w2 = dev_zw(g, e2, F1 ^ 1);
     double s = 0;
-    for (int t = 0; t < n; ++t) s += v[(size_t)e1 * M + F1 * n + t] + v[(size_t)e2 * M + (F1 ^ 1) * n + t];
+    for (int t = 0; t < n; ++t) s += w1 * v[(size_t)e1 * M + F1 * n + t] + w2 * v[(size_t)e2 * M + (F1 ^ 1) * n + t];
     c[j] = s;
   }
   bool ok = grid_sync(bar, err, epoch, (int)gridDim.x);

@@ -21,6 +21,9 @@ Workloads (the paper measures on no public dataset; these stand in for it):
   m in {4..32}, n in {8..24}, nrhs in {1..16}.
 * ``polynomial_problem``: u = a cubic polynomial with f = lap u and
   g = n . grad u, whose discrete solution is exact whenever n >= 4.
+* ``clustered_edges`` / ``jittered_edges``: element edges of graded grids -
+  tanh clustering toward both walls (the element-size profile of
+  wall-resolved grids), or uniform edges moved by a seeded fraction of h.
 """
 import numpy as np
 
@@ -88,3 +91,22 @@ def polynomial_problem(x, y, coeffs=(0.3, -1.1, 0.7, 0.45, -0.2, 0.9)):
         return nx * ux + ny * uy
 
     return f, u, g
+
+
+def clustered_edges(m, L=1.0, stretch=2.0):
+    """m + 1 edges on [0, L] clustered toward both ends by tanh stretching
+    (larger stretch, thinner wall elements)."""
+    s = np.linspace(-1.0, 1.0, m + 1)
+    e = np.tanh(stretch * s) / np.tanh(stretch)
+    e = L * (e + 1.0) / 2.0
+    e[0], e[-1] = 0.0, L
+    return e
+
+
+def jittered_edges(m, L, seed, amp=0.3):
+    """m + 1 edges on [0, L]: interior uniform edges moved by U(-amp, amp) h."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = L / m
+    e = np.arange(m + 1) * h
+    e[1:-1] += rng.uniform(-amp, amp, m - 1) * h
+    return e

@@ -125,17 +125,30 @@ def test_binding_refuses_short_host_or_mistyped_buffers():
         g.solve_host(np.zeros(g.r, dtype=np.float32), np.zeros(g.r))
 
 
-GRIDS = [(2, 2, 6, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (4, 3, 7, 1.0, 2.0), (5, 4, 4, 1.0, 1.0)]
+# graded grids (Sec. 1.2): column edges, row edges
+GRADED_A = ([0.0, 0.2, 0.5, 1.0, 1.3], [0.0, 0.35, 0.5, 1.1])
+GRADED_B = ([0.0, 0.3, 0.45, 1.0], [0.0, 0.5, 1.0, 1.5])     # rows uniform, columns graded
+GRIDS = [(2, 2, 6, 1.0, 1.0), (3, 2, 5, 1.5, 0.75), (4, 3, 7, 1.0, 2.0), (5, 4, 4, 1.0, 1.0),
+         (4, 3, 6, 0, 0) + GRADED_A, (3, 3, 5, 0, 0) + GRADED_B]
 
 
-@pytest.fixture(scope="module", params=GRIDS, ids=lambda p: "x".join(map(str, p[:3])))
-def pair(request):
-    mx, my, n, Lx, Ly = request.param
-    og = SMPMGrid(mx, my, n, Lx, Ly)
+def _grid_ids(p):
+    return "x".join(map(str, p[:3])) + ("g" if len(p) > 5 else "")
+
+
+def _make(p, flags=0):
+    mx, my, n, Lx, Ly = p[:5]
+    xs, ys = p[5:] if len(p) > 5 else (None, None)
+    og = SMPMGrid(mx, my, n, Lx, Ly, xs=xs, ys=ys)
     osys = SchurSystem(og)
-    lg = B.Grid(mx, my, n, Lx, Ly)
-    lg.factor_host_only()
+    lg = B.Grid(mx, my, n, Lx, Ly, xs=xs, ys=ys)
+    lg.factor_host_only(flags=flags)
     return og, osys, lg
+
+
+@pytest.fixture(scope="module", params=GRIDS, ids=_grid_ids)
+def pair(request):
+    return _make(request.param)
 
 
 def test_sizes_and_coords(pair):
@@ -213,6 +226,11 @@ def test_coarse_objects(pair):
     d = og.d
     C = lg.coarse_matrix()
     np.testing.assert_allclose(C, osys.C, atol=1e-11 * np.abs(osys.C).max())
+    # deflation weights (1 on uniform grids) and B 1 = Z c0
+    zw = lg.host_factor("zw").reshape(og.nel, 4)
+    w = np.array([zw[e, F] for (e, F, t) in og.slots])
+    np.testing.assert_allclose(w, osys.zweights, rtol=1e-14)
+    np.testing.assert_allclose(og.from_padded(lg.host_factor("B1")), osys.B1, rtol=1e-14)
     c0 = lg.host_factor("c0")
     assert abs(abs(c0 @ osys.c0) / (np.linalg.norm(c0) * np.linalg.norm(osys.c0)) - 1) < 1e-13
     uC = lg.host_factor("uC")
@@ -237,14 +255,9 @@ def test_null_vectors(pair):
 
 
 # ---------------------------------------------------- transposed system
-@pytest.fixture(scope="module", params=GRIDS[1:3], ids=lambda p: "x".join(map(str, p[:3])))
+@pytest.fixture(scope="module", params=GRIDS[1:3] + GRIDS[4:5], ids=_grid_ids)
 def apair(request):
-    mx, my, n, Lx, Ly = request.param
-    og = SMPMGrid(mx, my, n, Lx, Ly)
-    osys = SchurSystem(og)
-    lg = B.Grid(mx, my, n, Lx, Ly)
-    lg.factor_host_only(flags=B.FLAG_ADJOINT)
-    return og, osys, lg
+    return _make(request.param, flags=B.FLAG_ADJOINT)
 
 
 def _phi(og):
@@ -316,10 +329,13 @@ def test_adjoint_coarse_and_null_vectors(apair):
     r = np.random.default_rng(6).standard_normal(d)
     ref = AdjointDeflation(osys).coarse_solve(r)
     np.testing.assert_allclose(Ha @ r, ref, atol=1e-9 * np.abs(ref).max())
+    # left null vector of Phi S^T Phi: Phi B1 (= B1 where B1 is constant on
+    # every interface)
+    phi = _phi(og)
     uSa = og.from_padded(lg.host_factor("uSa"))
-    ref = osys.B1 / np.linalg.norm(osys.B1)
+    ref = (osys.B1 / np.linalg.norm(osys.B1))[phi]
     assert np.linalg.norm(uSa * np.sign(uSa @ ref) - ref) < 1e-14
-    assert np.linalg.norm(osys.S @ uSa) < 1e-12 * abs(osys.S).max()
+    assert np.linalg.norm(osys.S @ uSa[phi]) < 1e-12 * abs(osys.S).max()
 
 
 def test_transposed_fast_diagonalisation(apair):
@@ -327,7 +343,7 @@ def test_transposed_fast_diagonalisation(apair):
     n = og.n
     fd, fdT = lg.host_factor("fdx"), lg.host_factor("fdxT")
     fds = 2 * n * n + n
-    for cls in range(4):
+    for cls in range(len(fd) // fds):
         V, Vi, lam = (fd[cls * fds:cls * fds + n * n].reshape(n, n),
                       fd[cls * fds + n * n:cls * fds + 2 * n * n].reshape(n, n), fd[cls * fds + 2 * n * n:(cls + 1) * fds])
         W, Wi, lamT = (fdT[cls * fds:cls * fds + n * n].reshape(n, n),

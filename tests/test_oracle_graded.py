@@ -3,8 +3,12 @@ invertible maps of the master square; here axis-aligned rectangles whose
 width varies by column and height by row).
 
 On a graded grid every element's factors differ, tau_F and p_F differ across
-an interface, and B 1 is no longer constant on each interface, so the coarse
-matrix C = Z^T S Z of Sec. 2 becomes nonsingular.  The pins:
+an interface, and B 1 (the right null vector of S) is no longer constant on
+each interface.  With the 0/1 deflation vectors of Sec. 2 the coarse matrix
+C = Z^T S Z then becomes nonsingular and B 1 leaves the coarse space; the
+oracle's graded reading weights z_j by B 1 (divided by the mean of the two
+sides), which keeps B 1 = Z c0 and is the indicator on a uniform grid.  The
+pins:
 
 * L computed a second way, from Lagrange polynomials in physical coordinates
   (tests/smpm_by_polynomials.py), entry by entry;
@@ -15,9 +19,11 @@ matrix C = Z^T S Z of Sec. 2 becomes nonsingular.  The pins:
   each face uses the element's own size);
 * GLL mass: total = area, exact integral of a quartic;
 * a grid given by uniform edges is the uniform grid, with singular C;
-* Algorithms 1-3 and the adjoint reach the direct solution with the
-  nonsingular C; C is singular exactly when every interface has the same size
-  across it on both sides.
+* Algorithms 1-3 and the adjoint reach the direct solution; with indicator
+  vectors C is singular exactly when every interface has the same size across
+  it, with weighted vectors always (C c0 = 0, weights 1 on uniform grids);
+* on a wall-clustered grid the weighted deflation keeps the iteration count
+  near the uniform grid's, while the indicator vectors stagnate.
 
 Planted graded mistakes (the neighbour's gradient taken with the receiving
 element's size, the neighbour's own p_F on its trace, the penalty from the
@@ -141,9 +147,28 @@ def test_uniform_edges_give_the_uniform_grid():
     ([0.0, 0.5, 1.0, 1.5], [0.0, 0.3, 0.7], False),       # one row taller
     ([0.0, 0.5, 1.0, 1.5], [0.0, 0.3, 0.6, 1.1], False),  # the last row taller
 ])
-def test_coarse_matrix_singular_only_when_sizes_match(xs, ys, singular):
+def test_weighted_coarse_space_holds_B1(xs, ys, singular):
     g = SMPMGrid(len(xs) - 1, len(ys) - 1, 4, xs=xs, ys=ys)
     sysm = SchurSystem(g)
+    assert sysm.coarse_singular
+    assert np.abs(sysm.Z @ sysm.c0 - sysm.B1).max() < 1e-13 * np.abs(sysm.B1).max()
+    assert np.abs(sysm.C @ sysm.c0).max() < 1e-10 * np.abs(sysm.C).max() * np.linalg.norm(sysm.c0)
+    if singular:   # uniform: exactly the 0/1 vectors of Sec. 2
+        assert np.all(sysm.zweights == 1.0)
+    else:          # each side's weight is its B 1 over the interface mean
+        assert np.abs(sysm.zweights - 1.0).max() > 1e-3
+        assert np.allclose(sysm.Z.T @ sysm.Z @ np.ones(g.d) / (2 * g.n), 1.0, atol=0.5)
+
+
+@pytest.mark.parametrize("xs,ys,singular", [
+    ([0.0, 0.5, 1.0, 1.5], [0.0, 0.3, 0.6], True),        # uniform
+    ([0.0, 0.5, 1.0, 1.6], [0.0, 0.3, 0.6], False),       # one column wider
+    ([0.0, 0.5, 1.0, 1.5], [0.0, 0.3, 0.7], False),       # one row taller
+    ([0.0, 0.5, 1.0, 1.5], [0.0, 0.3, 0.6, 1.1], False),  # the last row taller
+])
+def test_indicator_coarse_matrix_singular_only_when_sizes_match(xs, ys, singular):
+    g = SMPMGrid(len(xs) - 1, len(ys) - 1, 4, xs=xs, ys=ys)
+    sysm = SchurSystem(g, deflation="indicator")
     assert sysm.coarse_singular == singular
     sv = np.linalg.svd(sysm.C, compute_uv=False)
     if singular:
@@ -154,10 +179,11 @@ def test_coarse_matrix_singular_only_when_sizes_match(xs, ys, singular):
         assert np.linalg.norm(sysm.apply_S(sysm.B1)) < 1e-10 * np.linalg.norm(sysm.B1)
 
 
-@pytest.mark.parametrize("alg", ["algorithm1", "algorithm2", "algorithm3"])
-def test_graded_algorithms_reach_direct_solution(alg):
+@pytest.mark.parametrize("alg,deflation", [("algorithm1", "weighted"), ("algorithm2", "weighted"),
+                                           ("algorithm3", "weighted"), ("algorithm3", "indicator")])
+def test_graded_algorithms_reach_direct_solution(alg, deflation):
     g = graded(6)
-    sysm = SchurSystem(g)
+    sysm = SchurSystem(g, deflation=deflation)
     x, y = g.coords()
     f, _ = inputs.fourier_rhs(x, y, seed=5)
     gb = g.boundary_g(lambda X, Y, nx, ny: np.cos(X) * nx + np.sin(Y) * ny)
@@ -167,9 +193,29 @@ def test_graded_algorithms_reach_direct_solution(alg):
     assert info["converged"]
     assert np.linalg.norm(u - ud) < 1e-10 * np.linalg.norm(ud)
     if alg == "algorithm3":
-        # deflation with the nonsingular C still projects exactly: the two
-        # terms of Eq. deflated_schur give S x_S = b_S
+        # either coarse space: the two terms of Eq. deflated_schur give
+        # S x_S = b_S (the assembly is exact for any coarse solve used
+        # consistently in P, Q and the coarse term)
         assert info["schur_relres"] < 1e-10
+
+
+def test_weighted_deflation_on_wall_clustered_grid():
+    """12 x 12 elements, n = 6, tanh-clustered toward the walls (sizes spanning
+    a factor of about 10): the weighted coarse space keeps Algorithm 3 well
+    below Algorithm 2; the 0/1 vectors leave B 1 outside it and stall."""
+    xs = inputs.clustered_edges(12, 1.0, 2.0)
+    g = SMPMGrid(12, 12, 6, xs=list(xs), ys=list(xs))
+    x, y = g.coords()
+    f, _ = inputs.fourier_rhs(x, y, seed=1002)
+    b = g.rhs(f)
+    its = {}
+    for defl in ("weighted", "indicator"):
+        sysm = SchurSystem(g, deflation=defl)
+        _, info = methods.algorithm3(sysm, b, tol=1e-10, maxit=300)
+        its[defl] = info["iterations"] if info["converged"] else 10 ** 6
+    _, info2 = methods.algorithm2(sysm, b, tol=1e-10, maxit=300)
+    assert its["weighted"] <= 45 and info2["iterations"] > 2 * its["weighted"], (its, info2["iterations"])
+    assert its["indicator"] > 4 * its["weighted"], its
 
 
 def test_graded_adjoint_matches_direct():
