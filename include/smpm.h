@@ -361,6 +361,42 @@ smpm_status smpm_batch_set_apply_kernel(smpm_batch b, int kind);
 /* Release the batch (not its handles; null is ignored). */
 void smpm_batch_destroy(smpm_batch b);
 
+/* Element-tile domain decomposition for running one grid on several devices
+ * (Sec. 2's block structure is local to elements and their neighbours; the
+ * method shards by tiles of elements).  Host only, no device work.  The
+ * mx x my elements are split into px x py contiguous tiles; rank
+ * ty * px + tx owns element columns [ix0, ix1) and rows [iy0, iy1), with
+ * ix0 = tx mx / px (integer division), so tile sizes differ by at most one,
+ * and the interface slots of its own elements.  Per step of Algorithm 3 a
+ * rank exchanges with each peer across a cut: the Schur apply's pushed
+ * products (push form: T_e v_e destined for the peer's slots), the
+ * block-Jacobi block inputs and outputs of black elements on the cut, and
+ * the partial interface sums of Z^T v (an all-reduce of d values, after
+ * which the coarse solve is replicated); the Gram-Schmidt dot products are
+ * all-reduced. */
+typedef struct {
+  int px, py, rank;
+  int ix0, ix1, iy0, iy1;  /* owned element columns [ix0, ix1) and rows [iy0, iy1) */
+  long long nel_owned;
+  int npeers;              /* ranks sharing a cut with this tile (<= 4) */
+  int peers[4];            /* peer across the tile's W, E, S, N side, -1 if none */
+  long long halo[4];       /* slots on that cut (n per cut interface), 0 if none */
+} smpm_tile;
+
+/* Tile of rank in the px x py decomposition of h's grid.  Errors: EINVAL
+ * (px > mx, py > my, rank out of range, null argument). */
+smpm_status smpm_partition_tile(smpm_handle h, int px, int py, int rank, smpm_tile* t);
+
+/* Halo of rank across side (0 W, 1 E, 2 S, 3 N): own[k] is rank's padded
+ * slot (e, side, s) on the cut face of its boundary element e, facing[k] the
+ * peer's slot (nbr(e, side), opposite side, s) across it; k runs along the cut
+ * (element row or column ascending, then s), so rank's facing list towards a
+ * peer equals the peer's own list towards rank.  own, facing: host arrays of
+ * halo[side] entries (either may be null).  Errors: EINVAL (also for a side
+ * without a peer). */
+smpm_status smpm_partition_halo(smpm_handle h, int px, int py, int rank, int side, long long* own,
+                                long long* facing);
+
 /* Release every resource of h (null is ignored). */
 void smpm_destroy(smpm_handle h);
 

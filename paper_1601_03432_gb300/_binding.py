@@ -23,7 +23,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "
 
 # every symbol include/smpm.h declares
 EXPORTS = [
-    "smpm_default_opts", "smpm_setup", "smpm_setup_graded", "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
+    "smpm_default_opts", "smpm_setup", "smpm_setup_graded", "smpm_partition_tile", "smpm_partition_halo",
+    "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
     "smpm_coarse_matrix", "smpm_factor_host_only", "smpm_host_factor", "smpm_destroy", "smpm_last_error",
@@ -51,6 +52,18 @@ class SmpmReport(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class SmpmTile(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int), ("py", ctypes.c_int), ("rank", ctypes.c_int),
+                ("ix0", ctypes.c_int), ("ix1", ctypes.c_int), ("iy0", ctypes.c_int), ("iy1", ctypes.c_int),
+                ("nel_owned", ctypes.c_longlong), ("npeers", ctypes.c_int), ("peers", ctypes.c_int * 4),
+                ("halo", ctypes.c_longlong * 4)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["peers"], d["halo"] = list(self.peers), list(self.halo)
+        return d
+
+
 class SmpmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
@@ -73,6 +86,8 @@ def lib():
         L.smpm_default_opts.restype = None
         L.smpm_setup.argtypes = [I, I, I, D, D, ctypes.POINTER(P)]
         L.smpm_setup_graded.argtypes = [I, I, I, P, P, ctypes.POINTER(P)]
+        L.smpm_partition_tile.argtypes = [P, I, I, I, ctypes.POINTER(SmpmTile)]
+        L.smpm_partition_halo.argtypes = [P, I, I, I, I, P, P]
         L.smpm_sizes.argtypes = [P] + [ctypes.POINTER(LL)] * 5
         L.smpm_node_coords.argtypes = [P, P, P]
         L.smpm_node_mass.argtypes = [P, P]
@@ -225,6 +240,20 @@ class Grid:
     def factor_host_only(self, **opts):
         o = default_opts(**opts)
         check(lib().smpm_factor_host_only(self.h, ctypes.byref(o)))
+
+    def partition_tile(self, px, py, rank):
+        """smpm_partition_tile: the element tile and the cut sides of rank."""
+        t = SmpmTile()
+        check(lib().smpm_partition_tile(self.h, px, py, rank, ctypes.byref(t)))
+        return t.as_dict()
+
+    def partition_halo(self, px, py, rank, side):
+        """smpm_partition_halo: (own, facing) padded slot lists across side."""
+        m = self.partition_tile(px, py, rank)["halo"][side]
+        own = np.empty(m, dtype=np.int64)
+        facing = np.empty(m, dtype=np.int64)
+        check(lib().smpm_partition_halo(self.h, px, py, rank, side, own.ctypes.data, facing.ctypes.data))
+        return own, facing
 
     def host_factor(self, name):
         n = ctypes.c_longlong()

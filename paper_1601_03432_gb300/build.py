@@ -1,6 +1,6 @@
 """Build step of the in-tree CUDA library ``libsmpm.so`` (sm_103a only).
 
-``build()`` compiles the two translation units in parallel with nvcc and links
+``build()`` compiles the translation units in parallel with nvcc and links
 them into ``paper_1601_03432_gb300/libsmpm.so``; a rebuild happens only when a
 source is newer than the library.
 """
@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmpm.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["smpm_solver.cu", "smpm_factor_host.cpp"]
+SOURCES = ["smpm_solver.cu", "smpm_factor_host.cpp", "smpm_partition.cpp"]
 HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp", "-I", os.path.join(ROOT, "include")]

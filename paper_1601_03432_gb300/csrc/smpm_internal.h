@@ -128,6 +128,9 @@ inline int yclass(const Geometry& g, int e) {
   int iy = e / g.mx;
   return g.graded ? iy : ((iy > 0 ? 1 : 0) | (iy < g.my - 1 ? 2 : 0));
 }
+// Element-tile partition (smpm_partition.cpp).
+int partition_tile(const Geometry& g, int px, int py, int rank, smpm_tile* t);
+int partition_halo(const Geometry& g, int px, int py, int rank, int side, long long* own, long long* facing);
 // GLL nodes and weights, differentiation matrix (host).
 void gll(int n, std::vector<double>* x, std::vector<double>* w);
 void diff_matrix(const std::vector<double>& x, std::vector<double>* D);

@@ -2574,6 +2574,25 @@ smpm_status smpm_setup(int mx, int my, int n, double Lx, double Ly, smpm_handle*
   return host_exception();
 }
 
+smpm_status smpm_partition_tile(smpm_handle h, int px, int py, int rank, smpm_tile* t) try {
+  if (!h || !t) return fail(SMPM_EINVAL, "null argument");
+  if (partition_tile(h->g, px, py, rank, t) != SMPM_OK)
+    return fail(SMPM_EINVAL, "tile grid must satisfy 1 <= px <= mx, 1 <= py <= my, 0 <= rank < px py");
+  return SMPM_OK;
+} catch (...) {
+  return host_exception();
+}
+
+smpm_status smpm_partition_halo(smpm_handle h, int px, int py, int rank, int side, long long* own,
+                                long long* facing) try {
+  if (!h) return fail(SMPM_EINVAL, "null handle");
+  if (partition_halo(h->g, px, py, rank, side, own, facing) != SMPM_OK)
+    return fail(SMPM_EINVAL, "no peer across that side, or tile grid out of range");
+  return SMPM_OK;
+} catch (...) {
+  return host_exception();
+}
+
 smpm_status smpm_sizes(smpm_handle h, long long* r, long long* kp, long long* d, long long* k, long long* nblack) try {
   if (!h) return fail(SMPM_EINVAL, "null handle");
   if (r) *r = h->g.r;
