@@ -386,6 +386,13 @@ def run_ours(args):
                         "hbm_frac": round(byts / (us * 1e-6) / 1e9 / hbm_peak, 3),
                         "tflops": round(2.0 * nela * Ma * Ma / (us * 1e-6) / 1e12, 3),
                         "speedup_vs_per_element": round(pt[name.split("_")[0]]["us"] / us, 2)}
+        # the autotuner's choice among the available apply kernels (its own
+        # CUDA-event medians, 512 MiB written between launches)
+        kind_names = {1: "warp", 2: "warp2", 3: "warp4", 4: "stream", 5: "class"}
+        for precision, name in ((0, "fp64"), (1, "fp32")):
+            chosen, ms = ga.autotune_apply(precision=precision, reps=5, flush=True)
+            pt["autotune_" + name] = {"chosen": kind_names[chosen],
+                                      "us": {kind_names[k]: round(1e3 * v, 2) for k, v in ms.items()}}
         curve.append(pt)
         ga.close()
     schur_apply = {"workload": "y = S v on one grid, operator-only factor step, L2 flushed before each launch "
@@ -402,6 +409,7 @@ def run_ours(args):
     batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and world == 1 else None
     config3 = run_config3(args, stream) if world == 1 else None
     config5 = run_config5(stream) if world == 1 else None
+    graded = run_graded(stream) if world == 1 else None
     sweeps = run_sweeps() if world == 1 else None
 
     traffic, traffic_src = kernel_traffic()
@@ -431,6 +439,7 @@ def run_ours(args):
             "batch": batch,
             "config3": config3,
             "config5": config5,
+            "graded": graded,
             "paper_sweeps": sweeps,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * g.r,
@@ -551,6 +560,40 @@ def run_config5(stream):
                      "gmres_us_per_step": round(1e3 * rep["gmres_ms"] / max(rep["iterations"], 1), 1),
                      "converged": rep["converged"]}
     out["coarse_bytes_per_step"] = 8 * g.d * g.d
+    g.close()
+    return out
+
+
+def run_graded(stream):
+    """32x32 elements, n = 16, both directions tanh-clustered toward the walls
+    (element sizes spanning a factor of about 11), FP64, tol 1e-10, Fourier f:
+    Algorithm 3 (deflation vectors weighted by B 1) and Algorithm 2, each timed
+    with CUDA events (median of 5)."""
+    import numpy as np
+    import torch
+    from paper_1601_03432_gb300 import Grid, inputs
+    xs = inputs.clustered_edges(32, 1.0, 2.0)
+    g = Grid(32, 32, 16, xs=xs, ys=xs)
+    x, y = g.node_coords()
+    f = torch.as_tensor(inputs.fourier_rhs(x, y, seed=7)[0], dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    h = np.diff(xs)
+    out = {"workload": "32x32 elements, n=16, tanh-clustered edges (stretch 2, size ratio %.1f), FP64, tol 1e-10, "
+                       "Fourier f (seed 7)" % (h.max() / h.min())}
+    for precond, name in ((2, "algorithm3"), (1, "algorithm2")):
+        g.factor(tol=1e-10, precond=precond)
+        rep = g.solve(f, u)[0]
+        ts = []
+        for _ in range(5):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            rep = g.solve(f, u)[0]
+            b_.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a_.elapsed_time(b_))
+        ms = sorted(ts)[len(ts) // 2]
+        out[name] = {"solves_per_s": 1e3 / ms, "ms": round(ms, 3), "iterations": rep["iterations"],
+                     "converged": rep["converged"], "schur_relres": rep["schur_relres"]}
     g.close()
     return out
 

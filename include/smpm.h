@@ -233,6 +233,32 @@ smpm_status smpm_apply_deflation_q(smpm_handle h, const double* v, double* y, vo
 smpm_status smpm_apply_schur_class(smpm_handle h, const double* v, double* y, void* stream);
 smpm_status smpm_apply_schur_class32(smpm_handle h, const float* v, float* y, void* stream);
 
+/* Kernels of y = S v (smpm_apply_schur, smpm_apply_schur32 and the S apply
+ * inside the deflation entry points): AUTO picks by thresholds (one warp per
+ * element for 4n <= 96, 1, 2 or 4 elements per warp by the element count, else
+ * the shared-memory stream); WARP: persistent CTAs, one warp per element,
+ * T_e read column by column from global memory; WARP2 / WARP4: 2 or 4 warps
+ * per element; STREAM: bulk copies of T_e into a shared-memory ring; CLASS:
+ * the element-class-shared product (smpm_apply_schur_class). */
+enum { SMPM_APPLY_AUTO = 0, SMPM_APPLY_WARP = 1, SMPM_APPLY_WARP2 = 2, SMPM_APPLY_WARP4 = 3,
+       SMPM_APPLY_STREAM = 4, SMPM_APPLY_CLASS = 5 };
+
+/* Fix the apply kernel of h.  Errors: ESTATE (not factored), EINVAL (kind
+ * not available on this grid: WARP* need 4n <= 96, CLASS its tile in shared
+ * memory). */
+smpm_status smpm_set_apply_kernel(smpm_handle h, int kind);
+
+/* Time every available apply kernel on h's grid in precision 0 (FP64) or 1
+ * (FP32, needs precision-1 factors): reps timed launches each after one
+ * warm-up (median of the CUDA-event times; reps < 1 means 5), with a 512 MiB
+ * write between launches when flush != 0 so that T_e comes from HBM.  The
+ * fastest becomes h's apply kernel.  ms_out (host, 5 entries, may be null):
+ * the median per kind WARP..CLASS, -1 where not available; chosen (may be
+ * null): the kind kept.  Scratch vectors are allocated and freed inside;
+ * synchronises the stream.  Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+smpm_status smpm_autotune_apply(smpm_handle h, int precision, int reps, int flush, double* ms_out, int* chosen,
+                                void* stream);
+
 /* b_S = B A^-1 b (right-hand side of Eq. schur_complement_system); b: r, bS: kp. */
 smpm_status smpm_schur_rhs(smpm_handle h, const double* b, double* bS, void* stream);
 /* u = A^-1 (b - E x) (back-substitution of Sec. 1.3); b: r, x: kp, u: r. */

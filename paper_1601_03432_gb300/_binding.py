@@ -24,6 +24,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOINTERFACE", "ENOMEM", "ECUDA", "ENOTCONV", "
 # every symbol include/smpm.h declares
 EXPORTS = [
     "smpm_default_opts", "smpm_setup", "smpm_setup_graded", "smpm_partition_tile", "smpm_partition_halo",
+    "smpm_set_apply_kernel", "smpm_autotune_apply",
     "smpm_sizes", "smpm_node_coords", "smpm_node_mass", "schur_factor",
     "schur_solve", "schur_solve_host", "smpm_apply_schur", "smpm_apply_precond", "smpm_apply_schur_precond",
     "smpm_apply_deflation", "smpm_apply_deflation_q", "smpm_schur_rhs", "smpm_recover", "smpm_null_vectors",
@@ -50,6 +51,9 @@ class SmpmReport(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+APPLY_AUTO, APPLY_WARP, APPLY_WARP2, APPLY_WARP4, APPLY_STREAM, APPLY_CLASS = range(6)
 
 
 class SmpmTile(ctypes.Structure):
@@ -88,6 +92,8 @@ def lib():
         L.smpm_setup_graded.argtypes = [I, I, I, P, P, ctypes.POINTER(P)]
         L.smpm_partition_tile.argtypes = [P, I, I, I, ctypes.POINTER(SmpmTile)]
         L.smpm_partition_halo.argtypes = [P, I, I, I, I, P, P]
+        L.smpm_set_apply_kernel.argtypes = [P, I]
+        L.smpm_autotune_apply.argtypes = [P, I, I, I, P, P, P]
         L.smpm_sizes.argtypes = [P] + [ctypes.POINTER(LL)] * 5
         L.smpm_node_coords.argtypes = [P, P, P]
         L.smpm_node_mass.argtypes = [P, P]
@@ -240,6 +246,19 @@ class Grid:
     def factor_host_only(self, **opts):
         o = default_opts(**opts)
         check(lib().smpm_factor_host_only(self.h, ctypes.byref(o)))
+
+    def set_apply_kernel(self, kind):
+        """smpm_set_apply_kernel: one of APPLY_AUTO .. APPLY_CLASS."""
+        check(lib().smpm_set_apply_kernel(self.h, int(kind)))
+
+    def autotune_apply(self, precision=0, reps=5, flush=True, stream=None):
+        """smpm_autotune_apply: times every available apply kernel, keeps the
+        fastest; returns (chosen kind, {kind: median ms})."""
+        ms = np.empty(5)
+        ch = ctypes.c_int()
+        check(lib().smpm_autotune_apply(self.h, int(precision), int(reps), 1 if flush else 0, ms.ctypes.data,
+                                        ctypes.byref(ch), _stream(stream)))
+        return ch.value, {k + 1: float(ms[k]) for k in range(5) if ms[k] >= 0}
 
     def partition_tile(self, px, py, rank):
         """smpm_partition_tile: the element tile and the cut sides of rank."""

@@ -556,7 +556,8 @@ __device__ __forceinline__ double deflate_slot_cg(const DevGeo& g, const S* y, c
   if (e2 < 0) return 0.0;
   double ys = (double)ldcg(y + sl);
   if (!chat) return ys;
-  double acc = dev_zw(g, e, F) * __ldcg(chat + dev_iface(g, e, F));
+  double acc = __ldcg(chat + dev_iface(g, e, F));
+  if (g.zw) acc *= dev_zw(g, e, F);  // uniform grids: weight 1, no FP64 multiply
   const S* R = Rs + ((size_t)e2 * M + (F ^ 1) * n + t) * 4;
 #pragma unroll
   for (int G = 0; G < 4; ++G) {

@@ -1012,6 +1012,7 @@ struct smpm_handle_s {
   bool op_factored = false;  // operator-only factor step (SMPM_FLAG_OPERATOR_ONLY): S can be applied
   // element classes (face-type masks) for the class-shared apply
   int ncls = 0, ntiles = 0, cls_ok = 0;  // cls_ok: the kernel's shared-memory limit is set
+  int apply_kind = 0;                     // kernel of smpm_apply_schur(32): SMPM_APPLY_*
   double* dTcls = nullptr;   // ncls * M*M, column-major
   float* dTcls32 = nullptr;
   int* dtiles = nullptr;     // ntiles * (class, first, count) into dclsel
@@ -1235,16 +1236,54 @@ smpm_status launch_schur_stream(smpm_handle h, const S* T, const S* v, S* y, cud
   return SMPM_OK;
 }
 
-smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
-  if (h->g.M <= 96 && h->dtab64) {  // register-streamed from global memory
-    int dev = 0, sms = 0;
-    CU(cudaGetDevice(&dev));
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CU(launch_schur_warp<double>(h->dtab64, h->g.nel, v, y, sms, st));
-    ++h->launches;
-    return SMPM_OK;
+template <typename S>
+smpm_status launch_schur_class(smpm_handle h, const S* T, const S* v, S* y, cudaStream_t st);
+
+// Whether apply kernel kind (SMPM_APPLY_*) can run on h's grid.
+bool apply_kind_ok(smpm_handle h, int kind, bool fp32) {
+  switch (kind) {
+    case SMPM_APPLY_AUTO: case SMPM_APPLY_STREAM: return true;
+    case SMPM_APPLY_WARP: case SMPM_APPLY_WARP2: case SMPM_APPLY_WARP4:
+      return h->g.M <= 96 && (fp32 ? h->dtab32 != nullptr : h->dtab64 != nullptr);
+    case SMPM_APPLY_CLASS: return h->cls_ok && (fp32 ? h->dTcls32 != nullptr : h->dTcls != nullptr);
+    default: return false;
   }
-  return launch_schur_stream<double>(h, h->dT, v, y, st);
+}
+
+// y = S v with the handle's apply kernel (SMPM_APPLY_AUTO: one warp per
+// element, register-streamed from global memory, for M <= 96 -- 1, 2 or 4
+// elements per warp by the element count -- else the shared-memory stream).
+template <typename S>
+smpm_status launch_schur_kind(smpm_handle h, int kind, const S* v, S* y, cudaStream_t st) {
+  const bool fp32 = sizeof(S) == 4;
+  const ElemMeta<S>* tab = reinterpret_cast<const ElemMeta<S>*>(fp32 ? (const void*)h->dtab32 : (const void*)h->dtab64);
+  const S* T = reinterpret_cast<const S*>(fp32 ? (const void*)h->dT32 : (const void*)h->dT);
+  if (kind == SMPM_APPLY_AUTO) kind = apply_kind_ok(h, SMPM_APPLY_WARP, fp32) ? -1 : SMPM_APPLY_STREAM;
+  if (kind == SMPM_APPLY_STREAM) return launch_schur_stream<S>(h, T, v, y, st);
+  if (kind == SMPM_APPLY_CLASS) {
+    const S* Tc = reinterpret_cast<const S*>(fp32 ? (const void*)h->dTcls32 : (const void*)h->dTcls);
+    return launch_schur_class<S>(h, Tc, v, y, st);
+  }
+  int dev = 0, sms = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long ne = h->g.nel;
+  if (kind == -1) {
+    CU(launch_schur_warp<S>(tab, ne, v, y, sms, st));
+  } else if (kind == SMPM_APPLY_WARP) {
+    k_schur_warp_batch<S><<<(unsigned)sms * 8, 256, 0, st>>>(tab, ne, v, y);
+  } else if (kind == SMPM_APPLY_WARP2) {
+    k_schur_warpk<S, 2><<<(unsigned)((ne + 3) / 4), 256, 0, st>>>(tab, ne, v, y);
+  } else {
+    k_schur_warpk<S, 4><<<(unsigned)((ne + 1) / 2), 256, 0, st>>>(tab, ne, v, y);
+  }
+  CU(cudaGetLastError());
+  ++h->launches;
+  return SMPM_OK;
+}
+
+smpm_status launch_schur(smpm_handle h, const double* v, double* y, cudaStream_t st) {
+  return launch_schur_kind<double>(h, h->apply_kind, v, y, st);
 }
 
 // t = M^-1 v (t fully written), then optionally y = S t and c = Z^T y.
@@ -3126,15 +3165,77 @@ smpm_status smpm_apply_schur32(smpm_handle h, const float* v, float* y, void* st
   NEED_OPERATOR();
   if (!v || !y) return fail(SMPM_EINVAL, "null vector");
   if (!h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
-  if (h->g.M <= 96 && h->dtab32) {
-    int dev = 0, sms = 0;
-    CU(cudaGetDevice(&dev));
-    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CU(launch_schur_warp<float>(h->dtab32, h->g.nel, v, y, sms, as_stream(stream)));
-    ++h->launches;
-    return SMPM_OK;
+  const int kind = apply_kind_ok(h, h->apply_kind, true) ? h->apply_kind : SMPM_APPLY_AUTO;
+  return launch_schur_kind<float>(h, kind, v, y, as_stream(stream));
+} catch (...) {
+  return host_exception();
+}
+
+smpm_status smpm_set_apply_kernel(smpm_handle h, int kind) try {
+  NEED_OPERATOR();
+  if (!apply_kind_ok(h, kind, false)) return fail(SMPM_EINVAL, "apply kernel not available on this grid");
+  h->apply_kind = kind;
+  return SMPM_OK;
+} catch (...) {
+  return host_exception();
+}
+
+smpm_status smpm_autotune_apply(smpm_handle h, int precision, int reps, int flush, double* ms_out, int* chosen,
+                                void* stream) try {
+  NEED_OPERATOR();
+  if (precision != 0 && precision != 1) return fail(SMPM_EINVAL, "precision must be 0 or 1");
+  if (precision == 1 && !h->dT32) return fail(SMPM_ESTATE, "FP32 factors exist only after schur_factor with precision = 1");
+  if (reps < 1) reps = 5;
+  cudaStream_t st = as_stream(stream);
+  const size_t es = precision ? sizeof(float) : sizeof(double);
+  void *v = nullptr, *y = nullptr, *fl = nullptr;
+  const size_t flush_bytes = flush ? ((size_t)512 << 20) : 0;  // several times L2
+  auto release = [&]() {
+    if (v) cudaFree(v);
+    if (y) cudaFree(y);
+    if (fl) cudaFree(fl);
+  };
+  if (cudaMalloc(&v, h->g.kp * es) != cudaSuccess || cudaMalloc(&y, h->g.kp * es) != cudaSuccess ||
+      (flush_bytes && cudaMalloc(&fl, flush_bytes) != cudaSuccess)) {
+    release();
+    cudaGetLastError();
+    return fail(SMPM_ENOMEM, "device allocation failed in the apply autotuner");
   }
-  return launch_schur_stream<float>(h, h->dT32, v, y, as_stream(stream));
+  cudaEvent_t a = nullptr, b = nullptr;
+  smpm_status res = SMPM_OK;
+  int best = SMPM_APPLY_AUTO;
+  double best_ms = 1e300;
+  if (cudaMemsetAsync(v, 0, h->g.kp * es, st) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess)
+    res = fail(SMPM_ECUDA, "autotuner setup failed");
+  for (int kind = SMPM_APPLY_WARP; res == SMPM_OK && kind <= SMPM_APPLY_CLASS; ++kind) {
+    if (ms_out) ms_out[kind - 1] = -1.0;
+    if (!apply_kind_ok(h, kind, precision == 1)) continue;
+    std::vector<float> t;
+    for (int r = 0; r <= reps && res == SMPM_OK; ++r) {  // r = 0 warms up
+      if (fl && cudaMemsetAsync(fl, r & 0xff, flush_bytes, st) != cudaSuccess) res = fail(SMPM_ECUDA, "flush failed");
+      if (res != SMPM_OK) break;
+      cudaEventRecord(a, st);
+      res = precision ? launch_schur_kind<float>(h, kind, (const float*)v, (float*)y, st)
+                      : launch_schur_kind<double>(h, kind, (const double*)v, (double*)y, st);
+      cudaEventRecord(b, st);
+      if (res == SMPM_OK && cudaEventSynchronize(b) != cudaSuccess) res = fail(SMPM_ECUDA, "apply kernel failed");
+      float ms = 0;
+      if (res == SMPM_OK && r > 0 && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) t.push_back(ms);
+    }
+    if (res != SMPM_OK || t.empty()) break;
+    std::sort(t.begin(), t.end());
+    const double med = t[t.size() / 2];
+    if (ms_out) ms_out[kind - 1] = med;
+    if (med < best_ms) { best_ms = med; best = kind; }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  release();
+  if (res != SMPM_OK) return res;
+  h->apply_kind = best;
+  if (chosen) *chosen = best;
+  return SMPM_OK;
 } catch (...) {
   return host_exception();
 }
