@@ -118,13 +118,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // of polling; smpm_set_barrier_spin_limit lowers it to exercise the timeout).
 __device__ long long g_barrier_spin_limit = 1LL << 28;
 
-__device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
+// work: run by thread 0 between its arrival and its wait (serial work of this
+// CTA overlapped with the other CTAs' arrival); it must touch only what no
+// other CTA reads before the barrier completes.
+template <typename Work>
+__device__ bool grid_sync_with(unsigned* bar, int* err, unsigned& epoch, int G, Work&& work) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
     epoch += (unsigned)G;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+    work();
     long long spins = 0;
     const long long limit = g_barrier_spin_limit;
     while ((int)(ld_acquire(bar) - epoch) < 0) {
@@ -141,6 +146,10 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned& epoch, int G) {
+  return grid_sync_with(bar, err, epoch, G, [] {});
 }
 
 // slot of entry i (< 2M) of the block of black element e: own slots first,
@@ -887,6 +896,66 @@ __device__ bool apply_op(const GmresArgs<S>& a, const Smem<S>& s, const S* src, 
   return true;
 }
 
+// Givens update of Hessenberg column j (thread 0; every CTA runs it on its
+// own copy): the j earlier rotations applied to s.col, the new rotation from
+// s.col[j] and the subdiagonal entry s.misc[4], the rotated right-hand side
+// gg and its last entry |gg[j+1]| (the residual estimate) in s.misc[2].
+template <typename S>
+__device__ void givens_column(const GmresArgs<S>& a, const Smem<S>& s, int j, int rank) {
+  const double bnext = s.misc[4];
+  // the rotated entry is carried in a register: one dependent FMA per
+  // rotation (the products with the unrotated entries do not depend on the
+  // chain); the operands of eight rotations are loaded into registers ahead
+  // of them, so only the FMA chain is serial
+  double xi = s.col[0];
+  int i0 = 0;
+  for (; i0 + 8 <= j; i0 += 8) {
+    double x1[8], c[8], sn[8], out[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      x1[u] = s.col[i0 + u + 1];
+      c[u] = s.gcs[i0 + u];
+      sn[u] = s.gsn[i0 + u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double cx1 = c[u] * x1[u], sx1 = sn[u] * x1[u];
+      out[u] = fma(c[u], xi, sx1);
+      xi = fma(-sn[u], xi, cx1);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s.col[i0 + u] = out[u];
+  }
+  for (int i = i0; i < j; ++i) {
+    const double x1 = s.col[i + 1], c = s.gcs[i], sn = s.gsn[i];
+    const double cx1 = c * x1, sx1 = sn * x1;
+    s.col[i] = fma(c, xi, sx1);
+    xi = fma(-sn, xi, cx1);
+  }
+  const double hh = xi * xi + bnext * bnext;
+  const double iden = hh > 0 ? rsqrt(hh) : 0.0;
+  const double cc = hh > 0 ? xi * iden : 1.0, ss = bnext * iden;
+  s.gcs[j] = cc;
+  s.gsn[j] = ss;
+  s.col[j] = hh * iden;
+  s.gg[j + 1] = -ss * s.gg[j];
+  s.gg[j] = cc * s.gg[j];
+  s.misc[2] = fabs(s.gg[j + 1]);
+  if (rank == 0) {
+    a.gs->g[j] = s.gg[j];
+    a.gs->g[j + 1] = s.gg[j + 1];
+  }
+}
+
+// column j of the triangular factor (rotated Hessenberg column), for the
+// end-of-cycle solve: all threads of CTA 0, after givens_column
+template <typename S>
+__device__ __forceinline__ void store_rcol(const GmresArgs<S>& a, const Smem<S>& s, int j, int rank) {
+  if (rank != 0) return;
+  double* Rc = a.gs->R + (size_t)j * (kMaxRestart + 1);
+  for (int l = threadIdx.x; l <= j; l += blockDim.x) Rc[l] = s.col[l];
+}
+
 // One GMRES solve by the CTAs of a team (the whole grid for k_gmres).
 // epoch: the team barrier's epoch, carried across consecutive bodies.
 // Returns false when a barrier or copy wait timed out (err set).
@@ -994,7 +1063,7 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
       s.invb[0] = 1.0 / beta;
     }
     __syncthreads();
-    int j = 0;
+    int j = 0, pending = -1;  // pending: the step whose Givens rotation is deferred
     for (; j < m && total < a.maxit; ++j) {
       double* accD = a.acc + (size_t)(2 * j) * m3;
       double* accE = a.acc + (size_t)(2 * j + 1) * m3;
@@ -1037,8 +1106,18 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
       __syncthreads();
       owned_dots(a, s, s.w, j + 2, accD);
       GM_TRACE(5);
-      if (!grid_sync(a.bar, a.err, epoch, a.G)) GM_FAIL();
+      if (!grid_sync_with(a.bar, a.err, epoch, a.G, [&] {
+            if (pending >= 0) givens_column(a, s, pending, rank);
+          }))
+        GM_FAIL();
       GM_TRACE(6);
+      if (pending >= 0) {  // the previous step's rotation and convergence test
+        store_rcol(a, s, pending, rank);
+        resid = s.misc[2];
+        pending = -1;
+        if (!isfinite(resid)) { nan = true; break; }
+        if (resid <= tolabs) { converged = true; break; }  // j columns: this step is dropped
+      }
       for (int l = threadIdx.x; l < j + 2; l += blockDim.x) {
         double v = __ldcg(accD + l);
         if (l <= j) {
@@ -1068,6 +1147,7 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
         }
       }
       __syncthreads();
+      GM_TRACE(10);
       if (threadIdx.x < 32) {  // ||h2||^2 and h1 + h2 in warp 0
         double q = 0;
         for (int l = threadIdx.x; l <= j; l += 32) {
@@ -1078,58 +1158,53 @@ __device__ bool gmres_body(const GmresArgs<S>& a, unsigned char* smraw, unsigned
         if (threadIdx.x == 0) s.misc[5] = q;
       }
       __syncthreads();
-      // ---- Givens update, replicated in every CTA (serial chain in thread 0)
+      GM_TRACE(11);
+      // ---- F: ||w2|| (Pythagorean) and the breakdown test now; the Givens
+      // rotation of column j -- a serial FP64 chain in thread 0, replicated in
+      // every CTA -- runs inside the next step's first grid barrier, while the
+      // other CTAs arrive, and its convergence test is read after it.  A step
+      // that converged thus costs one extra step of work, whose results
+      // (v_{j+1}, t, the dot products) are never used.
       if (threadIdx.x == 0) {
-        double bsq = s.misc[1] - s.misc[5];
-        double ib = bsq > 0 ? rsqrt(bsq) : 0.0;
-        double bnext = bsq > 0 ? bsq * ib : 0.0;
-        // the rotated entry is carried in a register: one dependent FMA per
-        // rotation (the products with the unrotated entries do not depend
-        // on the chain)
-        double xi = s.col[0];
-        for (int i = 0; i < j; ++i) {
-          const double x1 = s.col[i + 1], c = s.gcs[i], sn = s.gsn[i];
-          const double cx1 = c * x1, sx1 = sn * x1;
-          s.col[i] = fma(c, xi, sx1);
-          xi = fma(-sn, xi, cx1);
-        }
-        s.col[j] = xi;
-        double hh = s.col[j] * s.col[j] + bnext * bnext;
-        double iden = hh > 0 ? rsqrt(hh) : 0.0;
-        double cc = hh > 0 ? s.col[j] * iden : 1.0, ss = bnext * iden;
-        s.gcs[j] = cc;
-        s.gsn[j] = ss;
-        s.col[j] = hh * iden;
-        s.gg[j + 1] = -ss * s.gg[j];
-        s.gg[j] = cc * s.gg[j];
+        const double bsq = s.misc[1] - s.misc[5];
+        const double ib = bsq > 0 ? rsqrt(bsq) : 0.0;
         s.invb[j + 1] = ib;
-        s.misc[2] = fabs(s.gg[j + 1]);
         s.misc[3] = (bsq <= 1e-28 * s.misc[0]) ? 1.0 : 0.0;
-        s.misc[4] = bnext;
-        if (rank == 0) {
-          double* Rc = a.gs->R + (size_t)j * (kMaxRestart + 1);
-          for (int l = 0; l <= j; ++l) Rc[l] = s.col[l];
-          a.gs->g[j] = s.gg[j];
-          a.gs->g[j + 1] = s.gg[j + 1];
-        }
+        s.misc[4] = bsq > 0 ? bsq * ib : 0.0;  // the new subdiagonal entry
       }
       __syncthreads();
       GM_TRACE(13);
       ++total;
-      resid = s.misc[2];
-      if (!isfinite(resid) || !isfinite(s.misc[4])) { nan = true; ++j; break; }
-      if (resid <= tolabs) { converged = true; ++j; break; }
-      if (s.misc[3] != 0.0) { breakdown = true; ++j; break; }
+      if (!isfinite(s.misc[4]) || s.misc[3] != 0.0 || j + 1 >= m || total >= a.maxit) {
+        // last step of the cycle: rotate now
+        if (threadIdx.x == 0) givens_column(a, s, j, rank);
+        __syncthreads();
+        store_rcol(a, s, j, rank);
+        resid = s.misc[2];
+        if (!isfinite(resid) || !isfinite(s.misc[4])) { nan = true; ++j; break; }
+        if (resid <= tolabs) { converged = true; ++j; break; }
+        if (s.misc[3] != 0.0) { breakdown = true; ++j; break; }
+        continue;
+      }
+      pending = j;
     }
     jlast = j;
     if (nan) break;
-    // ---- end of cycle: y = R^-1 g (CTA 0), x += V diag(invb) y on owned entries
-    if (rank == 0 && threadIdx.x == 0) {
-      const int m1 = kMaxRestart + 1;
-      for (int i = j - 1; i >= 0; --i) {
-        double sum = a.gs->g[i];
-        for (int k = i + 1; k < j; ++k) sum -= a.gs->R[(size_t)k * m1 + i] * a.gs->y[k];
-        a.gs->y[i] = sum / a.gs->R[(size_t)i * m1 + i];
+    __syncthreads();  // the columns of R written by all threads of CTA 0
+    // ---- end of cycle: y = R^-1 g (warp 0 of CTA 0, column by column: y_k,
+    // then the entries above it lose R_ik y_k in parallel over the lanes),
+    // x += V diag(invb) y on owned entries
+    if (rank == 0 && threadIdx.x < 32) {
+      const int m1 = kMaxRestart + 1, lane = threadIdx.x;
+      for (int l = lane; l < j; l += 32) s.col[l] = a.gs->g[l];
+      __syncwarp();
+      for (int k = j - 1; k >= 0; --k) {
+        const double* Rk = a.gs->R + (size_t)k * m1;
+        const double yk = s.col[k] / Rk[k];
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) s.col[i] = fma(-Rk[i], yk, s.col[i]);
+        if (lane == 0) a.gs->y[k] = yk;
+        __syncwarp();
       }
     }
     // the accumulators are consumed: zero them for the next cycle
