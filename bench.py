@@ -69,6 +69,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch", type=int, default=512,
                    help="grids of the uneven batch section (0 skips it; 512 is the full seeded batch)")
+    p.add_argument("--headline-only", action="store_true",
+                   help="only the headline, mixed-precision and end-to-end solves (for an ncu launch list)")
     p.add_argument("--profile", choices=["gmres", "apply", "apply96", "bapply", "batch"], default=None,
                    help="run only a small fixed case for an ncu capture and exit (prints no bench line)")
     return p.parse_args()
@@ -335,7 +337,7 @@ def run_ours(args):
     # pass, so that no dirty line is written back inside the launch)
     from paper_1601_03432_gb300 import _binding as _B
     curve = []
-    for (amx, amy, an) in ((32, 32, 24), (64, 64, 24), (96, 96, 24), (128, 128, 16)):
+    for (amx, amy, an) in (() if args.headline_only else ((32, 32, 24), (64, 64, 24), (96, 96, 24), (128, 128, 16))):
         ga = Grid(amx, amy, an)
         ga.factor(precision=1, flags=_B.FLAG_OPERATOR_ONLY)
         Ma, nela = 4 * an, amx * amy
@@ -406,11 +408,12 @@ def run_ours(args):
     # the batch and precision-config sections run on single-GPU runs only: a
     # multi-GPU run measures the replicated headline solve and holds every GPU
     # for as short a time as that takes
-    batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and world == 1 else None
-    config3 = run_config3(args, stream) if world == 1 else None
-    config5 = run_config5(stream) if world == 1 else None
-    graded = run_graded(stream) if world == 1 else None
-    sweeps = run_sweeps() if world == 1 else None
+    full = world == 1 and not args.headline_only
+    batch = run_batch(args, stream, hbm_peak) if args.batch > 0 and full else None
+    config3 = run_config3(args, stream) if full else None
+    config5 = run_config5(stream) if full else None
+    graded = run_graded(stream) if full else None
+    sweeps = run_sweeps() if full else None
 
     traffic, traffic_src = kernel_traffic()
     cpu = None
