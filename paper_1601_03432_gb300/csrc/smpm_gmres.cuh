@@ -45,7 +45,9 @@ struct GmresArgs {
   const S* Gc;      // nblack * M*M, column-major G_b
   const S* Xc;      // nblack * 4*n*n, column-major X_F blocks
   const S* Rs;      // nel * M*4 row sums of T_e (deflation)
-  const double* H;  // d*d row-major coarse inverse
+  // d*d row-major coarse inverse: FP64, or its FP32 copy for the FP32 inner
+  // solves of the mixed-precision path
+  const typename std::conditional<sizeof(S) == 4, float, double>::type* H;
   S* vglob;         // kp : current basis vector (raw), exchanged between CTAs
   S* vown;          // G * (m+1) * ES : basis slices when not resident in smem
   S* t;             // kp
@@ -500,12 +502,68 @@ __device__ __forceinline__ double2 ld_h2(const double* p, bool stream) {
 }
 __device__ __forceinline__ double ld_h1(const double* p, bool stream) { return stream ? __ldcs(p) : __ldg(p); }
 
+// The FP32 inner solves of the mixed-precision path apply the coarse
+// inverse in FP32 (its FP32 copy, FP32 products and sums): an inner solve
+// needs only a relative 1e-4, and every refinement sweep recomputes the
+// residual in FP64.
+__device__ void coarse_rows32(const float* __restrict__ H32, const double* c, double* chat, int d, int r0, int r1,
+                              float* cf) {
+  for (int j = threadIdx.x; j < d; j += blockDim.x) cf[j] = (float)__ldcg(c + j);
+  __syncthreads();
+  const int rows = r1 - r0;
+  int P = 32;
+  while (P > 1 && P * rows > 2 * (int)blockDim.x) P >>= 1;
+  const int lane = threadIdx.x % P, grp = threadIdx.x / P, ngrp = blockDim.x / P;
+  const bool vec = (d & 3) == 0;  // rows start 16-byte aligned
+  for (int rb = 0; rb < rows; rb += ngrp) {
+    const int r = r0 + rb + grp;
+    float sum = 0.f;
+    if (r < r1) {
+      const float* hr = H32 + (size_t)r * d;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      int j = vec ? 4 * lane : lane;
+      if (vec) {
+        for (; j + 28 * P < d; j += 32 * P) {
+          float4 h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = __ldg(reinterpret_cast<const float4*>(hr + j + 4 * u * P));
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jj = j + 4 * u * P;
+            acc[u & 3] += h[u].x * cf[jj] + h[u].y * cf[jj + 1] + h[u].z * cf[jj + 2] + h[u].w * cf[jj + 3];
+          }
+        }
+        for (; j < d; j += 4 * P) {
+          const float4 h = __ldg(reinterpret_cast<const float4*>(hr + j));
+          acc[0] += h.x * cf[j] + h.y * cf[j + 1] + h.z * cf[j + 2] + h.w * cf[j + 3];
+        }
+      } else {
+        for (; j + 7 * P < d; j += 8 * P) {
+          float h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = __ldg(hr + j + u * P);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc[u & 3] += h[u] * cf[j + u * P];
+        }
+        for (; j < d; j += P) acc[0] += __ldg(hr + j) * cf[j];
+      }
+      sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+    for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
+    if (lane == 0 && r < r1) chat[r] = (double)sum;
+  }
+}
+
 template <typename S>
 __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
   const int d = (int)a.g.d;
   const int per = (d + a.G - 1) / a.G;
   const int r0 = team_rank(a) * per, r1 = min(d, r0 + per);
   if (r0 >= r1) return;
+  if constexpr (sizeof(S) == 4) {
+    coarse_rows32(a.H, a.c, a.chat, d, r0, r1, reinterpret_cast<float*>(s.cst));
+    return;
+  } else {
   for (int j = threadIdx.x; j < d; j += blockDim.x) s.cst[j] = __ldcg(a.c + j);
   __syncthreads();
   const bool stream = (size_t)d * d * sizeof(double) > ((size_t)48 << 20);
@@ -523,12 +581,12 @@ __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
       double acc[4] = {0, 0, 0, 0};
       if (vec) {
         int j = 2 * lane;
-        for (; j + 14 * P < d; j += 16 * P) {
-          double2 h[8];
+        for (; j + 30 * P < d; j += 32 * P) {
+          double2 h[16];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) h[u] = ld_h2(hr + j + 2 * u * P, stream);
+          for (int u = 0; u < 16; ++u) h[u] = ld_h2(hr + j + 2 * u * P, stream);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < 16; ++u) {
             const int jj = j + 2 * u * P;
             acc[u & 3] += h[u].x * cs[jj] + h[u].y * cs[jj + 1];
           }
@@ -552,6 +610,7 @@ __device__ void coarse_rows(const GmresArgs<S>& a, const Smem<S>& s) {
     }
     for (int o = P / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, P);
     if (lane == 0 && r < r1) a.chat[r] = sum;
+  }
   }
 }
 
@@ -664,40 +723,53 @@ __device__ __forceinline__ long long entry_slot(const GmresArgs<S>& a, int i) {
 
 // ---- warp-per-element phases -------------------------------------------
 // z[r] = sum_c A[c*M + r] x[c] for r < M by one warp: lane l owns rows
-// l, l+32, l+64, l+96 (M <= 128); A column-major in shared or global memory
-// (read-only), eight columns per step (four in FP64, whose registers and
-// pipe bind first) with all their loads issued first (up to 32 independent
-// loads per lane in flight: from global memory each step is one round trip);
-// x and z in the warp's shared scratch.  Ends with __syncwarp.
-template <typename S>
-__device__ __forceinline__ void warp_gemv(const S* A, const S* x, S* z, int M, int lane) {
-  constexpr int U = sizeof(S) == 4 ? 8 : 4;  // FP64: fewer registers, and its pipe, not latency, bounds it sooner
-  S acc[4] = {S(0), S(0), S(0), S(0)};
-  const int nr = (M - lane + 31) / 32;  // rows of this lane (0..4)
+// l, l+32, ... (up to NR of them, M <= 32 NR); A column-major in shared or
+// global memory (read-only), U columns per step with all their loads issued
+// first (U NR independent loads per lane in flight: from global memory each
+// step is one round trip); x and z in the warp's shared scratch.  Ends with
+// __syncwarp.
+template <typename S, int U, int NR>
+__device__ __forceinline__ void warp_gemv_u(const S* A, const S* x, S* z, int M, int lane) {
+  S acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = S(0);
+  const int nr = (M - lane + 31) / 32;  // rows of this lane (0..NR)
   int c = 0;
   for (; c + U <= M; c += U) {
-    S av[U][4];
+    S av[U][NR];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) av[u][j] = j < nr ? A[(size_t)(c + u) * M + lane + 32 * j] : S(0);
+      for (int j = 0; j < NR; ++j) av[u][j] = j < nr ? A[(size_t)(c + u) * M + lane + 32 * j] : S(0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const S xc = x[c + u];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] += av[u][j] * xc;
+      for (int j = 0; j < NR; ++j) acc[j] += av[u][j] * xc;
     }
   }
   for (; c < M; ++c) {
     const S xc = x[c];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < NR; ++j)
       if (j < nr) acc[j] += A[(size_t)c * M + lane + 32 * j] * xc;
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < NR; ++j)
     if (j < nr) z[lane + 32 * j] = acc[j];
   __syncwarp();
+}
+
+template <typename S>
+__device__ __forceinline__ void warp_gemv(const S* A, const S* x, S* z, int M, int lane) {
+  // lane owns rows lane + 32 j; U columns of loads are issued before their
+  // FMAs, so a warp keeps U * NR loads in flight (M <= 64: 16 columns x 2
+  // rows, else 8 x 4): matrices streamed from HBM need the bytes in flight
+  // more than the FP64 pipe needs short chains
+  if (M <= 64)
+    warp_gemv_u<S, 16, 2>(A, x, z, M, lane);
+  else
+    warp_gemv_u<S, 8, 4>(A, x, z, M, lane);
 }
 
 // Black block solves with one warp per owned block (blocks k = warp,

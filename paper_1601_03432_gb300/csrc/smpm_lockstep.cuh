@@ -303,8 +303,8 @@ __device__ void lk_white(const LockArgs<S>& A, const LockSmem<S>& s, const S* v,
 // and of each column's c, two entries per lane and step, and the loads of the
 // next step are issued before the FMAs of this one (software pipelining); the
 // R partial sums meet in warp shuffles.
-template <typename S>
-__device__ void lk_coarse(const LockArgs<S>& A) {
+template <typename S, typename HT>
+__device__ void lk_coarse_h(const LockArgs<S>& A, const HT* H) {
   const GmresArgs<S>& a = A.a;
   const int d = (int)a.g.d, R = A.R;
   const int per = (d + a.G - 1) / a.G;
@@ -313,14 +313,14 @@ __device__ void lk_coarse(const LockArgs<S>& A) {
   constexpr int U = 2, CG = 8;  // entries per lane and step; columns per pass over the row
   const int nfull = d / (32 * U);
   for (int r = r0 + warp; r < r1; r += nwarps) {
-    const double* hr = a.H + (size_t)r * d;
+    const HT* hr = H + (size_t)r * d;
     for (int c0 = 0; c0 < R; c0 += CG) {
       const int nc = min(CG, R - c0);
       const double* cb = a.c + (size_t)c0 * A.ds;
-      double acc[CG];
+      HT acc[CG];
 #pragma unroll
       for (int c = 0; c < CG; ++c) acc[c] = 0;
-      double h[U], cv[CG][U];
+      HT h[U], cv[CG][U];
       auto load = [&](int st) {
         const int j = st * 32 * U + lane;
 #pragma unroll
@@ -329,11 +329,11 @@ __device__ void lk_coarse(const LockArgs<S>& A) {
         for (int c = 0; c < CG; ++c)
           if (c < nc)
 #pragma unroll
-            for (int u = 0; u < U; ++u) cv[c][u] = __ldcg(cb + c * A.ds + j + 32 * u);
+            for (int u = 0; u < U; ++u) cv[c][u] = (HT)__ldcg(cb + c * A.ds + j + 32 * u);
       };
       if (nfull > 0) load(0);
       for (int st = 0; st < nfull; ++st) {
-        double hh[U], cc[CG][U];
+        HT hh[U], cc[CG][U];
 #pragma unroll
         for (int u = 0; u < U; ++u) hh[u] = h[u];
 #pragma unroll
@@ -348,20 +348,26 @@ __device__ void lk_coarse(const LockArgs<S>& A) {
             for (int u = 0; u < U; ++u) acc[c] += hh[u] * cc[c][u];
       }
       for (int j = nfull * 32 * U + lane; j < d; j += 32) {
-        const double hv = __ldg(hr + j);
+        const HT hv = __ldg(hr + j);
 #pragma unroll
         for (int c = 0; c < CG; ++c)
-          if (c < nc) acc[c] += hv * __ldcg(cb + c * A.ds + j);
+          if (c < nc) acc[c] += hv * (HT)__ldcg(cb + c * A.ds + j);
       }
 #pragma unroll
       for (int c = 0; c < CG; ++c) {
         if (c < nc) {
-          const double v = warp_sum(acc[c]);
+          const double v = (double)warp_sum(acc[c]);
           if (lane == 0) a.chat[(c0 + c) * A.ds + r] = v;
         }
       }
     }
   }
+}
+
+// FP32 inner solves apply the coarse inverse's FP32 copy (see coarse_rows32)
+template <typename S>
+__device__ void lk_coarse(const LockArgs<S>& A) {
+  lk_coarse_h(A, A.a.H);
 }
 
 // op(sc * src) -> y (and c, chat) for all columns; with own_j >= 0 the block

@@ -41,8 +41,8 @@
 #include <exception>
 #include <mutex>
 #include <new>
-#include <string>
 #include <type_traits>
+#include <string>
 #include <vector>
 
 #include "smpm_internal.h"
@@ -1046,6 +1046,7 @@ struct smpm_handle_s {
   double* wacc = nullptr;
   // mixed precision: FP32 operator copies and work vectors, FP64 residual
   float *dT32 = nullptr, *dG32 = nullptr, *dX32 = nullptr, *dRs32 = nullptr;
+  float* dH32 = nullptr;  // FP32 copy of the coarse inverse, for the FP32 inner solves
   float *wx32 = nullptr, *wt32 = nullptr, *wy32 = nullptr, *wV32 = nullptr, *wrg32 = nullptr, *wvown32 = nullptr;
   double *wr = nullptr, *wcr = nullptr, *wrn = nullptr;
   int *wdone = nullptr, *wnref = nullptr;
@@ -1432,7 +1433,7 @@ GmresArgs<float> gmres_args32(smpm_handle h, double tol) {
   a.white = h->dwhite;
   a.nblack = (int)h->f.black.size();
   a.nwhite = (int)h->f.white.size();
-  a.Tc = h->dT32; a.Gc = h->dG32; a.Xc = h->dX32; a.Rs = h->dRs32; a.H = h->dH;
+  a.Tc = h->dT32; a.Gc = h->dG32; a.Xc = h->dX32; a.Rs = h->dRs32; a.H = h->dH32;
   a.vglob = h->wV32; a.vown = h->wvown32; a.t = h->wt32; a.y = h->wy32;
   a.c = h->wc; a.chat = h->wchat; a.rhs = h->wrg32; a.x = h->wx32;
   a.acc = h->wacc; a.gs = h->wgs; a.bar = h->wbar; a.err = h->werr;
@@ -2965,7 +2966,8 @@ smpm_status factor_device(smpm_handle h, cudaStream_t st) {
       if (per_sm < 1) return fail(SMPM_ECUDA, "the refinement kernel does not fit on an SM");
       auto to32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
       if ((s = upload(h, &h->dT32, to32(Tc), st)) || (s = upload(h, &h->dG32, to32(Gc), st)) ||
-          (s = upload(h, &h->dX32, to32(Xc), st)) || (s = upload(h, &h->dRs32, to32(h->f.Rs), st)))
+          (s = upload(h, &h->dX32, to32(Xc), st)) || (s = upload(h, &h->dRs32, to32(h->f.Rs), st)) ||
+          (s = upload(h, &h->dH32, to32(h->f.H), st)))
         return s;
       if ((s = dalloc(h, &h->wx32, g.kp)) || (s = dalloc(h, &h->wt32, g.kp)) || (s = dalloc(h, &h->wy32, g.kp)) ||
           (s = dalloc(h, &h->wV32, g.kp)) || (s = dalloc(h, &h->wrg32, g.kp)) || (s = dalloc(h, &h->wr, g.kp)) ||
