@@ -403,3 +403,32 @@ def test_factors_are_identical_within_a_class(mx, my, n):
         r = firstb.setdefault(key, ib)
         assert np.array_equal(Gb[ib], Gb[r]) and np.array_equal(Xb[ib], Xb[r])
     assert len(first) <= 9
+
+
+def test_graded_setup_rejects_bad_edges():
+    """smpm_setup_graded: edges must be finite and strictly increasing, one
+    more than the element count in each direction."""
+    with pytest.raises(B.SmpmError) as ei:
+        B.Grid(3, 2, 4, xs=[0.0, 0.5, 0.5, 1.0], ys=[0.0, 0.3, 1.0])
+    assert ei.value.status == B.SMPM_EINVAL
+    with pytest.raises(B.SmpmError):
+        B.Grid(3, 2, 4, xs=[0.0, 0.5, np.nan, 1.0], ys=[0.0, 0.3, 1.0])
+    with pytest.raises(B.SmpmError):
+        B.Grid(3, 2, 4, xs=[0.0, 0.5, 0.7, 1.0], ys=[0.0, 1.0, 0.3])
+    with pytest.raises(ValueError):
+        B.Grid(3, 2, 4, xs=[0.0, 0.5, 1.0], ys=[0.0, 0.3, 1.0])
+    g = B.Grid(3, 2, 4, xs=[-1.0, 0.5, 0.7, 1.0], ys=[2.0, 2.3, 3.0])
+    x, y = g.node_coords()
+    assert x.min() == -1.0 and x.max() == 1.0 and y.min() == 2.0 and y.max() == 3.0
+    assert abs(g.node_mass().sum() - 2.0 * 1.0) < 1e-13
+
+
+def test_partition_rejects_bad_tiles():
+    g = B.Grid(4, 3, 4)
+    for px, py, rank in ((0, 1, 0), (5, 1, 0), (2, 4, 0), (2, 2, 4), (2, 2, -1)):
+        with pytest.raises(B.SmpmError) as ei:
+            g.partition_tile(px, py, rank)
+        assert ei.value.status == B.SMPM_EINVAL
+    t = g.partition_tile(2, 3, 5)
+    assert (t["ix0"], t["ix1"], t["iy0"], t["iy1"]) == (2, 4, 2, 3)
+    assert t["peers"] == [4, -1, 3, -1] and t["halo"] == [4, 0, 8, 0]
