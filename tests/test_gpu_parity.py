@@ -195,7 +195,7 @@ def test_config2_full_size(built):
     the bench workload.  At the bench's tol 1e-10 the iteration count equals
     the oracle's (+-1) and both iterative solutions agree; solved to 1e-12 the
     FP64 solution is within 1e-10 of the oracle's bordered direct solve and of
-    its Algorithm 3 (the benchmark spec's bound for the FP64 path)."""
+    its Algorithm 3 (the bound required of the FP64 path)."""
     og = SMPMGrid(16, 16, 16)
     osys = SchurSystem(og)
     lg = Grid(16, 16, 16)
