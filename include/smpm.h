@@ -146,7 +146,8 @@ smpm_status smpm_node_mass(smpm_handle h, double* w);
  * cudaStream_t (null = legacy default stream).  Errors: EINVAL (also for
  * precond > 0 on a grid with a single interface, whose only block-Jacobi
  * block is the whole singular S), ENOINTERFACE, ENOMEM (also, before any
- * work, when the dense coarse step's 6 (d+1)^2 host doubles exceed the
+ * work, when the dense coarse step's 3 (d+1)^2 host doubles (5 with
+ * SMPM_FLAG_ADJOINT) exceed the
  * machine's physical memory, and for any failed host allocation), ECUDA.
  * No C++ exception leaves any entry point of this library. */
 smpm_status schur_factor(smpm_handle h, const smpm_opts* o, void* stream);

@@ -101,10 +101,11 @@ struct DenseLU {
   bool ok = false;
 };
 
-DenseLU lu_factor(const double* A, int n) {
+// Factors the matrix held in A (moved in: no second copy of it is made).
+DenseLU lu_factor_move(std::vector<double>&& A, int n) {
   DenseLU f;
   f.n = n;
-  f.a.assign(A, A + static_cast<size_t>(n) * n);
+  f.a = std::move(A);
   f.piv.resize(n);
   double* a = f.a.data();
   f.ok = true;
@@ -700,7 +701,7 @@ int block_factors(const Geometry& g, const std::vector<int>& black, const std::v
             for (int q = 0; q < n; ++q) acc += X[(F * n + t) * n + q] * Y[(F * n + q) * M + col];
             A[(F * n + t) * M + col] = (F * n + t == col ? 1.0 : 0.0) - acc;
           }
-      DenseLU lu = lu_factor(A.data(), M);
+      DenseLU lu = lu_factor_move(std::move(A), M);
       if (!lu.ok) { bad += 1; continue; }
       std::vector<double> Gi(static_cast<size_t>(M) * M), col(M);
       for (int j = 0; j < M; ++j) {
@@ -795,13 +796,14 @@ void diff_matrix(const std::vector<double>& x, std::vector<double>* D) {
   }
 }
 
-// The coarse solve is dense (Sec. 2): C, the bordered K, its LU, the leading
-// block of K^-1, H = C^+ and its adjoint hold up to 6 (d+1)^2 doubles on the
-// host at once.  Refused before any work when that exceeds the machine's
-// physical memory.
-static int coarse_memory_check(const Geometry& g, std::string* err) {
+// The coarse solve is dense (Sec. 2): C, the LU of the bordered K (factored
+// in place) and the leading block of K^-1, which becomes H = C^+ in place,
+// hold 3 (d+1)^2 doubles on the host at once; with the adjoint, H and the
+// adjoint's Ha are separate arrays (5 (d+1)^2).  Refused before any work
+// when that exceeds the machine's physical memory.
+static int coarse_memory_check(const Geometry& g, bool adjoint, std::string* err) {
   const double dd = static_cast<double>(g.d + 1);
-  const double need = 6.0 * dd * dd * sizeof(double);
+  const double need = (adjoint ? 5.0 : 3.0) * dd * dd * sizeof(double);
   const long pages = sysconf(_SC_PHYS_PAGES), page = sysconf(_SC_PAGE_SIZE);
   const double have = static_cast<double>(pages) * static_cast<double>(page);
   if (pages <= 0 || page <= 0 || need <= have) return SMPM_OK;
@@ -816,7 +818,7 @@ static int coarse_memory_check(const Geometry& g, std::string* err) {
 static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, std::string* err) {
   const bool op_only = (o.flags & SMPM_FLAG_OPERATOR_ONLY) != 0;
   if (!op_only) {
-    const int st = coarse_memory_check(g, err);
+    const int st = coarse_memory_check(g, (o.flags & SMPM_FLAG_ADJOINT) != 0, err);
     if (st != SMPM_OK) return st;
   }
   const int n = g.n, M = g.M;
@@ -976,7 +978,7 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
       K1[static_cast<size_t>(i) * d1 + d] = f->c0[i] / c0n;
       K1[static_cast<size_t>(d) * d1 + i] = f->c0[i] / c0n;
     }
-    DenseLU lu = lu_factor(K1.data(), d1);
+    DenseLU lu = lu_factor_move(std::move(K1), d1);
     if (!lu.ok) { *err = "singular bordered coarse matrix"; return SMPM_EINVAL; }
     std::vector<double> y(d1, 0.0);
     y[d] = 1.0;
@@ -1002,13 +1004,18 @@ static int factor_host_body(const Geometry& g, const smpm_opts& o, Factors* f, s
       for (int i = 0; i < d; ++i)
         for (int c = 0; c < nc; ++c) Kinv[static_cast<size_t>(i) * d + j0 + c] = Bm[static_cast<size_t>(i) * nc + c];
     }
-    f->H.assign(static_cast<size_t>(d) * d, 0.0);
+    // H = Kinv (I - u_C u_C^T); in place unless the adjoint needs Kinv
+    const bool keep = (o.flags & SMPM_FLAG_ADJOINT) != 0;
+    lu = DenseLU();
+    if (keep) f->H.assign(static_cast<size_t>(d) * d, 0.0);
+    double* Hd = keep ? f->H.data() : Kinv.data();
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < d; ++i) {
       double s = 0;
       for (int j = 0; j < d; ++j) s += Kinv[static_cast<size_t>(i) * d + j] * f->uC[j];
-      for (int j = 0; j < d; ++j) f->H[static_cast<size_t>(i) * d + j] = Kinv[static_cast<size_t>(i) * d + j] - s * f->uC[j];
+      for (int j = 0; j < d; ++j) Hd[static_cast<size_t>(i) * d + j] = Kinv[static_cast<size_t>(i) * d + j] - s * f->uC[j];
     }
+    if (!keep) f->H = std::move(Kinv);
   }
 
   // null vectors of S and L

@@ -54,7 +54,7 @@ def test_bad_arguments():
 
 def test_coarse_step_beyond_host_memory_is_refused_before_any_work():
     """A 4096 x 4096 grid has d = 33,546,240 interfaces: its dense coarse
-    matrices (about 6 d^2 doubles) exceed any host, and the factor step says
+    matrices (3 d^2 doubles at least) exceed any host, and the factor step says
     so with ENOMEM at once instead of allocating the element factors first."""
     import time
     g = B.Grid(4096, 4096, 2)
