@@ -364,9 +364,74 @@ __device__ void lk_coarse_h(const LockArgs<S>& A, const HT* H) {
   }
 }
 
-// FP32 inner solves apply the coarse inverse's FP32 copy (see coarse_rows32)
+// FP32 columns: the coarse inverse's FP32 copy (see coarse_rows32).  The R
+// coarse vectors are converted to FP32 once per CTA, a chunk of dc entries of
+// every column at a time, into the idle warp tiles (converting them on every
+// row's pass costs as much as FP64 products); each warp keeps its rows'
+// partial sums in c_hat across the chunks.
 template <typename S>
-__device__ void lk_coarse(const LockArgs<S>& A) {
+__device__ void lk_coarse32_staged(const LockArgs<S>& A, float* cf, int dc) {
+  const GmresArgs<S>& a = A.a;
+  const int d = (int)a.g.d, R = A.R;
+  const int per = (d + a.G - 1) / a.G;
+  const int r0 = team_rank(a) * per, r1 = min(d, r0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  constexpr int CG = 8;
+  for (int j0 = 0; j0 < d; j0 += dc) {
+    const int len = min(dc, d - j0);
+    for (int i = threadIdx.x; i < R * len; i += blockDim.x) {
+      const int c = i / len, j = i - c * len;
+      cf[(size_t)c * dc + j] = (float)__ldcg(a.c + (size_t)c * A.ds + j0 + j);
+    }
+    __syncthreads();
+    for (int r = r0 + warp; r < r1; r += nwarps) {
+      const float* hr = a.H + (size_t)r * d + j0;
+      for (int c0 = 0; c0 < R; c0 += CG) {
+        const int nc = min(CG, R - c0);
+        const float* cc = cf + (size_t)c0 * dc;
+        float acc[CG];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[c] = 0.f;
+        int j = lane;
+        for (; j + 32 * 7 < len; j += 32 * 8) {  // eight entries per lane per step, loaded first
+          float h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = __ldg(hr + j + 32 * u);
+#pragma unroll
+          for (int c = 0; c < CG; ++c)
+            if (c < nc)
+#pragma unroll
+              for (int u = 0; u < 8; ++u) acc[c] += h[u] * cc[(size_t)c * dc + j + 32 * u];
+        }
+        for (; j < len; j += 32) {
+          const float hv = __ldg(hr + j);
+#pragma unroll
+          for (int c = 0; c < CG; ++c)
+            if (c < nc) acc[c] += hv * cc[(size_t)c * dc + j];
+        }
+#pragma unroll
+        for (int c = 0; c < CG; ++c)
+          if (c < nc) {
+            const float v = warp_sum(acc[c]);
+            double* out = a.chat + (size_t)(c0 + c) * A.ds + r;
+            if (lane == 0) *out = (j0 == 0 ? 0.0 : *out) + (double)v;
+          }
+      }
+    }
+    __syncthreads();  // the warp tiles take the next chunk, or the next phase
+  }
+}
+
+template <typename S>
+__device__ void lk_coarse(const LockArgs<S>& A, const LockSmem<S>& s) {
+  if constexpr (sizeof(S) == 4) {
+    const int room = (int)((size_t)(blockDim.x / 32) * lock_tile_elems(A.a.g.M, A.RC));
+    const int dc = (room / A.R) & ~31;  // entries per column and chunk
+    if (dc >= 256) {
+      lk_coarse32_staged(A, reinterpret_cast<float*>(s.wb), dc);
+      return;
+    }
+  }
   lk_coarse_h(A, A.a.H);
 }
 
@@ -385,7 +450,7 @@ __device__ bool lk_apply(const LockArgs<S>& A, const LockSmem<S>& s, const S* sr
   if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
   GM_TRACE(34);
   if (a.precond == 2) {
-    lk_coarse(A);
+    lk_coarse(A, s);
     GM_TRACE(35);
     if (!grid_sync(a.bar, a.err, epoch, a.G)) return false;
     GM_TRACE(36);
