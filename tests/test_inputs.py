@@ -50,3 +50,20 @@ def test_uneven_batch_recipe():
     assert a[:, 3].min() == 1 and a[:, 3].max() == 16
     assert a[:, 3].sum() == 4460                                        # the benchmark's right-hand-side count
     assert inputs.uneven_batch(512, seed=8) != probs
+
+
+def test_graded_edges_recipe():
+    """Clustered edges: symmetric, strictly increasing, exact end points,
+    thinnest at the walls; jittered edges: seeded, within 0.3 h of uniform."""
+    for m, L, st in ((8, 1.0, 2.0), (24, 1.3, 2.0), (5, 0.5, 1.5)):
+        e = inputs.clustered_edges(m, L, st)
+        h = np.diff(e)
+        assert e[0] == 0.0 and e[-1] == L and np.all(h > 0)
+        np.testing.assert_allclose(e + e[::-1], L, atol=1e-14)      # symmetric about L / 2
+        assert h[0] == h.min() and h[len(h) // 2] >= h.max() * (1 - 1e-12)
+    assert np.diff(inputs.clustered_edges(24, 1.0, 2.0)).max() / np.diff(inputs.clustered_edges(24, 1.0, 2.0)).min() > 10
+    e1, e2 = inputs.jittered_edges(7, 1.4, 3), inputs.jittered_edges(7, 1.4, 3)
+    assert np.array_equal(e1, e2) and not np.array_equal(e1, inputs.jittered_edges(7, 1.4, 4))
+    u = np.arange(8) * (1.4 / 7)
+    assert e1[0] == 0.0 and abs(e1[-1] - 1.4) < 1e-15 and np.all(np.diff(e1) > 0)
+    assert np.abs(e1 - u).max() <= 0.3 * 1.4 / 7 + 1e-15
