@@ -1,7 +1,7 @@
 """The element-tile partition (smpm_partition_tile / smpm_partition_halo)
 driving Algorithm 3 over gloo ranks on the CPU: every operator of the
 sharded solve (S, M^-1, P, Q, all-reduced dots) and the whole deflated GMRES
-against the oracle's global ones, on 2 and 4 ranks, a uniform and a graded
+against the oracle's global ones, on 2, 3 and 4 ranks, a uniform and a graded
 grid.  The tiles and halo lists are also checked on their own: they cover
 every element once, each cut has matching lists on its two sides, and the
 halo is n slots per cut interface."""
@@ -97,8 +97,8 @@ def _worker(rank, world, port, spec, px, py, inputs_, out):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("spec,px,py", [(UNIFORM, 2, 1), (UNIFORM, 2, 2), (GRADED, 2, 2)],
-                         ids=["uniform-2x1", "uniform-2x2", "graded-2x2"])
+@pytest.mark.parametrize("spec,px,py", [(UNIFORM, 2, 1), (UNIFORM, 3, 1), (UNIFORM, 2, 2), (GRADED, 2, 2)],
+                         ids=["uniform-2x1", "uniform-3x1", "uniform-2x2", "graded-2x2"])
 def test_sharded_algorithm3_matches_oracle(spec, px, py):
     og, lg = _grids(spec)
     lg.factor_host_only(tol=1e-11)   # builds the library before the ranks start
